@@ -1,0 +1,294 @@
+"""Pins that tie the FP64 oracle to facts fixed by the paper or by mathematics.
+
+Each ``pin_*`` takes the oracle function(s) it checks as arguments and raises
+AssertionError when the fact does not hold, so the same pin runs against the
+real oracle (tests/test_oracle_*.py) and against copies with a planted mistake
+(tests/test_oracle_mutations.py), which it must reject.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+from workloads import synth
+
+
+# --------------------------------------------------------------- Philox / draw
+
+def pin_philox_matches_numpy(philox_fn, cases=None):
+    """numpy's Philox4x64-10 (an independent implementation) increments its
+    256-bit counter before each block, so block(counter c) == numpy's first
+    four raw outputs when started from counter c - 1."""
+    rng = np.random.default_rng(5)
+    if cases is None:
+        cases = [((0, 0, 0, 0), (0, 0)), ((1, 0, 0, 0), (1607, 0)), ((0, 1, 0, 0), (2**64 - 1, 3)),
+                 ((2**64 - 1, 7, 0, 0), (12345, 1)), ((0, 0, 0, 1), (99, 2))]
+        for _ in range(20):
+            cases.append((tuple(int(x) for x in rng.integers(0, 2**64, 4, dtype=np.uint64, endpoint=False)),
+                          tuple(int(x) for x in rng.integers(0, 2**64, 2, dtype=np.uint64, endpoint=False))))
+    for ctr, key in cases:
+        c = ctr[0] | (ctr[1] << 64) | (ctr[2] << 128) | (ctr[3] << 192)
+        c = (c - 1) % (1 << 256)
+        start = np.array([(c >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+        bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=start)
+        want = tuple(int(x) for x in bg.random_raw(4))
+        got = tuple(int(x) for x in philox_fn(ctr, key))
+        assert got == want, (ctr, key)
+
+
+def pin_draw_is_partial_fisher_yates(draw_fn, philox_fn, N=37, k=11, seed=3, tag=1):
+    """The sparse-map draw equals Fisher-Yates run on an explicit array."""
+    a = list(range(N))
+    for i in range(k):
+        r = philox_fn((i, 0, 0, 0), (seed, tag))[0]
+        j = i + ((r * (N - i)) >> 64)
+        a[i], a[j] = a[j], a[i]
+    drawn, srt = draw_fn(seed, tag, N, k)
+    assert list(drawn) == a[:k]
+    assert list(srt) == sorted(a[:k])
+
+
+def pin_draw_uniform(draw_fn, N=20, k=4, trials=3000, seed0=100):
+    """Each index is drawn with probability k/N (chi-square), all distinct and in range."""
+    counts = np.zeros(N)
+    first = np.zeros(N)
+    for s in range(trials):
+        drawn, srt = draw_fn(seed0 + s, 0, N, k)
+        assert len(set(drawn.tolist())) == k and drawn.min() >= 0 and drawn.max() < N
+        assert np.all(np.diff(srt) > 0)
+        counts[drawn] += 1
+        first[drawn[0]] += 1
+    from scipy.stats import chisquare
+    assert chisquare(counts).pvalue > 1e-4
+    assert chisquare(first).pvalue > 1e-4
+
+
+# ----------------------------------------------------------------- sketching
+
+def pin_gather_intersection(gather_fn, A, rows, cols):
+    """W = R[:, J] = C[I, :] by definition (Algorithm 2, step 1)."""
+    C, Rt, W = gather_fn(A, rows, cols)
+    assert C.shape == (A.shape[0], len(cols)) and Rt.shape == (A.shape[1], len(rows))
+    assert np.array_equal(W, C[rows, :])
+    assert np.array_equal(W, Rt[cols, :].T)
+    assert np.array_equal(C[:, 0], np.asarray(A[:, cols[0]], dtype=np.float64))
+    assert np.array_equal(Rt[:, 0], np.asarray(A[rows[0], :], dtype=np.float64))
+
+
+def pin_pinv_exact_recovery(gather_fn, sketch_fn, m=60, n=45, r=5, k=8, seed=11):
+    """An exactly rank-r A with rank(W) = r is recovered exactly by C W^+ R."""
+    A = synth.exact_lowrank_int(m, n, r, seed=seed)
+    g = np.random.default_rng(seed)
+    for _ in range(3):
+        rows = np.sort(g.choice(m, k, replace=False))
+        cols = np.sort(g.choice(n, k, replace=False))
+        C, Rt, W = gather_fn(A, rows, cols)
+        if np.linalg.matrix_rank(W) != r:
+            continue
+        sk = sketch_fn(C, Rt, W, m, n, "pinv", 0.0)
+        assert sk.rank == r
+        Ah = (sk.U * sk.S) @ sk.V.T
+        assert np.linalg.norm(A - Ah) <= 1e-12 * np.linalg.norm(A)
+        return
+    raise AssertionError("no full-rank W drawn")
+
+
+def pin_pinv_equals_pseudoskeleton(gather_fn, sketch_fn, m=50, n=40, k=9, seed=4):
+    """U S V^T equals C W^+ R with W^+ from scipy's pinv (a different SVD driver)."""
+    import scipy.linalg
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((m, n))
+    rows = np.sort(g.choice(m, k, replace=False))
+    cols = np.sort(g.choice(n, k, replace=False))
+    C, Rt, W = gather_fn(A, rows, cols)
+    sk = sketch_fn(C, Rt, W, m, n, "pinv", 0.0)
+    want = C @ scipy.linalg.pinv(W) @ Rt.T
+    got = (sk.U * sk.S) @ sk.V.T
+    assert np.linalg.norm(got - want) <= 1e-9 * np.linalg.norm(want)
+
+
+def pin_stabilized_rank1_closed_form(gather_fn, sketch_fn, m=40, n=30, k=6, seed=2):
+    """For A = x y^T the stabilised routine returns exactly
+    A * |x_I| |y_J| sqrt(mn) / (k |x| |y|): sigma_1 = |x_I||y_J|, N_c = |x||y_J|,
+    N_r = |y||x_I|, S = sigma_1 sqrt(mn)/k. For sign vectors the factor is 1."""
+    g = np.random.default_rng(seed)
+    x = g.uniform(0.5, 2.0, m) * g.choice([-1.0, 1.0], m)
+    y = g.uniform(0.5, 2.0, n) * g.choice([-1.0, 1.0], n)
+    A = np.outer(x, y)
+    rows = np.sort(g.choice(m, k, replace=False))
+    cols = np.sort(g.choice(n, k, replace=False))
+    C, Rt, W = gather_fn(A, rows, cols)
+    sk = sketch_fn(C, Rt, W, m, n, "stabilized", 0.0)
+    assert sk.rank == 1
+    fac = np.linalg.norm(x[rows]) * np.linalg.norm(y[cols]) * math.sqrt(m * n) / (
+        k * np.linalg.norm(x) * np.linalg.norm(y))
+    Ah = (sk.U * sk.S) @ sk.V.T
+    assert np.allclose(Ah, fac * A, rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    assert abs(sk.S[0] - np.linalg.norm(x[rows]) * np.linalg.norm(y[cols]) * math.sqrt(m * n) / k) <= 1e-12 * sk.S[0]
+    xs, ys = np.sign(x), np.sign(y)
+    A = np.outer(xs, ys)
+    C, Rt, W = gather_fn(A, rows, cols)
+    sk = sketch_fn(C, Rt, W, m, n, "stabilized", 0.0)
+    assert np.allclose((sk.U * sk.S) @ sk.V.T, A, rtol=0, atol=1e-12)
+
+
+def pin_stabilized_rank2_hadamard(gather_fn, sketch_fn):
+    """A = a x1 y1^T + b x2 y2^T with Hadamard sign vectors whose samples stay
+    orthogonal: W's SVD is known in closed form and the stabilised routine
+    recovers A exactly, with S = (a sqrt(mn), b sqrt(mn))."""
+    H8 = np.array([[1, 1, 1, 1, 1, 1, 1, 1], [1, -1, 1, -1, 1, -1, 1, -1],
+                   [1, 1, -1, -1, 1, 1, -1, -1], [1, -1, -1, 1, 1, -1, -1, 1]], dtype=np.float64)
+    x1, x2 = np.tile(H8[1], 2), np.tile(H8[2], 2)          # m = 16
+    y1, y2 = np.tile(H8[1], 3), np.tile(H8[3], 3)          # n = 24
+    a, b = 3.0, 0.5
+    A = a * np.outer(x1, y1) + b * np.outer(x2, y2)
+    rows = np.array([0, 1, 2, 3])      # x1 = (1,-1,1,-1), x2 = (1,1,-1,-1): orthogonal
+    cols = np.array([8, 9, 10, 11])    # y1 = (1,-1,1,-1), y2 = (1,-1,-1,1): orthogonal
+    C, Rt, W = gather_fn(A, rows, cols)
+    sk = sketch_fn(C, Rt, W, 16, 24, "stabilized", 0.0)
+    assert sk.rank == 2
+    assert np.allclose(sk.sig[:2], [a * 4, b * 4], rtol=1e-14)
+    assert np.allclose(sk.S[:2], [a * math.sqrt(16 * 24), b * math.sqrt(16 * 24)], rtol=1e-13)
+    assert np.allclose((sk.U * sk.S) @ sk.V.T, A, atol=1e-12)
+
+
+def pin_unit_columns_and_truncation(gather_fn, sketch_fn, m=70, n=50, k=10, r=4, seed=9):
+    """Kept columns of U and V have unit norm, dropped ones are zero, and a
+    rank-r W keeps exactly r components; singular values match scipy's gesvd."""
+    import scipy.linalg
+    A = synth.exact_lowrank_int(m, n, r, seed=seed) + 0.0
+    g = np.random.default_rng(seed)
+    rows = np.sort(g.choice(m, k, replace=False))
+    cols = np.sort(g.choice(n, k, replace=False))
+    C, Rt, W = gather_fn(A, rows, cols)
+    for mode in ("pinv", "stabilized"):
+        sk = sketch_fn(C, Rt, W, m, n, mode, 0.0)
+        assert sk.rank == np.linalg.matrix_rank(W)
+        nu = np.linalg.norm(sk.U, axis=0)
+        nv = np.linalg.norm(sk.V, axis=0)
+        assert np.allclose(nu[:sk.rank], 1, atol=1e-14) and np.all(nu[sk.rank:] == 0)
+        assert np.allclose(nv[:sk.rank], 1, atol=1e-14) and np.all(nv[sk.rank:] == 0)
+        assert np.all(sk.S[sk.rank:] == 0) and np.all(sk.S[:sk.rank] > 0)
+        ref = scipy.linalg.svd(W, compute_uv=False, lapack_driver="gesvd")
+        assert np.allclose(sk.sig, ref, rtol=1e-12, atol=1e-12 * ref[0])
+
+
+# ------------------------------------------------------------------- k-means
+
+def _blobs(m, k2, d=2, seed=0, spread=0.05):
+    g = np.random.default_rng(seed)
+    centers = g.uniform(-5, 5, (k2, d))
+    lab = np.arange(m) % k2
+    return centers[lab] + spread * g.standard_normal((m, d))
+
+
+def pin_kmeans_bruteforce_optimum(kmeans_fn, trials=6):
+    """On tiny well-separated blobs, Lloyd from one point per blob reaches the
+    weighted-SSE optimum found by enumerating every labelling."""
+    for t in range(trials):
+        m, k2 = (7, 2) if t % 2 == 0 else (8, 3)
+        X = _blobs(m, k2, seed=t)
+        p = [0.0, 1.0, 2.0][t % 3]
+        w = np.linalg.norm(X, axis=1) ** p if p else np.ones(m)
+        best = np.inf
+        for lab in itertools.product(range(k2), repeat=m):
+            lab = np.array(lab)
+            e = 0.0
+            for j in range(k2):
+                mem = lab == j
+                if mem.any():
+                    z = (w[mem, None] * X[mem]).sum(0) / w[mem].sum()
+                    e += float((w[mem] * ((X[mem] - z) ** 2).sum(1)).sum())
+            best = min(best, e)
+        init = [j for j in range(k2)]          # rows 0..k2-1 lie in distinct blobs
+        res = kmeans_fn(X, init, 4, p)
+        D = np.array([((X - z) ** 2).sum(1) for z in res.Z]).T
+        e_final = float((w * D.min(1)).sum())
+        assert e_final <= best * (1 + 1e-9) + 1e-12, (e_final, best)
+
+
+def pin_kmeans_steps_exhaustive(kmeans_fn, M=40, d=3, k2=5, iters=4, p=1.0, seed=3):
+    """Every assignment is the lowest-index minimum over all centres, every
+    centre is the weighted mean of its members (or unchanged when empty), and
+    the weighted objective never increases (Eq. wkmeans)."""
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((M, d))
+    res = kmeans_fn(X, list(range(k2)), iters, p)
+    w = [math.sqrt(sum(float(v) ** 2 for v in X[l])) ** p for l in range(M)]
+    for t in range(iters):
+        Z = res.centres[t]
+        for l in range(M):
+            ds = [sum((float(X[l, q]) - float(Z[j, q])) ** 2 for q in range(d)) for j in range(k2)]
+            jbest = min(range(k2), key=lambda j: (ds[j], j))
+            assert res.labels[t][l] == jbest
+        Zn = res.centres[t + 1]
+        for j in range(k2):
+            mem = [l for l in range(M) if res.labels[t][l] == j]
+            ws = sum(w[l] for l in mem)
+            if ws > 0:
+                want = [sum(w[l] * float(X[l, q]) for l in mem) / ws for q in range(d)]
+            else:
+                want = list(Z[j])
+            assert np.allclose(Zn[j], want, rtol=1e-13, atol=1e-13)
+        e = sum(w[l] * sum((float(X[l, q]) - float(Z[res.labels[t][l], q])) ** 2 for q in range(d)) for l in range(M))
+        assert abs(e - res.energy[t]) <= 1e-10 * max(1.0, e)
+    assert all(res.energy[t + 1] <= res.energy[t] * (1 + 1e-12) for t in range(iters - 1))
+
+
+def pin_kmeans_ties_and_empty(kmeans_fn):
+    """A point equidistant from two centres goes to the lower index; a centre
+    that wins no point keeps its position."""
+    X = np.array([[0.0, 0.0], [2.0, 0.0], [1.0, 0.0], [10.0, 10.0]])
+    res = kmeans_fn(X, [0, 1], 1, 0.0)
+    assert res.labels[0].tolist() == [0, 1, 0, 1]
+    X = np.array([[1.0, 1.0], [1.0, 1.0], [1.5, 1.0], [5.0, 5.0]])
+    res = kmeans_fn(X, [0, 1, 3], 2, 0.0)
+    # centre 1 duplicates centre 0 and loses every tie -> empty, keeps (1, 1)
+    assert res.labels[0].tolist() == [0, 0, 0, 2]
+    assert np.array_equal(res.centres[1][1], [1.0, 1.0])
+    assert np.allclose(res.centres[1][0], [3.5 / 3, 1.0])
+
+
+def pin_kmeans_matches_sklearn(kmeans_fn, M=300, d=6, k2=7, iters=5, seed=1):
+    """sklearn's weighted Lloyd (independent code) gives the same centres
+    when no cluster empties."""
+    import pytest
+    sk = pytest.importorskip("sklearn.cluster")
+    g = np.random.default_rng(seed)
+    X = _blobs(M, k2, d=d, seed=seed, spread=1.0)
+    w = np.linalg.norm(X, axis=1) ** 1.5
+    init = list(range(k2))
+    res = kmeans_fn(X, init, iters, 1.5)
+    km = sk.KMeans(n_clusters=k2, init=X[init], n_init=1, max_iter=iters, tol=0.0,
+                   algorithm="lloyd").fit(X, sample_weight=w)
+    assert np.allclose(km.cluster_centers_, res.Z, rtol=1e-10, atol=1e-10)
+
+
+def pin_snap_bruteforce(snap_fn, M=30, d=3, k2=6, seed=8):
+    """Greedy distinct nearest rows, checked with explicit loops; the result is sorted."""
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((M, d))
+    Z = g.standard_normal((k2, d)) * 0.3
+    Z[1] = Z[0]                      # two centres with the same nearest row
+    order, srt = snap_fn(X, Z)
+    taken = []
+    for j in range(k2):
+        ds = [(sum((float(X[l, q]) - float(Z[j, q])) ** 2 for q in range(d)), l) for l in range(M) if l not in taken]
+        taken.append(min(ds)[1])
+    assert order.tolist() == taken
+    assert srt.tolist() == sorted(taken)
+    assert len(set(taken)) == k2
+
+
+# ---------------------------------------------------------------------- error
+
+def pin_error_closed_form(err_fn):
+    """|A - U S V^T|_F / |A|_F on a case computed by hand: A = I_2, U = V = e1, S = 1
+    leaves the residual e2 e2^T, so the error is 1/sqrt(2)."""
+    A = np.eye(2)
+    U = np.array([[1.0], [0.0]])
+    V = np.array([[1.0], [0.0]])
+    assert abs(err_fn(A, U, np.array([1.0]), V) - 1 / math.sqrt(2)) < 1e-15
+    assert err_fn(A, np.eye(2), np.ones(2), np.eye(2)) == 0.0

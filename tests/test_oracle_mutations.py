@@ -1,0 +1,111 @@
+"""Plants plausible mistakes in copies of oracle functions and checks that the
+pins reject every one of them (a dropped term, a wrong sign or index, a
+transposed operand). Runs on the CPU only; the oracle itself is not modified."""
+import inspect
+import textwrap
+
+import numpy as np
+import pytest
+
+from oracle import cabs_ref as o
+from tests import oracle_pins as pins
+
+
+def mutate(fn, old, new):
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, (fn.__name__, old)
+    ns = dict(o.__dict__)
+    exec(compile(src.replace(old, new), f"<mutant {fn.__name__}>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+def rejects(check):
+    try:
+        check()
+    except (AssertionError, IndexError, ValueError, ZeroDivisionError, FloatingPointError):
+        return True
+    return False
+
+
+SKETCH_MUTANTS = [
+    ("a = C @ Vw[:, :r]", "a = C @ Uw[:, :r]"),                         # transposed factor
+    ("b = Rt @ Uw[:, :r]", "b = Rt @ Vw[:, :r]"),
+    ("S[i] = Nc[i] * Nr[i] / sig[i]", "S[i] = Nc[i] * Nr[i] * sig[i]"),  # wrong exponent
+    ("S[i] = Nc[i] * Nr[i] / sig[i]", "S[i] = Nc[i] / sig[i]"),          # dropped term
+    ("S[i] = sig[i] * math.sqrt(m * n / (k_r * k_c))", "S[i] = sig[i]"),  # dropped scale
+    ("S[i] = sig[i] * math.sqrt(m * n / (k_r * k_c))", "S[i] = sig[i] * math.sqrt(m * n) / (k_r * k_c)"),
+    ("V[:, i] = b[:, i] / Nr[i]", "V[:, i] = b[:, i]"),                  # dropped normalisation
+    ("r = int(np.count_nonzero(sig > tol))", "r = int(np.count_nonzero(sig >= 0))"),  # no truncation
+]
+
+
+@pytest.mark.parametrize("old,new", SKETCH_MUTANTS)
+def test_sketching_mutants_rejected(old, new):
+    bad = mutate(o.sketching, old, new)
+    checks = [lambda: pins.pin_pinv_exact_recovery(o.gather_dense, bad),
+              lambda: pins.pin_pinv_equals_pseudoskeleton(o.gather_dense, bad),
+              lambda: pins.pin_stabilized_rank1_closed_form(o.gather_dense, bad),
+              lambda: pins.pin_stabilized_rank2_hadamard(o.gather_dense, bad),
+              lambda: pins.pin_unit_columns_and_truncation(o.gather_dense, bad)]
+    assert any(rejects(c) for c in checks)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("Rt = np.array(A[rows, :].T, dtype=np.float64)", "Rt = np.array(A[:, rows], dtype=np.float64)"),
+    ("W = np.array(A[np.ix_(rows, cols)], dtype=np.float64)", "W = np.array(A[np.ix_(cols, rows)].T, dtype=np.float64)"),
+])
+def test_gather_mutants_rejected(old, new):
+    bad = mutate(o.gather_dense, old, new)
+    A = np.arange(60.0).reshape(6, 10)
+    assert rejects(lambda: pins.pin_gather_intersection(bad, A, np.array([1, 4]), np.array([0, 3, 9])))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("for _ in range(10):", "for _ in range(9):"),
+    ("k0 = (k0 + _W0) & MASK64", "k0 = (k0 + _W1) & MASK64"),
+    ("c0, c1, c2, c3 = ((p1 >> 64) ^ c1 ^ k0, p1 & MASK64, (p0 >> 64) ^ c3 ^ k1, p0 & MASK64)",
+     "c0, c1, c2, c3 = ((p0 >> 64) ^ c1 ^ k0, p1 & MASK64, (p1 >> 64) ^ c3 ^ k1, p0 & MASK64)"),
+])
+def test_philox_mutants_rejected(old, new):
+    bad = mutate(o.philox4x64_10, old, new)
+    assert rejects(lambda: pins.pin_philox_matches_numpy(bad))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("j = i + mulhi64(r, N - i)", "j = i + mulhi64(r, N)"),
+    ("j = i + mulhi64(r, N - i)", "j = mulhi64(r, N - i)"),
+    ("moved[j] = vi", "moved[j] = vj"),
+])
+def test_draw_mutants_rejected(old, new):
+    bad = mutate(o.draw_indices, old, new)
+    assert rejects(lambda: pins.pin_draw_is_partial_fisher_yates(bad, o.philox4x64_10)) or \
+        rejects(lambda: pins.pin_draw_uniform(bad, trials=500))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("Znew[j] = (w[mem, None] * X[mem]).sum(axis=0) / wsum", "Znew[j] = X[mem].mean(axis=0)"),  # weights dropped
+    ("s = np.argmin(D, axis=1)", "s = D.shape[1] - 1 - np.argmin(D[:, ::-1], axis=1)"),         # ties to highest
+    ("Znew = Z.copy()", "Znew = np.zeros_like(Z)"),                                             # empty -> origin
+    ("res.energy.append(float((w * best).sum()))", "res.energy.append(float(best.sum()))"),      # unweighted energy
+])
+def test_kmeans_mutants_rejected(old, new):
+    bad = mutate(o.weighted_kmeans, old, new)
+    checks = [lambda: pins.pin_kmeans_steps_exhaustive(bad),
+              lambda: pins.pin_kmeans_ties_and_empty(bad),
+              lambda: pins.pin_kmeans_bruteforce_optimum(bad, trials=3)]
+    assert any(rejects(c) for c in checks)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("d[taken] = np.inf", "pass"),
+    ("taken[l] = True", "taken[l] = False"),
+])
+def test_snap_mutants_rejected(old, new):
+    bad = mutate(o.snap, old, new)
+    assert rejects(lambda: pins.pin_snap_bruteforce(bad))
+
+
+def test_error_mutant_rejected():
+    bad = mutate(o.rel_fro_error_dense, "return math.sqrt(num / den) if den > 0 else 0.0",
+                 "return num / den if den > 0 else 0.0")
+    assert rejects(lambda: pins.pin_error_closed_form(bad))

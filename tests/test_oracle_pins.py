@@ -1,0 +1,141 @@
+"""The FP64 oracle checked against what the paper and mathematics fix (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import cabs_ref as o
+from tests import oracle_pins as pins
+from workloads import synth
+
+
+def test_philox_matches_numpy_philox():
+    pins.pin_philox_matches_numpy(o.philox4x64_10)
+
+
+def test_philox_vectorised_matches_scalar():
+    g = np.random.default_rng(0)
+    c = g.integers(0, 2**63, (4, 64), dtype=np.int64).astype(np.uint64) * np.uint64(2)
+    key = (2**64 - 5, 77)
+    v = o.philox4x64_10_vec(c[0], c[1], c[2], c[3], *key)
+    for t in range(64):
+        want = o.philox4x64_10(tuple(int(x) for x in c[:, t]), key)
+        assert tuple(int(x[t]) for x in v) == want
+
+
+def test_mulhi64():
+    assert o.mulhi64(2**63, 10) == 5
+    assert o.mulhi64(2**64 - 1, 2**64 - 1) == 2**64 - 2
+    a = np.array([2**63, 2**64 - 1, 12345], dtype=np.uint64)
+    assert o.mulhi64_vec(a, 1000).tolist() == [500, 999, 0]
+
+
+def test_draw_is_partial_fisher_yates():
+    pins.pin_draw_is_partial_fisher_yates(o.draw_indices, o.philox4x64_10)
+    pins.pin_draw_is_partial_fisher_yates(o.draw_indices, o.philox4x64_10, N=5, k=5, seed=9, tag=0)
+
+
+def test_draw_uniform_distinct_sorted():
+    pins.pin_draw_uniform(o.draw_indices)
+
+
+def test_draw_full_permutation_and_edges():
+    d, s = o.draw_indices(4, 0, 16, 16)
+    assert sorted(d.tolist()) == list(range(16)) and s.tolist() == list(range(16))
+    d, s = o.draw_indices(4, 0, 1, 1)
+    assert d.tolist() == [0]
+    d, s = o.draw_indices(4, 0, 10, 0)
+    assert d.size == 0
+    with pytest.raises(ValueError):
+        o.draw_indices(4, 0, 3, 4)
+
+
+def test_gather_intersection_invariant():
+    A = synth.plain_lowrank(50, 40, 3).astype(np.float32)
+    rows, cols = np.array([1, 7, 30]), np.array([0, 5, 39, 22])
+    pins.pin_gather_intersection(o.gather_dense, A, rows, cols)
+    X, Y, sig = synth.rbf_mixture(31, 40, d=4, components=3, sigma_pairs=50)
+    C, Rt, W = o.gather_rbf(X, Y, sig, rows, cols)
+    assert np.array_equal(W, C[rows, :]) and np.array_equal(W, Rt[cols, :].T)
+
+
+def test_rbf_entry_closed_forms():
+    X = np.array([[0.0, 0.0], [1.0, 1.0]], dtype=np.float32)
+    Y = np.array([[0.0, 0.0], [0.0, 2.0]], dtype=np.float32)
+    # |x - y|^2 = 2 sigma^2 -> exp(-1); x = y -> 1
+    v = o.rbf_entries(X, Y, 1.0, [0, 1, 0], [0, 0, 1])
+    assert v[0] == 1.0 and abs(v[1] - np.exp(-1.0)) < 1e-16 and abs(v[2] - np.exp(-2.0)) < 1e-16
+
+
+def test_pinv_exact_recovery_rank_k():
+    pins.pin_pinv_exact_recovery(o.gather_dense, o.sketching)
+    pins.pin_pinv_exact_recovery(o.gather_dense, o.sketching, m=80, n=33, r=8, k=8, seed=5)
+
+
+def test_pinv_equals_pseudoskeleton():
+    pins.pin_pinv_equals_pseudoskeleton(o.gather_dense, o.sketching)
+
+
+def test_stabilized_rank1_closed_form():
+    pins.pin_stabilized_rank1_closed_form(o.gather_dense, o.sketching)
+
+
+def test_stabilized_rank2_closed_form():
+    pins.pin_stabilized_rank2_hadamard(o.gather_dense, o.sketching)
+
+
+def test_unit_columns_truncation_and_svd():
+    pins.pin_unit_columns_and_truncation(o.gather_dense, o.sketching)
+
+
+def test_kmeans_bruteforce_optimum():
+    pins.pin_kmeans_bruteforce_optimum(o.weighted_kmeans)
+
+
+def test_kmeans_steps_exhaustive():
+    pins.pin_kmeans_steps_exhaustive(o.weighted_kmeans)
+    pins.pin_kmeans_steps_exhaustive(o.weighted_kmeans, p=0.0, seed=4)
+
+
+def test_kmeans_ties_and_empty_clusters():
+    pins.pin_kmeans_ties_and_empty(o.weighted_kmeans)
+
+
+def test_kmeans_matches_sklearn():
+    pins.pin_kmeans_matches_sklearn(o.weighted_kmeans)
+
+
+def test_snap_bruteforce():
+    pins.pin_snap_bruteforce(o.snap)
+
+
+def test_error_closed_form():
+    pins.pin_error_closed_form(o.rel_fro_error_dense)
+
+
+def test_philox_published_known_answers():
+    """Known-answer vectors published with Philox (Salmon et al., SC'11)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x64_10_kat.txt")
+    n = 0
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        lhs, rhs = line.split(":")
+        w = [int(x, 16) for x in lhs.split()]
+        want = tuple(int(x, 16) for x in rhs.split())
+        assert o.philox4x64_10(w[:4], w[4:6]) == want
+        n += 1
+    assert n == 3
+
+
+def test_plain_fp64_regression_fixture():
+    """The oracle still produces the committed output on the plain FP64 workload."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "plain_fp64_2000x1500_k20.json")
+    gold = json.load(open(path))
+    A = synth.plain_lowrank()
+    for mode, g in gold.items():
+        r = o.cabs(o.DenseSource(A), k1=20, iters=5, seed=1607, mode=mode)
+        assert r.pilot_rows.tolist() == g["pilot_rows"] and r.pilot_cols.tolist() == g["pilot_cols"]
+        assert r.rows.tolist() == g["rows"] and r.cols.tolist() == g["cols"]
+        assert abs(o.rel_fro_error_dense(A, r.final.U, r.final.S, r.final.V) - g["final_err"]) <= 1e-9 * g["final_err"]
