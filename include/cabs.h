@@ -1,0 +1,290 @@
+/*
+ * cabs.h -- C ABI of libcabs, a single-GPU (GB300, sm_103a) implementation of
+ * cascaded bilateral sampling (CABS; Zhang, Liu, Zhang, Xiong, Xing, Ye,
+ * "Seeing the Forest from the Trees in Two Looks: Matrix Sketching by Cascaded
+ * Bilateral Sampling", arXiv 1607.07395).
+ *
+ * Problem (Algorithm 2): given an m x n matrix A that is read only through a
+ * few of its rows and columns, return A ~ U_bar diag(S_bar) V_bar^T and the
+ * sampled row and column indices.
+ *
+ * Conventions for every call below
+ *  - Pointers named d_* or documented as "device" are CUDA device pointers of
+ *    the current device; "host" pointers are ordinary CPU memory.
+ *  - Matrices are row-major. A is m x n with leading dimension lda >= n.
+ *    C (m x k) holds the sampled columns A[:, J]; R is kept transposed,
+ *    Rt (n x k) = A[I, :]^T, as in the proof of Theorem 1 of the paper.
+ *  - The working element type ("elem") is double when prec == CABS_PREC_FP64
+ *    and float otherwise. W, Sigma_w, S and every k x k core quantity are
+ *    always double (the core solve stays in FP64).
+ *  - Index arrays are int32 and 0-based.
+ *  - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and the call returns without
+ *    waiting, unless its comment says otherwise. Outputs are valid once the
+ *    stream reaches that point.
+ *  - The caller owns every buffer it passes in, including workspaces; the
+ *    library never frees or keeps them after the call returns (the serving
+ *    loop keeps its arena until cabs_serve_stop). Inputs are never written.
+ *  - Errors are reported by the returned status only; nothing aborts and no
+ *    C++ exception crosses this interface. A readable message for the
+ *    calling thread's last failure is available from cabs_last_error().
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    computes returns CABS_ECUDA.
+ */
+#ifndef CABS_H
+#define CABS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef struct cabs_ctx cabs_ctx;
+typedef void* cabs_stream; /* cudaStream_t */
+
+typedef enum {
+  CABS_OK = 0,
+  CABS_EINVAL = 1,   /* invalid argument (null pointer, size out of range, k > min(m, n), ...) */
+  CABS_ENOMEM = 2,   /* a workspace or arena is smaller than required */
+  CABS_ECUDA = 3,    /* a CUDA call or kernel launch failed */
+  CABS_ETIMEOUT = 4, /* a bounded device-side wait gave up, or a host wait timed out */
+  CABS_EBUSY = 5,    /* serving: no free slot / request still running */
+  CABS_ERANK = 6,    /* W is numerically zero: no component survives truncation */
+  CABS_ENOTFOUND = 7 /* serving: unknown ticket */
+} cabs_status;
+
+typedef enum {
+  CABS_PREC_FP64 = 0, /* every step in FP64 (parity mode) */
+  CABS_PREC_FP32 = 1, /* FP32 gathers, extrapolation, clustering; FP64 core */
+  CABS_PREC_TF32 = 2, /* as FP32, k-means distance contraction on TF32 tensor cores */
+  CABS_PREC_BF16 = 3  /* as FP32, k-means distance contraction on BF16 tensor cores */
+} cabs_prec;
+
+typedef enum {
+  /* Pseudo-skeleton A ~ C W^+ R (Section 2.2, Eq. W): S_i = N_c,i N_r,i / sigma_i. */
+  CABS_CORE_PINV = 0,
+  /* Stabilised sketching routine (Section 4.1): S_i = sigma_i sqrt(m n) / k. */
+  CABS_CORE_STABILIZED = 1
+} cabs_core;
+
+typedef enum { CABS_SRC_DENSE = 0, CABS_SRC_RBF = 1 } cabs_source_kind;
+
+/* Where the entries of A come from. */
+typedef struct {
+  int32_t kind;     /* cabs_source_kind */
+  /* CABS_SRC_DENSE: A, device, row-major m x n, leading dimension lda >= n,
+   * FP64 when a_is_f64 != 0, else FP32. */
+  const void* A;
+  int64_t lda;
+  int32_t a_is_f64;
+  /* CABS_SRC_RBF: A[i, j] = exp(-|x_i - y_j|^2 / (2 sigma^2)), generated on
+   * demand in the working precision and never stored. X (m x d) and Y (n x d)
+   * are device FP32 row-major; 1 <= d <= CABS_MAX_D; sigma > 0. */
+  const float* X;
+  const float* Y;
+  int32_t d;
+  float sigma;
+} cabs_source;
+
+#define CABS_MAX_K 256      /* largest k1 / k2 the sketch accepts */
+#define CABS_MAX_D 64       /* largest point dimension of the RBF generator */
+#define CABS_MAX_ITERS 64   /* largest number of k-means iterations */
+
+/* Parameters of one sketch (Algorithm 2). */
+typedef struct {
+  int64_t m, n;       /* A is m x n */
+  int32_t k1;         /* pilot samples per side, 1 <= k1 <= min(m, n, CABS_MAX_K) */
+  int32_t k2;         /* follow-up samples per side, 1 <= k2 <= k1 */
+  int32_t iters;      /* k-means iterations c (Section 4: c = 5), 0..CABS_MAX_ITERS */
+  uint64_t seed;      /* Philox key word 0 of the pilot draw */
+  int32_t prec;       /* cabs_prec */
+  int32_t core;       /* cabs_core */
+  float upsilon_pow;  /* Upsilon(t) = t^p of Eq. wkmeans; 0 = unweighted */
+  double trunc_rtol;  /* keep sigma_i > max(trunc_rtol, k 2^-52) sigma_1 */
+  int32_t flags;      /* CABS_FLAG_* */
+} cabs_params;
+
+#define CABS_FLAG_FOLLOW_ERR 1 /* also compute the follow-up encoding errors e_f */
+
+/* Device-side diagnostics, written by the kernels of one sketch. */
+typedef struct {
+  int32_t rank_pilot, rank_final;         /* kept singular values of W and W_bar */
+  int32_t sweeps_pilot, sweeps_final;     /* Jacobi sweeps of the FP64 SVDs */
+  int32_t T_rows, T_cols;                 /* max cluster size (Eq. T) of the last assignment */
+  int32_t status;                         /* bit 0: an SVD hit the sweep limit */
+  int32_t rechecked;                      /* reduced precision: assignments re-checked in FP32 */
+  double e_rows[CABS_MAX_ITERS];          /* weighted encoding error per k-means iteration */
+  double e_cols[CABS_MAX_ITERS];          /*   (iteration 0 = the pilot representatives) */
+  double e_follow_rows, e_follow_cols;    /* with the snapped follow-up representatives */
+} cabs_diag;
+
+/* Where one sketch's outputs go. All device memory, allocated by the caller. */
+typedef struct {
+  void* U;              /* elem, m x k2 (ld k2): U_bar; columns >= rank are zero */
+  double* S;            /* k2: S_bar (zeros beyond rank) */
+  void* V;              /* elem, n x k2 (ld k2): V_bar */
+  int32_t* rows;        /* k2: follow-up row indices I_bar^r, ascending */
+  int32_t* cols;        /* k2: follow-up column indices I_bar^c, ascending */
+  int32_t* pilot_rows;  /* k1: pilot row indices I^r, ascending */
+  int32_t* pilot_cols;  /* k1: pilot column indices I^c, ascending */
+  cabs_diag* diag;      /* optional (may be NULL) */
+} cabs_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context bound to CUDA device `device`. Returns CABS_ECUDA when the
+ * device cannot be used, CABS_EINVAL when out is NULL. */
+cabs_status cabs_create(cabs_ctx** out, int device);
+/* Destroys a context (stops its serving loop if one runs). NULL is a no-op. */
+void cabs_destroy(cabs_ctx* ctx);
+/* Message for the calling thread's last failure ("" if none). Never NULL. */
+const char* cabs_last_error(cabs_ctx* ctx);
+/* Library version string. */
+const char* cabs_version(void);
+
+/* ------------------------------------------------------- whole sketch */
+
+/* Bytes of device workspace cabs_sketch needs for these parameters. */
+cabs_status cabs_workspace_size(const cabs_source* src, const cabs_params* p, size_t* bytes);
+
+/* One CABS sketch (Algorithm 2): pilot draw, gather, sketching and embedding,
+ * weighted k-means on both embeddings, snap, follow-up gather and sketching.
+ * ws: device workspace of at least cabs_workspace_size() bytes, 256-byte
+ * aligned, owned by the caller and not used by anything else until the
+ * stream has passed this sketch. */
+cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
+                        void* ws, size_t ws_bytes, cabs_stream stream, const cabs_result* out);
+
+/* `count` independent sketches of different sizes in one call. Member i uses
+ * src[i], p[i], out[i] and the workspace slice ws + ws_offsets[i] (host array
+ * of byte offsets, each 256-aligned, slices of cabs_workspace_size bytes).
+ * Members are scheduled largest-first over `lanes` (1..16) internal streams
+ * forked from and joined back to `stream`; with CUDA graphs enabled
+ * (use_graph != 0) the launch sequence of the batch is captured once per
+ * distinct batch layout and replayed. Results are bit-identical to running
+ * each member alone with cabs_sketch. */
+cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const cabs_source* src,
+                                const cabs_params* p, void* ws, const size_t* ws_offsets,
+                                const cabs_result* out, int32_t lanes, int32_t use_graph,
+                                cabs_stream stream);
+
+/* Relative Frobenius error |A - U diag(S) V^T|_F / |A|_F (Section 5).
+ * samples == 0: exact, over every entry (dense sources only; FP64 sums of
+ * per-tile partial sums). samples > 0: over `samples` entries drawn with
+ * replacement by Philox key (seed, 2), counter (t, 0, 0, 0): row = hi64(w0 m),
+ * column = hi64(w1 n). U (m x k), S (k), V (n x k) as produced by cabs_sketch.
+ * ws: device workspace of cabs_error_workspace_size() bytes.
+ * *rel_fro is written on the host, so this call synchronises `stream`. */
+cabs_status cabs_error_workspace_size(const cabs_source* src, const cabs_params* p,
+                                      int64_t samples, size_t* bytes);
+cabs_status cabs_error(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
+                       const cabs_result* res, int64_t samples, uint64_t seed, void* ws,
+                       size_t ws_bytes, cabs_stream stream, double* rel_fro);
+
+/* ------------------------------------------------ hot-path steps, one by one */
+
+/* Step a1, Algorithm 2 step 1: k distinct uniform indices from [0, N).
+ * Partial Fisher-Yates over a virtual identity array; step i swaps positions
+ * i and i + hi64(r_i (N - i)), r_i = word 0 of Philox4x64-10 with counter
+ * (i, 0, 0, 0) and key (seed, tag). Tags: 0 rows, 1 columns.
+ * d_drawn (k, draw order) and d_sorted (k, ascending) are device int32.
+ * 0 <= k <= min(N, 4096), N < 2^31. */
+cabs_status cabs_draw_indices(cabs_ctx* ctx, uint64_t seed, int32_t tag, int64_t N, int32_t k,
+                              int32_t* d_drawn, int32_t* d_sorted, cabs_stream stream);
+
+/* Steps a2 / a7, Algorithm 2 steps 1 and 3: C = A[:, cols] (m x k_c, ld k_c),
+ * Rt = A[rows, :]^T (n x k_r, ld k_r), W = A[rows, cols] (k_r x k_c, FP64).
+ * C and Rt are elem of `prec`. Any of C, Rt, W may be NULL to skip it (W
+ * needs C). Dense entries are copied exactly; RBF entries are generated in
+ * elem. W equals C[rows, :] and Rt[cols, :]^T bit for bit. Indices are
+ * expected in [0, m) and [0, n); the kernels clamp any that are not, so a bad
+ * index never reads outside A, X or Y. */
+cabs_status cabs_gather(cabs_ctx* ctx, const cabs_source* src, int64_t m, int64_t n,
+                        const int32_t* d_rows, int32_t k_r, const int32_t* d_cols, int32_t k_c,
+                        int32_t prec, void* C, void* Rt, double* W, cabs_stream stream);
+
+/* Steps a3 / a4 / a8, Section 4.1 (sketching routine) and Algorithm 2 step 2.
+ * FP64 one-sided Jacobi SVD W = U_w Sigma_w V_w^T (k x k, k = k_r = k_c),
+ * truncation to sigma_i > max(trunc_rtol, k 2^-52) sigma_1, extrapolation
+ * a = C V_w (m x k), b = Rt U_w (n x k), column norms N_c, N_r, scale S
+ * (per cabs_core), then
+ *   embed == 0: out1 = U = a N_c^-1, out2 = V = b N_r^-1       (factors)
+ *   embed != 0: out1 = P = U S^1/2,  out2 = Q = V S^1/2        (embeddings)
+ * out1 (m x k) and out2 (n x k) are elem, ld k; S (k, FP64); columns and S
+ * entries beyond the kept rank are zero. d_rank (device int32, may be NULL)
+ * receives the kept rank; d_sweeps (may be NULL) the Jacobi sweep count;
+ * d_sig / d_Uw / d_Vw (may be NULL) receive Sigma_w (k, descending) and
+ * U_w, V_w (k x k, row-major). ws: cabs_sketching_workspace_size() bytes. */
+cabs_status cabs_sketching_workspace_size(int64_t m, int64_t n, int32_t k, int32_t prec, size_t* bytes);
+cabs_status cabs_sketching(cabs_ctx* ctx, int64_t m, int64_t n, int32_t k, int32_t prec, int32_t core,
+                      double trunc_rtol, const void* C, const void* Rt, const double* W,
+                      int32_t embed, void* out1, double* S, void* out2, int32_t* d_rank,
+                      int32_t* d_sweeps, double* d_sig, double* d_Uw, double* d_Vw, void* ws,
+                      size_t ws_bytes, cabs_stream stream);
+
+/* Step a5, Section 3.2 Eq. wkmeans and Algorithm 2 step 3: `iters` Lloyd
+ * iterations on the M points X (M x d, elem, ld d) with weights
+ * w_l = |X_l|^upsilon_pow (0^0 = 1), from centres X[init_rows[0..k2)].
+ * Assign: lowest-index argmin of squared distance; update: weighted mean of
+ * the members, an empty cluster keeps its centre.
+ * d_labels: iters x M int32 (every iteration's assignment) or NULL;
+ * d_centres: k2 x d elem, receives the final centres (after `iters` updates);
+ * d_energy: iters doubles (weighted encoding error of each assignment) or NULL;
+ * d_T: max cluster size of the last assignment (int32) or NULL.
+ * FP64 mode computes distances by direct differences; FP32 by the expansion
+ * |z|^2 - 2 x.z on CUDA cores; TF32/BF16 on tensor cores with an FP32
+ * re-check of near ties. ws: cabs_kmeans_workspace_size() bytes. */
+cabs_status cabs_kmeans_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t iters, int32_t prec,
+                                       size_t* bytes);
+cabs_status cabs_kmeans(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const int32_t* d_init_rows,
+                        int32_t k2, int32_t iters, int32_t prec, float upsilon_pow, int32_t* d_labels,
+                        void* d_centres, double* d_energy, int32_t* d_T, void* ws, size_t ws_bytes,
+                        cabs_stream stream);
+
+/* Step a6, Section 3.2 (each centre replaced by its closest in-sample point):
+ * centres Z (k2 x d, elem) taken in index order, each picks the nearest row
+ * of X (M x d, elem) not yet picked, ties to the lowest row index; distances
+ * by direct differences in elem. d_order (k2, pick order) and d_sorted (k2,
+ * ascending) are device int32. ws: cabs_snap_workspace_size() bytes. */
+cabs_status cabs_snap_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t prec, size_t* bytes);
+cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const void* Z, int32_t k2,
+                      int32_t prec, int32_t* d_order, int32_t* d_sorted, void* ws, size_t ws_bytes,
+                      cabs_stream stream);
+
+/* ------------------------------------------------------------- serving */
+
+/* Continuous-batching request loop on one device. The caller hands over an
+ * HBM arena (device memory, `arena_bytes`, owned by the caller and not
+ * touched by it until cabs_serve_stop returns); each request's workspace and
+ * its resident results are carved from the arena. A request is admitted when
+ * a slot is free and its footprint fits in the unused arena; requests on the
+ * device run concurrently on up to `max_slots` streams. */
+cabs_status cabs_serve_start(cabs_ctx* ctx, void* arena, size_t arena_bytes, int32_t max_slots);
+/* Queues one request (copies *src and *p). The request's result buffers are
+ * resident in the arena until cabs_serve_release. Thread-safe. */
+cabs_status cabs_serve_submit(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
+                              uint64_t* ticket);
+/* Waits up to timeout_ms (0 = poll) for a request. On CABS_OK, *res points
+ * into the arena (device pointers valid until release) and *latency_ms holds
+ * submit-to-completion time. CABS_EBUSY: not finished yet. */
+cabs_status cabs_serve_poll(cabs_ctx* ctx, uint64_t ticket, cabs_result* res, double* latency_ms,
+                            int32_t timeout_ms);
+/* Frees a finished request's resident results. */
+cabs_status cabs_serve_release(cabs_ctx* ctx, uint64_t ticket);
+/* Stops admitting, waits for requests on the device, joins the loop. */
+cabs_status cabs_serve_stop(cabs_ctx* ctx);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CABS_H */

@@ -1,0 +1,59 @@
+// Internal declarations shared by the ABI layer (api.cu) and the serving loop
+// (serve.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cabs {
+
+// Selects a device for the lifetime of the guard and restores the previous one.
+struct DeviceGuard {
+  int prev = 0;
+  int target = 0;
+  bool ok = false;
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+};
+
+// Slices of one sketch's workspace (see carve_sketch).
+struct SketchWs {
+  int *pr_drawn, *pc_drawn, *fr_order, *fc_order;
+  void *C, *Rt, *P, *Q, *Zr, *Zc;
+  double *W, *S_pilot;
+  cabs_diag* diag;
+  void *core, *side_r, *side_c;
+  size_t core_bytes, side_r_bytes, side_c_bytes;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct ServeState;
+
+SketchWs carve_sketch(Carve& cv, const cabs_params& p);
+size_t sketch_ws_bytes(const cabs_params& p);
+cabs_status validate_source(const cabs_source* src, int64_t m, int64_t n);
+cabs_status validate_params(const cabs_params* p);
+cabs_status validate_result(const cabs_result* out);
+cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
+                           const cabs_result& out);
+
+}  // namespace cabs
+
+// The opaque context of the ABI.
+struct cabs_ctx {
+  int device = 0;
+  std::mutex graph_mu;
+  std::unordered_map<uint64_t, cabs::GraphEntry> graphs;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> lane_events;
+  cudaEvent_t fork_event = nullptr;
+  cabs::ServeState* serve = nullptr;
+};

@@ -1,0 +1,360 @@
+// Steps a3 / a4 / a8 -- the sketching routine of Section 4.1 and the pilot
+// embedding of Algorithm 2, step 2.
+//
+//  1. FP64 SVD W = U_w Sigma_w V_w^T (one-sided Jacobi, Hestenes form): the
+//     columns of W are rotated pairwise until mutually orthogonal; the
+//     accumulated rotations give V_w, the column norms Sigma_w, the normalised
+//     columns U_w. Pairs follow the round-robin (circle) schedule so the k/2
+//     pairs of a round are independent and run on different warps. The sweep
+//     stops when no pair has |w_p . w_q| > 1e-15 |w_p| |w_q|.
+//  2. Truncation: keep sigma_i > max(trunc_rtol, k 2^-52) sigma_1; dropped
+//     components get zero columns in U_w and V_w, hence zero factors and S.
+//  3. Extrapolation a = C V_w (m x k), b = Rt U_w (n x k) on CUDA cores, in
+//     the working precision; each CTA also writes the FP64 sum of squares of
+//     its tile's columns, and the norms N_c, N_r are summed in a fixed order
+//     (deterministic).
+//  4. Scale: S_i = N_c,i N_r,i / sigma_i (pseudo-skeleton C W^+ R, Eq. W) or
+//     S_i = sigma_i sqrt(mn)/k (stabilised form); the factors are
+//     U = a N_c^-1, V = b N_r^-1, or the embeddings P = U S^1/2, Q = V S^1/2.
+//
+// FP64 throughput on this part is 1/64 of FP32, so the SVD dominates for
+// large k; it is written for correctness first (one CTA per matrix).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cabs {
+namespace {
+
+constexpr int kSvdThreads = 1024;
+constexpr int kMaxSweeps = 40;
+constexpr double kJacobiTol = 1e-15;
+constexpr size_t kSvdSmemLimit = 200 * 1024;
+
+__device__ __forceinline__ void pair_of(int round, int pr, int kk, int& p, int& q) {
+  if (pr == 0) {
+    p = round;
+    q = kk - 1;
+  } else {
+    p = (round + pr) % (kk - 1);
+    q = (round - pr + kk - 1) % (kk - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// One CTA. W (k x k, row-major). Wc/Vc: column-major scratch (shared memory
+// when use_smem, else the given global buffers). Outputs: sig (k, descending),
+// Uw, Vw (k x k row-major, column r = r-th singular vector, zero beyond rank).
+__global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double* __restrict__ W, int k,
+                                                                  double trunc_rtol, int use_smem,
+                                                                  double* Wc_g, double* Vc_g,
+                                                                  double* __restrict__ sig_out,
+                                                                  double* __restrict__ Uw_out,
+                                                                  double* __restrict__ Vw_out, int* rank_out,
+                                                                  int* sweeps_out, int* status) {
+  extern __shared__ __align__(16) double svd_smem[];
+  __shared__ double sig[CABS_MAX_K];
+  __shared__ int pos[CABS_MAX_K];
+  __shared__ int rotated;
+  __shared__ int rank_s;
+  double* Wc = use_smem ? svd_smem : Wc_g;
+  double* Vc = use_smem ? svd_smem + (size_t)k * k : Vc_g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int kk2 = k * k;
+  for (int e = tid; e < kk2; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Wc[(size_t)j * k + i] = W[e];
+    Vc[e] = (i == j) ? 1.0 : 0.0;
+  }
+  if (tid == 0) rotated = 0;
+  __syncthreads();
+
+  const int kk = k + (k & 1);
+  const int npairs = kk / 2;
+  int sweep = 0;
+  bool converged = (k < 2);
+  while (!converged && sweep < kMaxSweeps) {
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        int p, q;
+        pair_of(round, pr, kk, p, q);
+        if (q >= k) continue;
+        double* wp = Wc + (size_t)p * k;
+        double* wq = Wc + (size_t)q * k;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wp[i], y = wq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > kJacobiTol * sqrt(a) * sqrt(b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = 1.0 / sqrt(fma(t, t, 1.0));
+          const double s = c * t;
+          double* vp = Vc + (size_t)p * k;
+          double* vq = Vc + (size_t)q * k;
+          for (int i = lane; i < k; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = c * x - s * y;
+            wq[i] = s * x + c * y;
+            const double u = vp[i], v = vq[i];
+            vp[i] = c * u - s * v;
+            vq[i] = s * u + c * v;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    const int any = rotated;
+    __syncthreads();
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    converged = (any == 0);
+  }
+
+  // singular values = column norms, then a rank sort (descending, stable)
+  for (int j = warp; j < k; j += nwarps) {
+    const double* wj = Wc + (size_t)j * k;
+    double a = 0.0;
+    for (int i = lane; i < k; i += 32) a = fma(wj[i], wj[i], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[j] = sqrt(a);
+  }
+  __syncthreads();
+  for (int j = tid; j < k; j += blockDim.x) {
+    const double sj = sig[j];
+    int r = 0;
+    for (int i = 0; i < k; ++i) r += (sig[i] > sj) || (sig[i] == sj && i < j);
+    pos[j] = r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double smax = 0.0;
+    for (int j = 0; j < k; ++j) smax = fmax(smax, sig[j]);
+    int r = 0;
+    if (smax > 0.0) {
+      const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
+      for (int j = 0; j < k; ++j) r += sig[j] > tol;
+    }
+    rank_s = r;
+    if (rank_out) *rank_out = r;
+    if (sweeps_out) *sweeps_out = sweep;
+    if (status && !converged) atomicOr(status, 1);
+  }
+  __syncthreads();
+  const int rank = rank_s;
+  for (int j = tid; j < k; j += blockDim.x) sig_out[pos[j]] = sig[j];
+  for (int e = tid; e < kk2; e += blockDim.x) {
+    const int j = e / k, i = e - j * k;  // column j, row i (column-major walk)
+    const int r = pos[j];
+    const bool keep = r < rank;
+    Vw_out[(size_t)i * k + r] = keep ? Vc[e] : 0.0;
+    Uw_out[(size_t)i * k + r] = keep ? Wc[e] / sig[j] : 0.0;
+  }
+}
+
+// out[M x N] = X[M x K] * B[K x N] with X in T and B in FP64 (converted to T);
+// N = K = k. Also the FP64 sum of squares of each output column over this
+// CTA's rows: part[blockIdx.y * N + col].
+constexpr int kGBM = 64, kGBN = 64, kGBK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ X, long long M, int K,
+                                                         const double* __restrict__ B, int N, T* __restrict__ out,
+                                                         double* __restrict__ part) {
+  __shared__ __align__(16) T As[kGBK][kGBM + 4];
+  __shared__ __align__(16) T Bs[kGBK][kGBN + 4];
+  __shared__ double colsq[16][kGBN];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const long long m0 = (long long)blockIdx.y * kGBM;
+  const int n0 = blockIdx.x * kGBN;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += kGBK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = tid + 256 * e;       // 0..1023
+      const int r = idx >> 4, c = idx & 15;  // X tile: 64 rows x 16 k
+      const long long gm = m0 + r;
+      const int gk = k0 + c;
+      As[c][r] = (gm < M && gk < K) ? X[gm * K + gk] : T(0);
+      const int br = idx >> 6, bc = idx & 63;  // B tile: 16 k x 64 cols
+      const int bk = k0 + br, bn = n0 + bc;
+      Bs[br][bc] = (bk < K && bn < N) ? (T)B[(size_t)bk * N + bn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGBK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double sq[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn < N) {
+        out[gm * N + gn] = acc[i][j];
+        const double v = (double)acc[i][j];
+        sq[j] = fma(v, v, sq[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) colsq[ty][tx * 4 + j] = sq[j];
+  __syncthreads();
+  if (tid < kGBN) {
+    double s = 0.0;
+    for (int r = 0; r < 16; ++r) s += colsq[r][tid];
+    const int gn = n0 + tid;
+    if (gn < N) part[(size_t)blockIdx.y * N + gn] = s;
+  }
+}
+
+// One CTA of k threads: column norms, S and the per-column scale factors.
+__global__ void core_finalize_kernel(const double* __restrict__ part1, int nb1, const double* __restrict__ part2,
+                                     int nb2, int k, const double* __restrict__ sig, const int* __restrict__ rank_p,
+                                     int core, int embed, double mn_over_kk, double* __restrict__ S,
+                                     double* __restrict__ f1, double* __restrict__ f2) {
+  const int r = threadIdx.x;
+  if (r >= k) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < nb1; ++b) s1 += part1[(size_t)b * k + r];
+  for (int b = 0; b < nb2; ++b) s2 += part2[(size_t)b * k + r];
+  const double nc = sqrt(s1), nr = sqrt(s2);
+  const int rank = *rank_p;
+  double sv = 0.0, a = 0.0, c = 0.0;
+  if (r < rank && nc > 0.0 && nr > 0.0) {
+    sv = (core == CABS_CORE_STABILIZED) ? sig[r] * sqrt(mn_over_kk) : nc * nr / sig[r];
+    const double e = embed ? sqrt(sv) : 1.0;
+    a = e / nc;
+    c = e / nr;
+  }
+  S[r] = sv;
+  f1[r] = a;
+  f2[r] = c;
+}
+
+template <typename T>
+__global__ void scale_cols_kernel(T* __restrict__ X, long long M, int k, const double* __restrict__ f) {
+  __shared__ T fs[CABS_MAX_K];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) fs[r] = (T)f[r];
+  __syncthreads();
+  const long long total = M * k;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % k);
+    X[e] *= fs[r];
+  }
+}
+
+struct CoreWs {
+  double *Wc, *Vc, *sig, *Uw, *Vw, *part1, *part2, *f1, *f2;
+  int *rank, *sweeps;
+};
+
+CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
+  CoreWs w;
+  w.Wc = cv.take<double>((size_t)k * k);
+  w.Vc = cv.take<double>((size_t)k * k);
+  w.sig = cv.take<double>(k);
+  w.Uw = cv.take<double>((size_t)k * k);
+  w.Vw = cv.take<double>((size_t)k * k);
+  w.part1 = cv.take<double>((size_t)ceil_div(m, kGBM) * k);
+  w.part2 = cv.take<double>((size_t)ceil_div(n, kGBM) * k);
+  w.f1 = cv.take<double>(k);
+  w.f2 = cv.take<double>(k);
+  w.rank = cv.take<int>(1);
+  w.sweeps = cv.take<int>(1);
+  return w;
+}
+
+template <typename T>
+cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol, const T* C, const T* Rt,
+                       const double* W, bool embed, T* out1, double* S, T* out2, int* d_rank, int* d_sweeps,
+                       int* d_status, double* d_sig, double* d_Uw, double* d_Vw, void* ws, size_t ws_bytes,
+                       cudaStream_t stream) {
+  Carve cv(ws, ws_bytes);
+  CoreWs w = carve_core(cv, m, n, k);
+  if (!cv.fits()) {
+    set_error("core workspace too small: need %zu bytes, got %zu", cv.used, ws_bytes);
+    return CABS_ENOMEM;
+  }
+  double* sig = d_sig ? d_sig : w.sig;
+  double* Uw = d_Uw ? d_Uw : w.Uw;
+  double* Vw = d_Vw ? d_Vw : w.Vw;
+  int* rank = d_rank ? d_rank : w.rank;
+  int* sweeps = d_sweeps ? d_sweeps : w.sweeps;
+  const size_t smem_need = (size_t)2 * k * k * sizeof(double);
+  const int use_smem = smem_need <= kSvdSmemLimit;
+  const size_t smem = use_smem ? smem_need : 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  svd_jacobi_kernel<<<1, kSvdThreads, smem, stream>>>(W, k, trunc_rtol, use_smem, w.Wc, w.Vc, sig, Uw, Vw, rank,
+                                                      sweeps, d_status);
+  CABS_LAUNCHED("svd_jacobi_kernel");
+  const int nb1 = ceil_div(m, kGBM), nb2 = ceil_div(n, kGBM);
+  dim3 g1(ceil_div(k, kGBN), nb1), g2(ceil_div(k, kGBN), nb2);
+  extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1);
+  CABS_LAUNCHED("extrap_gemm_kernel(C V_w)");
+  extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2);
+  CABS_LAUNCHED("extrap_gemm_kernel(Rt U_w)");
+  const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);
+  core_finalize_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
+                                                     mn_over_kk, S, w.f1, w.f2);
+  CABS_LAUNCHED("core_finalize_kernel");
+  const int sms = sm_count();
+  scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(m * k, 256), sms * 8)), 256, 0, stream>>>(out1, m, k, w.f1);
+  CABS_LAUNCHED("scale_cols_kernel(1)");
+  scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(n * k, 256), sms * 8)), 256, 0, stream>>>(out2, n, k, w.f2);
+  CABS_LAUNCHED("scale_cols_kernel(2)");
+  return CABS_OK;
+}
+
+}  // namespace
+
+size_t core_ws_bytes(int64_t m, int64_t n, int k, bool /*elem_f64*/) {
+  Carve cv;
+  carve_core(cv, m, n, k);
+  return cv.used;
+}
+
+cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
+                        const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
+                        int* d_rank, int* d_sweeps, int* d_status, double* d_sig, double* d_Uw, double* d_Vw,
+                        void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (elem_f64)
+    return core_typed<double>(m, n, k, core, trunc_rtol, (const double*)C, (const double*)Rt, W, embed,
+                              (double*)out1, S, (double*)out2, d_rank, d_sweeps, d_status, d_sig, d_Uw, d_Vw, ws,
+                              ws_bytes, stream);
+  return core_typed<float>(m, n, k, core, trunc_rtol, (const float*)C, (const float*)Rt, W, embed, (float*)out1, S,
+                           (float*)out2, d_rank, d_sweeps, d_status, d_sig, d_Uw, d_Vw, ws, ws_bytes, stream);
+}
+
+}  // namespace cabs

@@ -1,0 +1,45 @@
+// Host-side launchers of the hot-path kernels (internal, not part of the ABI).
+// Every launcher validates nothing beyond what its kernel needs, enqueues on
+// `stream`, and returns CABS_ECUDA if the launch failed.
+#pragma once
+
+#include "common.cuh"
+
+namespace cabs {
+
+// a1: two independent draws (rows and columns) in one launch; pass k1 = 0 for one.
+cabs_status launch_draw2(uint64_t seed, int tag0, long long N0, int k0, int* drawn0, int* sorted0, int tag1,
+                         long long N1, int k1, int* drawn1, int* sorted1, cudaStream_t stream);
+
+// a2/a7: gathers. `elem_f64` selects the output element type of C and Rt.
+cabs_status launch_gather(const cabs_source& src, int64_t m, int64_t n, const int* rows, int kr, const int* cols,
+                          int kc, bool elem_f64, void* C, void* Rt, double* W, cudaStream_t stream);
+
+// a3/a4/a8: the sketching routine. Workspace bytes for (m, n, k, elem).
+size_t core_ws_bytes(int64_t m, int64_t n, int k, bool elem_f64);
+cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
+                        const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
+                        int* d_rank, int* d_sweeps, int* d_status, double* d_sig, double* d_Uw, double* d_Vw,
+                        void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// a5: weighted k-means.
+size_t kmeans_ws_bytes(int64_t M, int d, int k2, int iters, int prec);
+cabs_status launch_kmeans(const void* X, int64_t M, int d, const int* init_rows, int k2, int iters, int prec,
+                          float upsilon_pow, int* labels, void* centres, double* energy, int* d_T, int* d_recheck,
+                          void* ws, size_t ws_bytes, cudaStream_t stream);
+// Weighted encoding error of X with representatives X[reps] (k2 rows), nearest assignment.
+cabs_status launch_encoding_error(const void* X, int64_t M, int d, const int* reps, int k2, int prec,
+                                  float upsilon_pow, double* out, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// a6: snap.
+size_t snap_ws_bytes(int64_t M, int d, int k2, int prec);
+cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
+                        void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// a9: relative Frobenius error.
+size_t error_ws_bytes(int64_t m, int64_t n, int64_t samples, bool elem_f64);
+cabs_status launch_error(const cabs_source& src, int64_t m, int64_t n, int k, bool elem_f64, int prec,
+                         const void* U, const double* S, const void* V, int64_t samples, uint64_t seed, void* ws,
+                         size_t ws_bytes, double* d_out2 /* num, den */, cudaStream_t stream);
+
+}  // namespace cabs

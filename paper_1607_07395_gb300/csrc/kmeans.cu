@@ -1,0 +1,502 @@
+// Step a5 -- weighted k-means sampling on the pilot embeddings (Section 3.2,
+// Eq. wkmeans; Algorithm 2, step 3).
+//
+// Objective: sum_l w_l |x_l - z_s(l)|^2 with w_l = Upsilon(|x_l|) = |x_l|^p.
+// Each iteration assigns every point to its nearest centre (ties to the lower
+// centre index) and moves each centre to the weighted mean of its members;
+// a centre with no weight keeps its position. Centres start at the points
+// given by init_rows (the pilot rows, in draw order).
+//
+// Assignment kernels
+//   FP64: direct differences sum_q (x_q - z_q)^2, summed in dimension order.
+//   FP32: expansion |z|^2 - 2 x.z (|x|^2 is common to a row), a register-tiled
+//         CUDA-core contraction: a CTA holds 64 points x all (<= 256)
+//         centres, each thread 8 x 8 accumulators; the row argmin is a
+//         warp-shuffle reduction over the 32 lanes that share a point row.
+//   TF32/BF16: tensor-core contraction (separate kernel file), with near ties
+//         re-checked in FP32.
+// Update kernel: one CTA per centre; each warp scans a fixed slice of the
+// labels and sums its members in index order; the 8 warp sums are added in
+// a fixed order, so the centres do not depend on scheduling.
+// Energies (weighted encoding errors) are per-CTA FP64 partials summed in a
+// fixed order.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_assign.cuh"
+
+namespace cabs {
+namespace {
+
+// -------------------------------------------------------------- helpers
+
+template <typename T>
+__global__ void point_prep_kernel(const T* __restrict__ X, long long M, int d, float p, T* __restrict__ xn,
+                                  T* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long l = warp; l < M; l += nwarps) {
+    T s = T(0);
+    for (int q = lane; q < d; q += 32) s = fma(X[l * d + q], X[l * d + q], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      xn[l] = s;
+      w[l] = (p == 0.0f) ? T(1) : (T)pow((double)dev_sqrt<T>(s), (double)p);
+    }
+  }
+}
+
+template <typename T>
+__global__ void init_centres_kernel(const T* __restrict__ X, long long M, int d, const int* __restrict__ rows,
+                                    int k2, T* __restrict__ Z) {
+  const int j = blockIdx.x;
+  if (j >= k2) return;
+  const long long l = min(max((long long)rows[j], 0ll), M - 1);
+  for (int q = threadIdx.x; q < d; q += blockDim.x) Z[(size_t)j * d + q] = X[l * d + q];
+}
+
+template <typename T>
+__global__ void centre_norms_kernel(const T* __restrict__ Z, int k2, int d, T* __restrict__ zn) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= k2) return;
+  T s = T(0);
+  for (int q = lane; q < d; q += 32) s = fma(Z[(size_t)j * d + q], Z[(size_t)j * d + q], s);
+  s = warp_sum(s);
+  if (lane == 0) zn[j] = s;
+}
+
+// ------------------------------------------------------ FP32 assignment
+
+constexpr int kAM = 64;   // points per CTA tile
+constexpr int kAK = 16;   // dimensions per stage
+constexpr int kAN = 256;  // centres per CTA (all of them)
+
+__global__ void __launch_bounds__(256) assign_f32_kernel(const float* __restrict__ X, long long M, int d,
+                                                         const float* __restrict__ Z, const float* __restrict__ zn,
+                                                         int k2, const float* __restrict__ xn,
+                                                         const float* __restrict__ w, int* __restrict__ labels,
+                                                         double* __restrict__ part_e) {
+  __shared__ __align__(16) float xs[kAK][kAM + 4];
+  __shared__ __align__(16) float zs[kAK][kAN + 4];
+  __shared__ double esum[8];
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  double e_local = 0.0;
+  const long long m0 = (long long)blockIdx.x * kAM;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[i][c] = 0.f;
+  for (int q0 = 0; q0 < d; q0 += kAK) {
+    {
+      const int p = tid >> 2, qq = (tid & 3) * 4;
+      const long long l = m0 + p;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int q = q0 + qq + e;
+        xs[qq + e][p] = (l < M && q < d) ? X[l * d + q] : 0.f;
+      }
+      const int j = tid;
+#pragma unroll
+      for (int e = 0; e < kAK; ++e) {
+        const int q = q0 + e;
+        zs[e][j] = (j < k2 && q < d) ? Z[(size_t)j * d + q] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kAK; ++kk) {
+      float a[8], b[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = xs[kk][ty * 8 + i];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) b[c] = zs[kk][tx + 32 * c];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
+    }
+    __syncthreads();
+  }
+  float znr[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = tx + 32 * c;
+    znr[c] = j < k2 ? zn[j] : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long l = m0 + ty * 8 + i;
+    float best = pos_inf<float>();
+    int bj = 0x7fffffff;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = tx + 32 * c;
+      const float dist = fmaf(-2.f, acc[i][c], znr[c]);
+      if (j < k2 && dist < best) {
+        best = dist;
+        bj = j;
+      }
+    }
+    warp_argmin(best, bj);
+    if (tx == 0 && l < M) {
+      labels[l] = bj;
+      e_local += (double)w[l] * fmax(0.0, (double)best + (double)xn[l]);
+    }
+  }
+  if (tx == 0) esum[ty] = e_local;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += esum[i];
+    part_e[blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------ FP64 assignment
+
+constexpr int kDM = 32;  // points per CTA
+constexpr int kDG = 8;   // centres per stage (one per thread group lane)
+
+__global__ void __launch_bounds__(256) assign_f64_kernel(const double* __restrict__ X, long long M, int d,
+                                                         const double* __restrict__ Z, int k2,
+                                                         const double* __restrict__ w, int* __restrict__ labels,
+                                                         double* __restrict__ part_e) {
+  extern __shared__ __align__(16) double dsm[];
+  const int ld = d + 1;
+  double* xs = dsm;             // kDM x ld
+  double* zs = dsm + kDM * ld;  // kDG x ld
+  __shared__ double esum[8];
+  const int tid = threadIdx.x, pl = tid >> 3, g = tid & 7;
+  const long long m0 = (long long)blockIdx.x * kDM;
+  for (int e = tid; e < kDM * d; e += blockDim.x) {
+    const int p = e / d, q = e - p * d;
+    const long long l = m0 + p;
+    xs[p * ld + q] = l < M ? X[l * d + q] : 0.0;
+  }
+  double best = pos_inf<double>();
+  int bj = 0x7fffffff;
+  for (int c0 = 0; c0 < k2; c0 += kDG) {
+    __syncthreads();
+    for (int e = tid; e < kDG * d; e += blockDim.x) {
+      const int jj = e / d, q = e - jj * d;
+      const int j = c0 + jj;
+      zs[jj * ld + q] = j < k2 ? Z[(size_t)j * d + q] : 0.0;
+    }
+    __syncthreads();
+    const int j = c0 + g;
+    if (j < k2) {
+      double s = 0.0;
+      const double* xr = xs + pl * ld;
+      const double* zr = zs + g * ld;
+      for (int q = 0; q < d; ++q) {
+        const double t = xr[q] - zr[q];
+        s = fma(t, t, s);
+      }
+      if (s < best) {
+        best = s;
+        bj = j;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bj, off);
+    if (lex_less(ov, oi, best, bj)) {
+      best = ov;
+      bj = oi;
+    }
+  }
+  const long long l = m0 + pl;
+  double e = 0.0;
+  if (g == 0 && l < M) {
+    labels[l] = bj;
+    e = w[l] * best;
+  }
+  e = warp_sum(e);
+  if ((tid & 31) == 0) esum[tid >> 5] = e;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) s += esum[i];
+    part_e[blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------- update
+
+constexpr int kUWarps = 8;
+constexpr int kUMaxPerLane = CABS_MAX_K / 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) update_kernel(const T* __restrict__ X, long long M, int d,
+                                                     const int* __restrict__ labels, const T* __restrict__ w,
+                                                     const T* __restrict__ Zcur, T* __restrict__ Znext,
+                                                     int* __restrict__ counts) {
+  __shared__ T accs[kUWarps][CABS_MAX_K];
+  __shared__ T wsums[kUWarps];
+  __shared__ int cnts[kUWarps];
+  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const long long lo = M * wi / kUWarps, hi = M * (wi + 1) / kUWarps;
+  T acc[kUMaxPerLane];
+#pragma unroll
+  for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = T(0);
+  T wsum = T(0);
+  int cnt = 0;
+  for (long long base = lo; base < hi; base += 32) {
+    const long long l = base + lane;
+    const int lab = l < hi ? labels[l] : -1;
+    unsigned mask = __ballot_sync(0xffffffffu, lab == j);
+    while (mask) {
+      long long ls[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (mask) {
+          const int b = __ffs(mask) - 1;
+          mask &= mask - 1;
+          ls[u] = base + b;
+        } else {
+          ls[u] = -1;
+        }
+      }
+      T xv[4][kUMaxPerLane];
+      T wv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        wv[u] = ls[u] >= 0 ? w[ls[u]] : T(0);
+#pragma unroll
+        for (int s = 0; s < kUMaxPerLane; ++s) {
+          const int q = lane + 32 * s;
+          xv[u][s] = (ls[u] >= 0 && q < d) ? X[ls[u] * d + q] : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ls[u] >= 0) {
+#pragma unroll
+          for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = fma(wv[u], xv[u][s], acc[s]);
+          wsum += wv[u];
+          ++cnt;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kUMaxPerLane; ++s) {
+    const int q = lane + 32 * s;
+    if (q < CABS_MAX_K) accs[wi][q] = acc[s];
+  }
+  if (lane == 0) {
+    wsums[wi] = wsum;
+    cnts[wi] = cnt;
+  }
+  __syncthreads();
+  T W = T(0);
+  int C = 0;
+  for (int i = 0; i < kUWarps; ++i) {
+    W += wsums[i];
+    C += cnts[i];
+  }
+  for (int q = threadIdx.x; q < d; q += blockDim.x) {
+    T s = T(0);
+    for (int i = 0; i < kUWarps; ++i) s += accs[i][q];
+    Znext[(size_t)j * d + q] = W > T(0) ? s / W : Zcur[(size_t)j * d + q];
+  }
+  if (threadIdx.x == 0 && counts) counts[j] = C;
+}
+
+__global__ void max_count_kernel(const int* __restrict__ counts, int k2, int* __restrict__ out) {
+  __shared__ int mx[256];
+  int m = 0;
+  for (int j = threadIdx.x; j < k2; j += blockDim.x) m = max(m, counts[j]);
+  mx[threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) r = max(r, mx[i]);
+    *out = r;
+  }
+}
+
+__global__ void energy_reduce_kernel(const double* __restrict__ part, int nb, int iters, double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= iters) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(size_t)t * nb + b];
+  out[t] = s;
+}
+
+template <typename T>
+__global__ void copy_kernel(const T* __restrict__ a, T* __restrict__ b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// ---------------------------------------------------------- workspace
+
+struct KmWs {
+  void *xn, *w, *Za, *Zb, *zn;
+  int *labels, *counts, *T;
+  double *part_e, *energy;
+};
+
+int assign_blocks(int64_t M, int prec) {
+  if (prec == CABS_PREC_FP64) return ceil_div(M, kDM);
+  if (prec == CABS_PREC_FP32) return ceil_div(M, kAM);
+  return tc_assign_blocks(M);
+}
+
+KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
+  const size_t eb = elem_bytes(prec);
+  KmWs w;
+  w.xn = cv.take<char>(M * eb);
+  w.w = cv.take<char>(M * eb);
+  w.Za = cv.take<char>((size_t)k2 * d * eb);
+  w.Zb = cv.take<char>((size_t)k2 * d * eb);
+  w.zn = cv.take<char>((size_t)k2 * eb);
+  w.labels = cv.take<int>(M);
+  w.counts = cv.take<int>(k2);
+  w.T = cv.take<int>(1);
+  w.part_e = cv.take<double>((size_t)std::max(iters, 1) * assign_blocks(M, prec));
+  w.energy = cv.take<double>(std::max(iters, 1));
+  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) tc_assign_carve(cv, M, d, k2);
+  return w;
+}
+
+template <typename T>
+cabs_status assign_once(const T* X, int64_t M, int d, const T* Z, int k2, int prec, const T* xn, const T* w, T* zn,
+                        int* labels, double* part_e, int* d_recheck, void* tcws, cudaStream_t stream);
+
+template <>
+cabs_status assign_once<double>(const double* X, int64_t M, int d, const double* Z, int k2, int prec,
+                                const double* xn, const double* w, double* zn, int* labels, double* part_e,
+                                int* d_recheck, void* tcws, cudaStream_t stream) {
+  const int nb = ceil_div(M, kDM);
+  const size_t smem = (size_t)(kDM + kDG) * (d + 1) * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(assign_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  assign_f64_kernel<<<nb, 256, smem, stream>>>(X, M, d, Z, k2, w, labels, part_e);
+  return check_cuda("assign_f64_kernel");
+}
+
+template <>
+cabs_status assign_once<float>(const float* X, int64_t M, int d, const float* Z, int k2, int prec, const float* xn,
+                               const float* w, float* zn, int* labels, double* part_e, int* d_recheck, void* tcws,
+                               cudaStream_t stream) {
+  centre_norms_kernel<float><<<ceil_div(k2, 8), 256, 0, stream>>>(Z, k2, d, zn);
+  CABS_LAUNCHED("centre_norms_kernel");
+  if (prec == CABS_PREC_FP32) {
+    assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, xn, w, labels, part_e);
+    return check_cuda("assign_f32_kernel");
+  }
+  return tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prec == CABS_PREC_BF16, tcws,
+                          stream);
+}
+
+template <typename T>
+cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int k2, int iters, int prec, float p,
+                         int* labels_out, T* centres, double* energy, int* d_T, int* d_recheck, void* ws,
+                         size_t ws_bytes, cudaStream_t stream) {
+  Carve cv(ws, ws_bytes);
+  KmWs w = carve_km(cv, M, d, k2, iters, prec);
+  void* tcws = nullptr;
+  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
+    Carve c2(ws, ws_bytes);
+    carve_km(c2, M, d, k2, iters, CABS_PREC_FP32);  // same prefix
+    tcws = c2.base + c2.used;
+  }
+  if (!cv.fits()) {
+    set_error("k-means workspace too small: need %zu bytes, got %zu", cv.used, ws_bytes);
+    return CABS_ENOMEM;
+  }
+  const int sms = sm_count();
+  T* xn = (T*)w.xn;
+  T* wt = (T*)w.w;
+  point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, xn, wt);
+  CABS_LAUNCHED("point_prep_kernel");
+  T* Zc = (T*)w.Za;
+  T* Zn = (T*)w.Zb;
+  init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, init_rows, k2, Zc);
+  CABS_LAUNCHED("init_centres_kernel");
+  const int nb = assign_blocks(M, prec);
+  for (int t = 0; t < iters; ++t) {
+    int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
+    CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, w.part_e + (size_t)t * nb, d_recheck,
+                            tcws, stream));
+    update_kernel<T><<<k2, 256, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts);
+    CABS_LAUNCHED("update_kernel");
+    T* tmp = Zc;
+    Zc = Zn;
+    Zn = tmp;
+  }
+  if (iters > 0) {
+    if (energy) {
+      energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, iters, energy);
+      CABS_LAUNCHED("energy_reduce_kernel");
+    }
+    if (d_T) {
+      max_count_kernel<<<1, 256, 0, stream>>>(w.counts, k2, d_T);
+      CABS_LAUNCHED("max_count_kernel");
+    }
+  }
+  copy_kernel<T><<<std::max(1, ceil_div((int64_t)k2 * d, 256)), 256, 0, stream>>>(Zc, centres, (long long)k2 * d);
+  return check_cuda("copy_kernel");
+}
+
+template <typename T>
+cabs_status enc_err_typed(const T* X, int64_t M, int d, const int* reps, int k2, int prec, float p, double* out,
+                          void* ws, size_t ws_bytes, cudaStream_t stream) {
+  Carve cv(ws, ws_bytes);
+  KmWs w = carve_km(cv, M, d, k2, 1, prec);
+  void* tcws = nullptr;
+  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
+    Carve c2(ws, ws_bytes);
+    carve_km(c2, M, d, k2, 1, CABS_PREC_FP32);
+    tcws = c2.base + c2.used;
+  }
+  if (!cv.fits()) {
+    set_error("encoding-error workspace too small");
+    return CABS_ENOMEM;
+  }
+  const int sms = sm_count();
+  point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, (T*)w.xn,
+                                                                                           (T*)w.w);
+  CABS_LAUNCHED("point_prep_kernel");
+  init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, reps, k2, (T*)w.Za);
+  CABS_LAUNCHED("init_centres_kernel");
+  const int nb = assign_blocks(M, prec);
+  CABS_TRY(assign_once<T>(X, M, d, (T*)w.Za, k2, prec, (T*)w.xn, (T*)w.w, (T*)w.zn, w.labels, w.part_e, nullptr,
+                          tcws, stream));
+  energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, 1, out);
+  return check_cuda("energy_reduce_kernel");
+}
+
+}  // namespace
+
+size_t kmeans_ws_bytes(int64_t M, int d, int k2, int iters, int prec) {
+  Carve cv;
+  carve_km(cv, M, d, k2, iters, prec);
+  return cv.used;
+}
+
+cabs_status launch_kmeans(const void* X, int64_t M, int d, const int* init_rows, int k2, int iters, int prec,
+                          float upsilon_pow, int* labels, void* centres, double* energy, int* d_T, int* d_recheck,
+                          void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (prec == CABS_PREC_FP64)
+    return kmeans_typed<double>((const double*)X, M, d, init_rows, k2, iters, prec, upsilon_pow, labels,
+                                (double*)centres, energy, d_T, d_recheck, ws, ws_bytes, stream);
+  return kmeans_typed<float>((const float*)X, M, d, init_rows, k2, iters, prec, upsilon_pow, labels, (float*)centres,
+                             energy, d_T, d_recheck, ws, ws_bytes, stream);
+}
+
+cabs_status launch_encoding_error(const void* X, int64_t M, int d, const int* reps, int k2, int prec,
+                                  float upsilon_pow, double* out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (prec == CABS_PREC_FP64)
+    return enc_err_typed<double>((const double*)X, M, d, reps, k2, prec, upsilon_pow, out, ws, ws_bytes, stream);
+  return enc_err_typed<float>((const float*)X, M, d, reps, k2, prec, upsilon_pow, out, ws, ws_bytes, stream);
+}
+
+}  // namespace cabs

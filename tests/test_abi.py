@@ -1,0 +1,114 @@
+"""The C-ABI library loads and exports what include/cabs.h declares; the
+ctypes structures match the C layout; argument validation works on the host
+(no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1607_07395_gb300 import cabs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cabs.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(cabs.LIB_PATH):
+        from paper_1607_07395_gb300 import build
+        build.build()
+    return cabs.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cabs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    for nm in names:
+        assert hasattr(L, nm), nm
+    assert sorted(cabs.exported_names()) == names
+    out = subprocess.run(["nm", "-D", "--defined-only", cabs.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln and ln.split()[-1].startswith("cabs_")}
+    assert exported == set(names)
+
+
+def test_struct_layout_matches_c():
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "cabs.h"
+#define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("cabs_source %zu\ncabs_params %zu\ncabs_diag %zu\ncabs_result %zu\n", sizeof(cabs_source),
+         sizeof(cabs_params), sizeof(cabs_diag), sizeof(cabs_result));
+  F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma)
+  F(cabs_params, seed) F(cabs_params, upsilon_pow) F(cabs_params, trunc_rtol) F(cabs_params, flags)
+  F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_result, diag)
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        lines = dict(ln.rsplit(" ", 1) for ln in subprocess.run([exe], capture_output=True, text=True,
+                                                                check=True).stdout.split("\n") if ln)
+    for name, cls in [("cabs_source", cabs.cabs_source), ("cabs_params", cabs.cabs_params),
+                      ("cabs_diag", cabs.cabs_diag), ("cabs_result", cabs.cabs_result)]:
+        assert int(lines[name]) == C.sizeof(cls), name
+    for key, val in lines.items():
+        if "." in key:
+            t, f = key.split(".")
+            assert getattr(getattr(cabs, t), f).offset == int(val), key
+
+
+def _src():
+    return cabs.cabs_source(kind=cabs.SRC_DENSE, A=0x1000, lda=1500, a_is_f64=1)
+
+
+def test_workspace_size_and_validation_on_host(L):
+    p = cabs.make_params(2000, 1500, 20)
+    n = C.c_size_t()
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(p), C.byref(n)) == cabs.CABS_OK
+    assert n.value > (2000 + 1500) * 20 * 8 * 2
+    small = n.value
+    p2 = cabs.make_params(2000, 1500, 20, prec="fp32")
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(p2), C.byref(n)) == cabs.CABS_OK
+    assert n.value < small
+    bad = [cabs.make_params(2000, 1500, 1501), cabs.make_params(2000, 1500, 20, k2=21),
+           cabs.make_params(2000, 1500, 257), cabs.make_params(2000, 1500, 20, iters=65),
+           cabs.make_params(0, 1500, 1), cabs.make_params(2000, 1500, 20, prec=7)]
+    for b in bad:
+        assert L.cabs_workspace_size(C.byref(_src()), C.byref(b), C.byref(n)) == cabs.CABS_EINVAL
+        assert L.cabs_last_error(None)
+    s = _src()
+    s.lda = 1499
+    assert L.cabs_workspace_size(C.byref(s), C.byref(p), C.byref(n)) == cabs.CABS_EINVAL
+    r = cabs.cabs_source(kind=cabs.SRC_RBF, X=0x1000, Y=0x2000, d=65, sigma=1.0)
+    assert L.cabs_workspace_size(C.byref(r), C.byref(p), C.byref(n)) == cabs.CABS_EINVAL
+    r.d, r.sigma = 16, 0.0
+    assert L.cabs_workspace_size(C.byref(r), C.byref(p), C.byref(n)) == cabs.CABS_EINVAL
+
+
+def test_null_arguments_rejected(L):
+    p = cabs.make_params(100, 90, 10)
+    assert L.cabs_workspace_size(None, C.byref(p), None) == cabs.CABS_EINVAL
+    assert L.cabs_sketch(None, C.byref(_src()), C.byref(p), None, 0, None, None) == cabs.CABS_EINVAL
+    assert L.cabs_draw_indices(None, 1, 0, 10, 3, None, None, None) == cabs.CABS_EINVAL
+    assert L.cabs_create(None, 0) == cabs.CABS_EINVAL
+
+
+def test_no_cpu_fallback_without_gpu(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert L.cabs_create(C.byref(h), 0) == cabs.CABS_ECUDA
