@@ -257,6 +257,21 @@ cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const 
                       int32_t prec, int32_t* d_order, int32_t* d_sorted, void* ws, size_t ws_bytes,
                       cabs_stream stream);
 
+/* ----------------------------------------------------------- profiling */
+
+/* Per-kernel device timing: while enabled, CUDA events are recorded on the
+ * launching stream around every kernel launch that libcabs issues in this
+ * process (not inside a CUDA graph capture). Off by default; process-wide. */
+cabs_status cabs_profile_enable(cabs_ctx* ctx, int32_t on);
+/* Waits for the timed launches, then writes up to `max` rows, one per kernel
+ * name: names (max rows of name_len chars, NUL-terminated), launch counts and
+ * summed device milliseconds. Returns the number of rows written; reset != 0
+ * clears the accumulated totals. */
+int32_t cabs_profile_read(cabs_ctx* ctx, char* names, int32_t name_len, int64_t* launches, double* total_ms,
+                          int32_t max, int32_t reset);
+/* Number of kernel launches libcabs has issued in this process. */
+int64_t cabs_launch_count(void);
+
 /* ------------------------------------------------------------- serving */
 
 /* Continuous-batching request loop on one device. The caller hands over an

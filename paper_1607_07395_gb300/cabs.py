@@ -95,6 +95,9 @@ def lib():
         "cabs_serve_poll": ([vp, u64, P(cabs_result), P(f64), i32], i32),
         "cabs_serve_release": ([vp, u64], i32),
         "cabs_serve_stop": ([vp], i32),
+        "cabs_profile_enable": ([vp, i32], i32),
+        "cabs_profile_read": ([vp, C.c_char_p, i32, P(i64), P(f64), i32, i32], i32),
+        "cabs_launch_count": ([], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -109,7 +112,8 @@ def exported_names():
             "cabs_sketch_batched", "cabs_error_workspace_size", "cabs_error", "cabs_draw_indices", "cabs_gather",
             "cabs_sketching_workspace_size", "cabs_sketching", "cabs_kmeans_workspace_size", "cabs_kmeans",
             "cabs_snap_workspace_size", "cabs_snap", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
-            "cabs_serve_release", "cabs_serve_stop"]
+            "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
+            "cabs_launch_count"]
 
 
 def _check(status, ctx=None):
@@ -384,6 +388,30 @@ def cabs_snap(ctx: Context, X, Z, prec="fp64", stream=None):
     _check(lib().cabs_snap(ctx.h, _ptr(X), M, d, _ptr(Z), k2, p, _ptr(order), _ptr(srt), wp, wn, _stream(stream)),
            ctx.h)
     return order, srt
+
+
+# -------------------------------------------------------------- profiling
+
+def cabs_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().cabs_profile_enable(ctx.h, int(on)), ctx.h)
+
+
+def cabs_profile_read(ctx: Context, reset: bool = True, max_rows: int = 128):
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    name_len = 64
+    names = C.create_string_buffer(max_rows * name_len)
+    launches = (C.c_int64 * max_rows)()
+    ms = (C.c_double * max_rows)()
+    n = lib().cabs_profile_read(ctx.h, names, name_len, launches, ms, max_rows, int(reset))
+    out = {}
+    for i in range(n):
+        nm = names.raw[i * name_len:(i + 1) * name_len].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def cabs_launch_count() -> int:
+    return int(lib().cabs_launch_count())
 
 
 # ---------------------------------------------------------------- serving

@@ -13,6 +13,7 @@
 #include "api_internal.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 
@@ -153,8 +154,7 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   const int64_t m = p.m, n = p.n;
   const int k1 = p.k1, k2 = p.k2;
   cabs_diag* dg = out.diag ? out.diag : w.diag;
-  diag_clear_kernel<<<1, 256, 0, s>>>(dg);
-  CABS_LAUNCHED("diag_clear_kernel");
+  CABS_LAUNCH(s, "diag_clear_kernel", diag_clear_kernel<<<1, 256, 0, s>>>(dg));
   // Algorithm 2, step 1: pilot sampling
   CABS_TRY(launch_draw2(p.seed, 0, m, k1, w.pr_drawn, out.pilot_rows, 1, n, k1, w.pc_drawn, out.pilot_cols, s));
   CABS_TRY(launch_gather(src, m, n, out.pilot_rows, k1, out.pilot_cols, k1, f64, w.C, w.Rt, w.W, s));

@@ -21,6 +21,7 @@
 // large k; it is written for correctness first (one CTA per matrix).
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 namespace {
@@ -316,24 +317,18 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   const size_t smem = use_smem ? smem_need : 0;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  svd_jacobi_kernel<<<1, kSvdThreads, smem, stream>>>(W, k, trunc_rtol, use_smem, w.Wc, w.Vc, sig, Uw, Vw, rank,
-                                                      sweeps, d_status);
-  CABS_LAUNCHED("svd_jacobi_kernel");
+  CABS_LAUNCH(stream, "svd_jacobi_kernel", svd_jacobi_kernel<<<1, kSvdThreads, smem, stream>>>(W, k, trunc_rtol, use_smem, w.Wc, w.Vc, sig, Uw, Vw, rank,
+                                                      sweeps, d_status));
   const int nb1 = ceil_div(m, kGBM), nb2 = ceil_div(n, kGBM);
   dim3 g1(ceil_div(k, kGBN), nb1), g2(ceil_div(k, kGBN), nb2);
-  extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1);
-  CABS_LAUNCHED("extrap_gemm_kernel(C V_w)");
-  extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2);
-  CABS_LAUNCHED("extrap_gemm_kernel(Rt U_w)");
+  CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));
+  CABS_LAUNCH(stream, "extrap_gemm_kernel(Rt U_w)", extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2));
   const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);
-  core_finalize_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
-                                                     mn_over_kk, S, w.f1, w.f2);
-  CABS_LAUNCHED("core_finalize_kernel");
+  CABS_LAUNCH(stream, "core_finalize_kernel", core_finalize_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
+                                                     mn_over_kk, S, w.f1, w.f2));
   const int sms = sm_count();
-  scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(m * k, 256), sms * 8)), 256, 0, stream>>>(out1, m, k, w.f1);
-  CABS_LAUNCHED("scale_cols_kernel(1)");
-  scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(n * k, 256), sms * 8)), 256, 0, stream>>>(out2, n, k, w.f2);
-  CABS_LAUNCHED("scale_cols_kernel(2)");
+  CABS_LAUNCH(stream, "scale_cols_kernel(1)", scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(m * k, 256), sms * 8)), 256, 0, stream>>>(out1, m, k, w.f1));
+  CABS_LAUNCH(stream, "scale_cols_kernel(2)", scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(n * k, 256), sms * 8)), 256, 0, stream>>>(out2, n, k, w.f2));
   return CABS_OK;
 }
 

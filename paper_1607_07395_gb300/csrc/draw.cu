@@ -13,6 +13,7 @@
 // all threads.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 namespace {
@@ -120,8 +121,8 @@ cabs_status launch_draw2(uint64_t seed, int tag0, long long N0, int k0, int* dra
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
-  draw_kernel<<<jobs, kDrawThreads, smem, stream>>>(a, b);
-  return check_cuda("draw_kernel");
+  CABS_LAUNCH(stream, "draw_kernel", draw_kernel<<<jobs, kDrawThreads, smem, stream>>>(a, b));
+  return CABS_OK;
 }
 
 }  // namespace cabs

@@ -17,6 +17,7 @@
 // Rt[J_t, p] == C[I_p, t] bit for bit.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 namespace {
@@ -161,25 +162,21 @@ cabs_status gather_typed(const cabs_source& src, int64_t m, int64_t n, const int
   if (src.kind == CABS_SRC_DENSE) {
     if (C && kc > 0) {
       const int blocks = std::max(1, std::min(ceil_div(m, (kGatherThreads / 32) * kRowsPerWarp), sms * 8));
-      if (src.a_is_f64)
-        gather_cols_kernel<double, Tout><<<blocks, kGatherThreads, 0, stream>>>((const double*)src.A, src.lda, m,
-                                                                                 n, cols, kc, C);
-      else
-        gather_cols_kernel<float, Tout><<<blocks, kGatherThreads, 0, stream>>>((const float*)src.A, src.lda, m,
-                                                                                n, cols, kc, C);
-      CABS_LAUNCHED("gather_cols_kernel");
+      CABS_LAUNCH(stream, "gather_cols_kernel",
+                  if (src.a_is_f64) gather_cols_kernel<double, Tout><<<blocks, kGatherThreads, 0, stream>>>(
+                      (const double*)src.A, src.lda, m, n, cols, kc, C);
+                  else gather_cols_kernel<float, Tout><<<blocks, kGatherThreads, 0, stream>>>(
+                      (const float*)src.A, src.lda, m, n, cols, kc, C));
     }
     if (Rt && kr > 0) {
       const int py = ceil_div(kr, kTileP);
       const int px = std::max(1, std::min(ceil_div(n, kTileJ), std::max(1, sms * 8 / py)));
       dim3 grid(px, py);
-      if (src.a_is_f64)
-        gather_rows_t_kernel<double, Tout><<<grid, kGatherThreads, 0, stream>>>((const double*)src.A, src.lda, m,
-                                                                                 n, rows, kr, Rt);
-      else
-        gather_rows_t_kernel<float, Tout><<<grid, kGatherThreads, 0, stream>>>((const float*)src.A, src.lda, m,
-                                                                                n, rows, kr, Rt);
-      CABS_LAUNCHED("gather_rows_t_kernel");
+      CABS_LAUNCH(stream, "gather_rows_t_kernel",
+                  if (src.a_is_f64) gather_rows_t_kernel<double, Tout><<<grid, kGatherThreads, 0, stream>>>(
+                      (const double*)src.A, src.lda, m, n, rows, kr, Rt);
+                  else gather_rows_t_kernel<float, Tout><<<grid, kGatherThreads, 0, stream>>>(
+                      (const float*)src.A, src.lda, m, n, rows, kr, Rt));
     }
   } else {
     const double inv2s2 = 1.0 / (2.0 * (double)src.sigma * (double)src.sigma);
@@ -188,19 +185,16 @@ cabs_status gather_typed(const cabs_source& src, int64_t m, int64_t n, const int
       cudaFuncSetAttribute(rbf_block_kernel<Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (C && kc > 0) {
       const int blocks = std::max(1, std::min(ceil_div(m, kGatherThreads / 32), sms * 8));
-      rbf_block_kernel<Tout><<<blocks, kGatherThreads, smem, stream>>>(src.X, m, src.Y, n, cols, kc, src.d, inv2s2, C);
-      CABS_LAUNCHED("rbf_block_kernel(C)");
+      CABS_LAUNCH(stream, "rbf_block_kernel(C)", rbf_block_kernel<Tout><<<blocks, kGatherThreads, smem, stream>>>(src.X, m, src.Y, n, cols, kc, src.d, inv2s2, C));
     }
     if (Rt && kr > 0) {
       const int blocks = std::max(1, std::min(ceil_div(n, kGatherThreads / 32), sms * 8));
-      rbf_block_kernel<Tout><<<blocks, kGatherThreads, smem, stream>>>(src.Y, n, src.X, m, rows, kr, src.d, inv2s2, Rt);
-      CABS_LAUNCHED("rbf_block_kernel(Rt)");
+      CABS_LAUNCH(stream, "rbf_block_kernel(Rt)", rbf_block_kernel<Tout><<<blocks, kGatherThreads, smem, stream>>>(src.Y, n, src.X, m, rows, kr, src.d, inv2s2, Rt));
     }
   }
   if (W && C && kr > 0 && kc > 0) {
     const int total = kr * kc;
-    w_from_c_kernel<Tout><<<ceil_div(total, 256), 256, 0, stream>>>(C, m, kc, rows, kr, W);
-    CABS_LAUNCHED("w_from_c_kernel");
+    CABS_LAUNCH(stream, "w_from_c_kernel", w_from_c_kernel<Tout><<<ceil_div(total, 256), 256, 0, stream>>>(C, m, kc, rows, kr, W));
   }
   return CABS_OK;
 }

@@ -22,6 +22,7 @@
 // fixed order.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 #include "tc_assign.cuh"
 
 namespace cabs {
@@ -378,19 +379,18 @@ cabs_status assign_once<double>(const double* X, int64_t M, int d, const double*
   const size_t smem = (size_t)(kDM + kDG) * (d + 1) * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(assign_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  assign_f64_kernel<<<nb, 256, smem, stream>>>(X, M, d, Z, k2, w, labels, part_e);
-  return check_cuda("assign_f64_kernel");
+  CABS_LAUNCH(stream, "assign_f64_kernel", assign_f64_kernel<<<nb, 256, smem, stream>>>(X, M, d, Z, k2, w, labels, part_e));
+  return CABS_OK;
 }
 
 template <>
 cabs_status assign_once<float>(const float* X, int64_t M, int d, const float* Z, int k2, int prec, const float* xn,
                                const float* w, float* zn, int* labels, double* part_e, int* d_recheck, void* tcws,
                                cudaStream_t stream) {
-  centre_norms_kernel<float><<<ceil_div(k2, 8), 256, 0, stream>>>(Z, k2, d, zn);
-  CABS_LAUNCHED("centre_norms_kernel");
+  CABS_LAUNCH(stream, "centre_norms_kernel", centre_norms_kernel<float><<<ceil_div(k2, 8), 256, 0, stream>>>(Z, k2, d, zn));
   if (prec == CABS_PREC_FP32) {
-    assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, xn, w, labels, part_e);
-    return check_cuda("assign_f32_kernel");
+    CABS_LAUNCH(stream, "assign_f32_kernel", assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, xn, w, labels, part_e));
+    return CABS_OK;
   }
   return tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prec == CABS_PREC_BF16, tcws,
                           stream);
@@ -415,35 +415,30 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
   const int sms = sm_count();
   T* xn = (T*)w.xn;
   T* wt = (T*)w.w;
-  point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, xn, wt);
-  CABS_LAUNCHED("point_prep_kernel");
+  CABS_LAUNCH(stream, "point_prep_kernel", point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, xn, wt));
   T* Zc = (T*)w.Za;
   T* Zn = (T*)w.Zb;
-  init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, init_rows, k2, Zc);
-  CABS_LAUNCHED("init_centres_kernel");
+  CABS_LAUNCH(stream, "init_centres_kernel", init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, init_rows, k2, Zc));
   const int nb = assign_blocks(M, prec);
   for (int t = 0; t < iters; ++t) {
     int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
     CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, w.part_e + (size_t)t * nb, d_recheck,
                             tcws, stream));
-    update_kernel<T><<<k2, 256, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts);
-    CABS_LAUNCHED("update_kernel");
+    CABS_LAUNCH(stream, "update_kernel", update_kernel<T><<<k2, 256, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts));
     T* tmp = Zc;
     Zc = Zn;
     Zn = tmp;
   }
   if (iters > 0) {
     if (energy) {
-      energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, iters, energy);
-      CABS_LAUNCHED("energy_reduce_kernel");
+      CABS_LAUNCH(stream, "energy_reduce_kernel", energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, iters, energy));
     }
     if (d_T) {
-      max_count_kernel<<<1, 256, 0, stream>>>(w.counts, k2, d_T);
-      CABS_LAUNCHED("max_count_kernel");
+      CABS_LAUNCH(stream, "max_count_kernel", max_count_kernel<<<1, 256, 0, stream>>>(w.counts, k2, d_T));
     }
   }
-  copy_kernel<T><<<std::max(1, ceil_div((int64_t)k2 * d, 256)), 256, 0, stream>>>(Zc, centres, (long long)k2 * d);
-  return check_cuda("copy_kernel");
+  CABS_LAUNCH(stream, "copy_kernel", copy_kernel<T><<<std::max(1, ceil_div((int64_t)k2 * d, 256)), 256, 0, stream>>>(Zc, centres, (long long)k2 * d));
+  return CABS_OK;
 }
 
 template <typename T>
@@ -462,16 +457,14 @@ cabs_status enc_err_typed(const T* X, int64_t M, int d, const int* reps, int k2,
     return CABS_ENOMEM;
   }
   const int sms = sm_count();
-  point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, (T*)w.xn,
-                                                                                           (T*)w.w);
-  CABS_LAUNCHED("point_prep_kernel");
-  init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, reps, k2, (T*)w.Za);
-  CABS_LAUNCHED("init_centres_kernel");
+  CABS_LAUNCH(stream, "point_prep_kernel", point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, (T*)w.xn,
+                                                                                           (T*)w.w));
+  CABS_LAUNCH(stream, "init_centres_kernel", init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, reps, k2, (T*)w.Za));
   const int nb = assign_blocks(M, prec);
   CABS_TRY(assign_once<T>(X, M, d, (T*)w.Za, k2, prec, (T*)w.xn, (T*)w.w, (T*)w.zn, w.labels, w.part_e, nullptr,
                           tcws, stream));
-  energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, 1, out);
-  return check_cuda("energy_reduce_kernel");
+  CABS_LAUNCH(stream, "energy_reduce_kernel", energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, 1, out));
+  return CABS_OK;
 }
 
 }  // namespace

@@ -11,6 +11,7 @@
 // Per-CTA partial sums are added in a fixed order (deterministic).
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 namespace {
@@ -184,15 +185,13 @@ cabs_status error_typed(const cabs_source& src, int64_t m, int64_t n, int k, con
   }
   double* part = (double*)ws;
   if (samples > 0) {
-    residual_sampled_kernel<T><<<(int)nb, 256, 0, stream>>>(src, m, n, k, U, S, V, samples, seed, part);
-    CABS_LAUNCHED("residual_sampled_kernel");
+    CABS_LAUNCH(stream, "residual_sampled_kernel", residual_sampled_kernel<T><<<(int)nb, 256, 0, stream>>>(src, m, n, k, U, S, V, samples, seed, part));
   } else {
     dim3 grid(ceil_div(n, kRT), ceil_div(m, kRT));
-    residual_dense_kernel<T><<<grid, 256, 0, stream>>>(U, S, V, k, src.A, src.a_is_f64, src.lda, m, n, part);
-    CABS_LAUNCHED("residual_dense_kernel");
+    CABS_LAUNCH(stream, "residual_dense_kernel", residual_dense_kernel<T><<<grid, 256, 0, stream>>>(U, S, V, k, src.A, src.a_is_f64, src.lda, m, n, part));
   }
-  pair_reduce_kernel<<<1, 256, 0, stream>>>(part, nb, out2);
-  return check_cuda("pair_reduce_kernel");
+  CABS_LAUNCH(stream, "pair_reduce_kernel", pair_reduce_kernel<<<1, 256, 0, stream>>>(part, nb, out2));
+  return CABS_OK;
 }
 
 }  // namespace

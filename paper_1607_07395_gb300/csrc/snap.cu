@@ -18,6 +18,7 @@
 //     centre. The picks are then sorted ascending.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "profile.cuh"
 
 namespace cabs {
 namespace {
@@ -293,18 +294,16 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* or
   const size_t dtile = (size_t)kSM * (kSN + 1) * sizeof(T);
   const size_t smem = std::max(stage, dtile);
   cudaFuncSetAttribute(snap_cand_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r);
-  CABS_LAUNCHED("snap_cand_kernel");
-  snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r);
-  CABS_LAUNCHED("snap_merge_kernel");
+  CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
+  CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
   const size_t bm_bytes = (size_t)((M + 31) / 32) * 4;
   const int use_smem = bm_bytes <= kBitmapSmemLimit;
   const size_t gsm = use_smem ? bm_bytes : 0;
   if (gsm > 48 * 1024)
     cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-  snap_greedy_kernel<T><<<1, kGreedyThreads, gsm, stream>>>(X, M, d, Z, k2, w.top_r, use_smem, w.bitmap, order,
-                                                            sorted);
-  return check_cuda("snap_greedy_kernel");
+  CABS_LAUNCH(stream, "snap_greedy_kernel", snap_greedy_kernel<T><<<1, kGreedyThreads, gsm, stream>>>(X, M, d, Z, k2, w.top_r, use_smem, w.bitmap, order,
+                                                            sorted));
+  return CABS_OK;
 }
 
 }  // namespace
