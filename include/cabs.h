@@ -187,6 +187,24 @@ cabs_status cabs_error(cabs_ctx* ctx, const cabs_source* src, const cabs_params*
                        const cabs_result* res, int64_t samples, uint64_t seed, void* ws,
                        size_t ws_bytes, cabs_stream stream, double* rel_fro);
 
+/* The same error as cabs_error, for callers that cannot allocate device
+ * memory when they need it: code running inside another framework's memory
+ * pool that forbids cudaMalloc/cudaFree during a step, or programs that
+ * reserve all device memory up front and have no workspace to hand out. It
+ * takes no workspace and calls no allocating routine. The paper has no
+ * counterpart; this is a service of the library. Its scratch is one fixed
+ * file-scope device array (about 256 KiB on every device that loads libcabs,
+ * held until the process exits). Limits: the exact error (samples == 0,
+ * dense source) takes m <= 1,048,576 rows and returns CABS_EINVAL beyond; the
+ * sampled error takes any sample count. The first call on a device looks up
+ * the array's address with that device current: make it before any CUDA
+ * stream capture starts. Every call shares the array and leaves its contents
+ * behind; calls whose kernels overlap on the GPU (other streams or threads)
+ * race on it and may return wrong values. Synchronises `stream`. */
+cabs_status cabs_error_noalloc(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
+                               const cabs_result* res, int64_t samples, uint64_t seed, cabs_stream stream,
+                               double* rel_fro);
+
 /* ------------------------------------------------ hot-path steps, one by one */
 
 /* Step a1, Algorithm 2 step 1: k distinct uniform indices from [0, N).

@@ -98,6 +98,7 @@ def lib():
         "cabs_profile_enable": ([vp, i32], i32),
         "cabs_profile_read": ([vp, C.c_char_p, i32, P(i64), P(f64), i32, i32], i32),
         "cabs_launch_count": ([], i64),
+        "cabs_error_noalloc": ([vp, P(cabs_source), P(cabs_params), P(cabs_result), i64, u64, vp, P(f64)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -113,7 +114,7 @@ def exported_names():
             "cabs_sketching_workspace_size", "cabs_sketching", "cabs_kmeans_workspace_size", "cabs_kmeans",
             "cabs_snap_workspace_size", "cabs_snap", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
-            "cabs_launch_count"]
+            "cabs_launch_count", "cabs_error_noalloc"]
 
 
 def _check(status, ctx=None):
@@ -301,6 +302,16 @@ def cabs_error(ctx: Context, src: Source, p: cabs_params, sk: Sketch, samples=0,
     out = C.c_double()
     _check(lib().cabs_error(ctx.h, C.byref(src.c), C.byref(p), C.byref(sk.result), samples, seed, wp, wn,
                             _stream(stream), C.byref(out)), ctx.h)
+    return out.value
+
+
+def cabs_error_noalloc(ctx: Context, src: Source, p: cabs_params, sk: Sketch, samples=0, seed=1607,
+                       stream=None) -> float:
+    """cabs_error for callers that cannot allocate device memory: no workspace,
+    scratch in a fixed device array inside libcabs (exact error: m <= 1,048,576)."""
+    out = C.c_double()
+    _check(lib().cabs_error_noalloc(ctx.h, C.byref(src.c), C.byref(p), C.byref(sk.result), samples, seed,
+                                    _stream(stream), C.byref(out)), ctx.h)
     return out.value
 
 
