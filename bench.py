@@ -392,7 +392,9 @@ def run_cabs(args):
                latency_ms=dict(p50=round(statistics.median(per_step), 4),
                                p99=round(sorted(per_step)[min(len(per_step) - 1,
                                                               int(math.ceil(0.99 * len(per_step))) - 1)], 4)),
-               rel_fro_error=errs[-1], gpu_launches=int(launches), roofline=roof, kernels=table, gather=gather,
+               rel_fro_error=errs[-1], gpu_launches=int(launches),
+               diag=dict(svd_sweeps=sweeps, svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
+                         snap_fallbacks=int(diag.snap_fallbacks)), roofline=roof, kernels=table, gather=gather,
                e2e=e2e, clocks=clocks)
     if not args.no_cpu:
         res["cpu_baseline"] = run_cpu_baseline(args.workload, args.cpu_steps)

@@ -117,11 +117,15 @@ typedef struct {
   int32_t rank_pilot, rank_final;         /* kept singular values of W and W_bar */
   int32_t sweeps_pilot, sweeps_final;     /* Jacobi sweeps of the FP64 SVDs */
   int32_t T_rows, T_cols;                 /* max cluster size (Eq. T) of the last assignment */
-  int32_t status;                         /* bit 0: an SVD hit the sweep limit */
+  int32_t status;                         /* bit 0: the FP64 Jacobi hit its sweep limit; bit 1: the
+                                           * FP64 refinement did not converge and the FP64 Jacobi ran;
+                                           * bit 2: a bounded device-side wait gave up */
   int32_t rechecked;                      /* reduced precision: assignments re-checked in FP32 */
   double e_rows[CABS_MAX_ITERS];          /* weighted encoding error per k-means iteration */
   double e_cols[CABS_MAX_ITERS];          /*   (iteration 0 = the pilot representatives) */
   double e_follow_rows, e_follow_cols;    /* with the snapped follow-up representatives */
+  int32_t snap_fallbacks;                 /* centres whose 8 nearest rows were all taken */
+  int32_t reserved;
 } cabs_diag;
 
 /* Where one sketch's outputs go. All device memory, allocated by the caller. */

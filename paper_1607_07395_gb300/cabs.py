@@ -47,7 +47,8 @@ class cabs_diag(C.Structure):
     _fields_ = [("rank_pilot", C.c_int32), ("rank_final", C.c_int32), ("sweeps_pilot", C.c_int32),
                 ("sweeps_final", C.c_int32), ("T_rows", C.c_int32), ("T_cols", C.c_int32), ("status", C.c_int32),
                 ("rechecked", C.c_int32), ("e_rows", C.c_double * MAX_ITERS), ("e_cols", C.c_double * MAX_ITERS),
-                ("e_follow_rows", C.c_double), ("e_follow_cols", C.c_double)]
+                ("e_follow_rows", C.c_double), ("e_follow_cols", C.c_double), ("snap_fallbacks", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class cabs_result(C.Structure):

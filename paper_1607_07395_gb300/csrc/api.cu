@@ -167,8 +167,10 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
                          &dg->T_rows, &dg->rechecked, w.side_r, w.side_r_bytes, s));
   CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
                          &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, s));
-  CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes, s));
-  CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes, s));
+  CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes,
+                       &dg->snap_fallbacks, s));
+  CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
+                       &dg->snap_fallbacks, s));
   if (p.flags & CABS_FLAG_FOLLOW_ERR) {
     CABS_TRY(launch_encoding_error(w.P, m, k1, out.rows, k2, p.prec, p.upsilon_pow, &dg->e_follow_rows, w.side_r,
                                    w.side_r_bytes, s));
@@ -274,7 +276,7 @@ cabs_status cabs_error_workspace_size(const cabs_source* src, const cabs_params*
   CABS_TRY(validate_source(src, p->m, p->n));
   CABS_REQUIRE(samples >= 0, "samples must be >= 0");
   CABS_REQUIRE(samples > 0 || src->kind == CABS_SRC_DENSE, "the exact error needs a dense source");
-  *bytes = error_ws_bytes(p->m, p->n, samples, p->prec == CABS_PREC_FP64) + 256;
+  *bytes = error_ws_bytes(*src, p->m, p->n, p->k2, samples, p->prec) + 256;
   return CABS_OK;
 }
 
@@ -409,7 +411,7 @@ cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const 
   CABS_REQUIRE(X && Z && d_order && d_sorted, "NULL input or output");
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
-  return launch_snap(X, M, d, Z, k2, prec, d_order, d_sorted, ws, ws_bytes, (cudaStream_t)stream);
+  return launch_snap(X, M, d, Z, k2, prec, d_order, d_sorted, ws, ws_bytes, nullptr, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -157,6 +157,13 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Number of SMs of the current device (cached per device).

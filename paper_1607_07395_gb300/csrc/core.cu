@@ -22,148 +22,10 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
+#include "svd.cuh"
 
 namespace cabs {
 namespace {
-
-constexpr int kSvdThreads = 1024;
-constexpr int kMaxSweeps = 40;
-constexpr double kJacobiTol = 1e-15;
-constexpr size_t kSvdSmemLimit = 200 * 1024;
-
-__device__ __forceinline__ void pair_of(int round, int pr, int kk, int& p, int& q) {
-  if (pr == 0) {
-    p = round;
-    q = kk - 1;
-  } else {
-    p = (round + pr) % (kk - 1);
-    q = (round - pr + kk - 1) % (kk - 1);
-  }
-  if (p > q) {
-    const int t = p;
-    p = q;
-    q = t;
-  }
-}
-
-// One CTA. W (k x k, row-major). Wc/Vc: column-major scratch (shared memory
-// when use_smem, else the given global buffers). Outputs: sig (k, descending),
-// Uw, Vw (k x k row-major, column r = r-th singular vector, zero beyond rank).
-__global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double* __restrict__ W, int k,
-                                                                  double trunc_rtol, int use_smem,
-                                                                  double* Wc_g, double* Vc_g,
-                                                                  double* __restrict__ sig_out,
-                                                                  double* __restrict__ Uw_out,
-                                                                  double* __restrict__ Vw_out, int* rank_out,
-                                                                  int* sweeps_out, int* status) {
-  extern __shared__ __align__(16) double svd_smem[];
-  __shared__ double sig[CABS_MAX_K];
-  __shared__ int pos[CABS_MAX_K];
-  __shared__ int rotated;
-  __shared__ int rank_s;
-  double* Wc = use_smem ? svd_smem : Wc_g;
-  double* Vc = use_smem ? svd_smem + (size_t)k * k : Vc_g;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int kk2 = k * k;
-  for (int e = tid; e < kk2; e += blockDim.x) {
-    const int i = e / k, j = e - i * k;
-    Wc[(size_t)j * k + i] = W[e];
-    Vc[e] = (i == j) ? 1.0 : 0.0;
-  }
-  if (tid == 0) rotated = 0;
-  __syncthreads();
-
-  const int kk = k + (k & 1);
-  const int npairs = kk / 2;
-  int sweep = 0;
-  bool converged = (k < 2);
-  while (!converged && sweep < kMaxSweeps) {
-    for (int round = 0; round < kk - 1; ++round) {
-      for (int pr = warp; pr < npairs; pr += nwarps) {
-        int p, q;
-        pair_of(round, pr, kk, p, q);
-        if (q >= k) continue;
-        double* wp = Wc + (size_t)p * k;
-        double* wq = Wc + (size_t)q * k;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < k; i += 32) {
-          const double x = wp[i], y = wq[i];
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          g = fma(x, y, g);
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (fabs(g) > kJacobiTol * sqrt(a) * sqrt(b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
-                                              : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-          const double c = 1.0 / sqrt(fma(t, t, 1.0));
-          const double s = c * t;
-          double* vp = Vc + (size_t)p * k;
-          double* vq = Vc + (size_t)q * k;
-          for (int i = lane; i < k; i += 32) {
-            const double x = wp[i], y = wq[i];
-            wp[i] = c * x - s * y;
-            wq[i] = s * x + c * y;
-            const double u = vp[i], v = vq[i];
-            vp[i] = c * u - s * v;
-            vq[i] = s * u + c * v;
-          }
-          if (lane == 0) rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    ++sweep;
-    const int any = rotated;
-    __syncthreads();
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    converged = (any == 0);
-  }
-
-  // singular values = column norms, then a rank sort (descending, stable)
-  for (int j = warp; j < k; j += nwarps) {
-    const double* wj = Wc + (size_t)j * k;
-    double a = 0.0;
-    for (int i = lane; i < k; i += 32) a = fma(wj[i], wj[i], a);
-    a = warp_sum(a);
-    if (lane == 0) sig[j] = sqrt(a);
-  }
-  __syncthreads();
-  for (int j = tid; j < k; j += blockDim.x) {
-    const double sj = sig[j];
-    int r = 0;
-    for (int i = 0; i < k; ++i) r += (sig[i] > sj) || (sig[i] == sj && i < j);
-    pos[j] = r;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double smax = 0.0;
-    for (int j = 0; j < k; ++j) smax = fmax(smax, sig[j]);
-    int r = 0;
-    if (smax > 0.0) {
-      const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
-      for (int j = 0; j < k; ++j) r += sig[j] > tol;
-    }
-    rank_s = r;
-    if (rank_out) *rank_out = r;
-    if (sweeps_out) *sweeps_out = sweep;
-    if (status && !converged) atomicOr(status, 1);
-  }
-  __syncthreads();
-  const int rank = rank_s;
-  for (int j = tid; j < k; j += blockDim.x) sig_out[pos[j]] = sig[j];
-  for (int e = tid; e < kk2; e += blockDim.x) {
-    const int j = e / k, i = e - j * k;  // column j, row i (column-major walk)
-    const int r = pos[j];
-    const bool keep = r < rank;
-    Vw_out[(size_t)i * k + r] = keep ? Vc[e] : 0.0;
-    Uw_out[(size_t)i * k + r] = keep ? Wc[e] / sig[j] : 0.0;
-  }
-}
 
 // out[M x N] = X[M x K] * B[K x N] with X in T and B in FP64 (converted to T);
 // N = K = k. Also the FP64 sum of squares of each output column over this
@@ -276,14 +138,14 @@ __global__ void scale_cols_kernel(T* __restrict__ X, long long M, int k, const d
 }
 
 struct CoreWs {
-  double *Wc, *Vc, *sig, *Uw, *Vw, *part1, *part2, *f1, *f2;
+  SvdWs svd;
+  double *sig, *Uw, *Vw, *part1, *part2, *f1, *f2;
   int *rank, *sweeps;
 };
 
 CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
   CoreWs w;
-  w.Wc = cv.take<double>((size_t)k * k);
-  w.Vc = cv.take<double>((size_t)k * k);
+  w.svd = carve_svd(cv, k);
   w.sig = cv.take<double>(k);
   w.Uw = cv.take<double>((size_t)k * k);
   w.Vw = cv.take<double>((size_t)k * k);
@@ -312,13 +174,7 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   double* Vw = d_Vw ? d_Vw : w.Vw;
   int* rank = d_rank ? d_rank : w.rank;
   int* sweeps = d_sweeps ? d_sweeps : w.sweeps;
-  const size_t smem_need = (size_t)2 * k * k * sizeof(double);
-  const int use_smem = smem_need <= kSvdSmemLimit;
-  const size_t smem = use_smem ? smem_need : 0;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  CABS_LAUNCH(stream, "svd_jacobi_kernel", svd_jacobi_kernel<<<1, kSvdThreads, smem, stream>>>(W, k, trunc_rtol, use_smem, w.Wc, w.Vc, sig, Uw, Vw, rank,
-                                                      sweeps, d_status));
+  CABS_TRY(launch_svd(W, k, trunc_rtol, sig, Uw, Vw, rank, sweeps, d_status, w.svd, stream));
   const int nb1 = ceil_div(m, kGBM), nb2 = ceil_div(n, kGBM);
   dim3 g1(ceil_div(k, kGBN), nb1), g2(ceil_div(k, kGBN), nb2);
   CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));

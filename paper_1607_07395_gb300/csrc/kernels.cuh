@@ -34,10 +34,14 @@ cabs_status launch_encoding_error(const void* X, int64_t M, int d, const int* re
 // a6: snap.
 size_t snap_ws_bytes(int64_t M, int d, int k2, int prec);
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
-                        void* ws, size_t ws_bytes, cudaStream_t stream);
+                        void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream);
 
 // a9: relative Frobenius error.
-size_t error_ws_bytes(int64_t m, int64_t n, int64_t samples, bool elem_f64);
+size_t error_ws_bytes(const cabs_source& src, int64_t m, int64_t n, int k, int64_t samples, int prec);
+size_t tc_residual_ws_bytes(int64_t m, int64_t n, int k, bool tf32);
+cabs_status launch_tc_residual(const cabs_source& src, int64_t m, int64_t n, int k, bool tf32, const float* U,
+                               const double* S, const float* V, void* ws, size_t ws_bytes, double* out2,
+                               cudaStream_t stream);
 cabs_status launch_error(const cabs_source& src, int64_t m, int64_t n, int k, bool elem_f64, int prec,
                          const void* U, const double* S, const void* V, int64_t samples, uint64_t seed, void* ws,
                          size_t ws_bytes, double* d_out2 /* num, den */, cudaStream_t stream);

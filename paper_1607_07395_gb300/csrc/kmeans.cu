@@ -339,7 +339,7 @@ __global__ void copy_kernel(const T* __restrict__ a, T* __restrict__ b, long lon
 // ---------------------------------------------------------- workspace
 
 struct KmWs {
-  void *xn, *w, *Za, *Zb, *zn;
+  void *xn, *w, *Za, *Zb, *zn, *tc;
   int *labels, *counts, *T;
   double *part_e, *energy;
 };
@@ -363,18 +363,22 @@ KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
   w.T = cv.take<int>(1);
   w.part_e = cv.take<double>((size_t)std::max(iters, 1) * assign_blocks(M, prec));
   w.energy = cv.take<double>(std::max(iters, 1));
-  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) tc_assign_carve(cv, M, d, k2);
+  w.tc = nullptr;
+  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
+    w.tc = cv.base ? cv.base + cv.used : nullptr;
+    tc_assign_carve(cv, M, d, k2);
+  }
   return w;
 }
 
 template <typename T>
 cabs_status assign_once(const T* X, int64_t M, int d, const T* Z, int k2, int prec, const T* xn, const T* w, T* zn,
-                        int* labels, double* part_e, int* d_recheck, void* tcws, cudaStream_t stream);
+                        int* labels, double* part_e, int* d_recheck, bool first, void* tcws, cudaStream_t stream);
 
 template <>
 cabs_status assign_once<double>(const double* X, int64_t M, int d, const double* Z, int k2, int prec,
                                 const double* xn, const double* w, double* zn, int* labels, double* part_e,
-                                int* d_recheck, void* tcws, cudaStream_t stream) {
+                                int* d_recheck, bool first, void* tcws, cudaStream_t stream) {
   const int nb = ceil_div(M, kDM);
   const size_t smem = (size_t)(kDM + kDG) * (d + 1) * sizeof(double);
   if (smem > 48 * 1024)
@@ -385,14 +389,14 @@ cabs_status assign_once<double>(const double* X, int64_t M, int d, const double*
 
 template <>
 cabs_status assign_once<float>(const float* X, int64_t M, int d, const float* Z, int k2, int prec, const float* xn,
-                               const float* w, float* zn, int* labels, double* part_e, int* d_recheck, void* tcws,
-                               cudaStream_t stream) {
+                               const float* w, float* zn, int* labels, double* part_e, int* d_recheck, bool first,
+                               void* tcws, cudaStream_t stream) {
   CABS_LAUNCH(stream, "centre_norms_kernel", centre_norms_kernel<float><<<ceil_div(k2, 8), 256, 0, stream>>>(Z, k2, d, zn));
   if (prec == CABS_PREC_FP32) {
     CABS_LAUNCH(stream, "assign_f32_kernel", assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, xn, w, labels, part_e));
     return CABS_OK;
   }
-  return tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prec == CABS_PREC_BF16, tcws,
+  return tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prec == CABS_PREC_BF16, first, tcws,
                           stream);
 }
 
@@ -402,12 +406,7 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
                          size_t ws_bytes, cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
   KmWs w = carve_km(cv, M, d, k2, iters, prec);
-  void* tcws = nullptr;
-  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
-    Carve c2(ws, ws_bytes);
-    carve_km(c2, M, d, k2, iters, CABS_PREC_FP32);  // same prefix
-    tcws = c2.base + c2.used;
-  }
+  void* tcws = w.tc;
   if (!cv.fits()) {
     set_error("k-means workspace too small: need %zu bytes, got %zu", cv.used, ws_bytes);
     return CABS_ENOMEM;
@@ -423,7 +422,7 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
   for (int t = 0; t < iters; ++t) {
     int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
     CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, w.part_e + (size_t)t * nb, d_recheck,
-                            tcws, stream));
+                            t == 0, tcws, stream));
     CABS_LAUNCH(stream, "update_kernel", update_kernel<T><<<k2, 256, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts));
     T* tmp = Zc;
     Zc = Zn;
@@ -446,12 +445,7 @@ cabs_status enc_err_typed(const T* X, int64_t M, int d, const int* reps, int k2,
                           void* ws, size_t ws_bytes, cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
   KmWs w = carve_km(cv, M, d, k2, 1, prec);
-  void* tcws = nullptr;
-  if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
-    Carve c2(ws, ws_bytes);
-    carve_km(c2, M, d, k2, 1, CABS_PREC_FP32);
-    tcws = c2.base + c2.used;
-  }
+  void* tcws = w.tc;
   if (!cv.fits()) {
     set_error("encoding-error workspace too small");
     return CABS_ENOMEM;
@@ -462,7 +456,7 @@ cabs_status enc_err_typed(const T* X, int64_t M, int d, const int* reps, int k2,
   CABS_LAUNCH(stream, "init_centres_kernel", init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, reps, k2, (T*)w.Za));
   const int nb = assign_blocks(M, prec);
   CABS_TRY(assign_once<T>(X, M, d, (T*)w.Za, k2, prec, (T*)w.xn, (T*)w.w, (T*)w.zn, w.labels, w.part_e, nullptr,
-                          tcws, stream));
+                          true, tcws, stream));
   CABS_LAUNCH(stream, "energy_reduce_kernel", energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, 1, out));
   return CABS_OK;
 }

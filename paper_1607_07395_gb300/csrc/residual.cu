@@ -196,14 +196,23 @@ cabs_status error_typed(const cabs_source& src, int64_t m, int64_t n, int k, con
 
 }  // namespace
 
-size_t error_ws_bytes(int64_t m, int64_t n, int64_t samples, bool /*elem_f64*/) {
+static bool use_tc_residual(const cabs_source& src, int64_t samples, int prec) {
+  return samples == 0 && src.kind == CABS_SRC_DENSE && !src.a_is_f64 &&
+         (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16);
+}
+
+size_t error_ws_bytes(const cabs_source& src, int64_t m, int64_t n, int k, int64_t samples, int prec) {
+  if (use_tc_residual(src, samples, prec)) return tc_residual_ws_bytes(m, n, k, prec == CABS_PREC_TF32);
   const long long nb = samples > 0 ? sampled_blocks(samples) : dense_blocks(m, n);
   return align256((size_t)nb * 16) + 256;
 }
 
-cabs_status launch_error(const cabs_source& src, int64_t m, int64_t n, int k, bool elem_f64, int /*prec*/,
+cabs_status launch_error(const cabs_source& src, int64_t m, int64_t n, int k, bool elem_f64, int prec,
                          const void* U, const double* S, const void* V, int64_t samples, uint64_t seed, void* ws,
                          size_t ws_bytes, double* d_out2, cudaStream_t stream) {
+  if (use_tc_residual(src, samples, prec))
+    return launch_tc_residual(src, m, n, k, prec == CABS_PREC_TF32, (const float*)U, S, (const float*)V, ws, ws_bytes,
+                              d_out2, stream);
   if (elem_f64)
     return error_typed<double>(src, m, n, k, (const double*)U, S, (const double*)V, samples, seed, ws, ws_bytes,
                                d_out2, stream);

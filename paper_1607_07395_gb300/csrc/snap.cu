@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) snap_cand_kernel(const T* __restrict__ X,
     }
     __syncthreads();
     const int kq = min(kSK, d - q0);
+    const int nc = (k2 + 31) >> 5;  // centre columns in use (the rest are padding)
     for (int kk = 0; kk < kq; ++kk) {
       T a[8], b[8];
 #pragma unroll
@@ -77,12 +78,15 @@ __global__ void __launch_bounds__(256) snap_cand_kernel(const T* __restrict__ X,
 #pragma unroll
       for (int c = 0; c < 8; ++c) b[c] = zs[kk * (kSN + 1) + tx + 32 * c];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int c = 0; c < 8; ++c) {
+        if (c < nc) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const T t = a[i] - b[c];
-          acc[i][c] = fma(t, t, acc[i][c]);
+          for (int i = 0; i < 8; ++i) {
+            const T t = a[i] - b[c];
+            acc[i][c] = fma(t, t, acc[i][c]);
+          }
         }
+      }
     }
     __syncthreads();
   }
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(const T* __
                                                                       const T* __restrict__ Z, int k2,
                                                                       const int* __restrict__ top_r, int use_smem,
                                                                       unsigned* bitmap_g, int* __restrict__ order,
-                                                                      int* __restrict__ sorted) {
+                                                                      int* __restrict__ sorted, int* fallbacks) {
   extern __shared__ __align__(16) unsigned bm_smem[];
   __shared__ int picks[CABS_MAX_K];
   __shared__ int fb_j;
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(const T* __
         }
       if (bi >= 0 && bi < M) taken[bi >> 5] |= 1u << (bi & 31);
       picks[j] = bi;
+      if (fallbacks) atomicAdd(fallbacks, 1);
     }
     __syncthreads();
     ++j;
@@ -282,7 +287,7 @@ SnapWs carve_snap(Carve& cv, int64_t M, int k2, size_t eb) {
 
 template <typename T>
 cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* order, int* sorted, void* ws,
-                       size_t ws_bytes, cudaStream_t stream) {
+                       size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
   SnapWs w = carve_snap(cv, M, k2, sizeof(T));
   if (!cv.fits()) {
@@ -302,7 +307,7 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* or
   if (gsm > 48 * 1024)
     cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
   CABS_LAUNCH(stream, "snap_greedy_kernel", snap_greedy_kernel<T><<<1, kGreedyThreads, gsm, stream>>>(X, M, d, Z, k2, w.top_r, use_smem, w.bitmap, order,
-                                                            sorted));
+                                                            sorted, fallbacks));
   return CABS_OK;
 }
 
@@ -315,10 +320,12 @@ size_t snap_ws_bytes(int64_t M, int d, int k2, int prec) {
 }
 
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
-                        void* ws, size_t ws_bytes, cudaStream_t stream) {
+                        void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
   if (prec == CABS_PREC_FP64)
-    return snap_typed<double>((const double*)X, M, d, (const double*)Z, k2, order, sorted, ws, ws_bytes, stream);
-  return snap_typed<float>((const float*)X, M, d, (const float*)Z, k2, order, sorted, ws, ws_bytes, stream);
+    return snap_typed<double>((const double*)X, M, d, (const double*)Z, k2, order, sorted, ws, ws_bytes, fallbacks,
+                              stream);
+  return snap_typed<float>((const float*)X, M, d, (const float*)Z, k2, order, sorted, ws, ws_bytes, fallbacks,
+                           stream);
 }
 
 }  // namespace cabs

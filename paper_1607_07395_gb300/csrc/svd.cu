@@ -1,0 +1,793 @@
+// Step a3 -- the SVD W = U_w Sigma_w V_w^T of the k x k intersection matrix
+// (Section 4.1), computed to FP64 accuracy.
+//
+// FP64 arithmetic on this GPU runs at 1/64 of the FP32 rate, and an SVD of a
+// few hundred columns is latency-bound, so the work is split:
+//
+//  Phase A (FP32, Jacobi): one-sided (Hestenes) Jacobi on an FP32 copy of W,
+//    run to convergence. For k <= 64 one CTA holds W and V in shared memory
+//    and processes the k/2 disjoint pairs of each round-robin round on its
+//    warps. For larger k a thread-block cluster holds the columns in the
+//    shared memories of its CTAs: each CTA owns two blocks of columns, rotates
+//    every pair across them (and, once per sweep, the pairs inside them), then
+//    the blocks move one step along the round-robin circle through distributed
+//    shared memory; one cluster barrier per round, double-buffered.
+//  Phase B (FP64, refinement): from U0, V0, iterate
+//      T = U^T W V,  R = I - U^T U,  S = I - V^T V,
+//      d_i = T_ii / (1 - (R_ii + S_ii) / 2),
+//      for i != j with a = T_ij + d_j R_ij, b = T_ji + d_j S_ij:
+//        F_ij = (a d_j + b d_i) / (d_j^2 - d_i^2),  G_ij = (a d_i + b d_j) / (d_j^2 - d_i^2),
+//      F_ii = R_ii / 2, G_ii = S_ii / 2;  U <- U + U F,  V <- V + V G,
+//    which solves the first-order conditions U'^T U' = I, V'^T V' = I and
+//    U'^T W V' diagonal, and so converges quadratically. Every product is an
+//    FP64 GEMM spread over all SMs. Pairs with d_i^2 ~ d_j^2 keep only the
+//    orthogonality correction. Iteration t's kernels exit at once if an
+//    earlier iteration already converged (a device-side flag; no host sync).
+//  Fallback: if Phase B has not converged after its iterations, the one-CTA
+//    FP64 Jacobi SVD runs instead (status bit 1).
+// The result is sorted by singular value and truncated as before.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "profile.cuh"
+#include "svd.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cabs {
+namespace {
+
+constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
+constexpr float kTolA = 1e-5f;          // Phase A rotation threshold |g| > tol sqrt(a b)
+constexpr int kMaxSweepsA = 40;
+constexpr double kTolB = 1e-12;         // Phase B: converged when max |F_ij|, |G_ij| (i != j) < tol
+constexpr int kItersB = 6;
+constexpr int kNotDone = 0x7fffffff;
+
+__device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& q) {
+  if (pr == 0) {
+    p = round;
+    q = kk - 1;
+  } else {
+    p = (round + pr) % (kk - 1);
+    q = (round - pr + kk - 1) % (kk - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Rotates columns x, y (length k, lane-strided) so that they become
+// orthogonal; returns true if a rotation was applied. x, y, vx, vy may live
+// in shared or distributed shared memory.
+__device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, float* vy, int k, int lane) {
+  float a = 0.f, b = 0.f, g = 0.f;
+  for (int i = lane; i < k; i += 32) {
+    const float u = x[i], v = y[i];
+    a = fmaf(u, u, a);
+    b = fmaf(v, v, b);
+    g = fmaf(u, v, g);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  g = warp_sum(g);
+  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) return false;
+  const float zeta = (b - a) / (2.f * g);
+  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  const float c = rsqrtf(fmaf(t, t, 1.f));
+  const float s = c * t;
+  for (int i = lane; i < k; i += 32) {
+    const float u = x[i], v = y[i];
+    x[i] = c * u - s * v;
+    y[i] = s * u + c * v;
+    const float p = vx[i], q = vy[i];
+    vx[i] = c * p - s * q;
+    vy[i] = s * p + c * q;
+  }
+  return true;
+}
+
+// Writes U0 (normalised columns) and V0 in FP64, column-major k x k.
+__device__ __forceinline__ void emit_column(const float* w, const float* v, int k, int gc, int lane, double* U0,
+                                            double* V0) {
+  float a = 0.f;
+  for (int i = lane; i < k; i += 32) a = fmaf(w[i], w[i], a);
+  a = warp_sum(a);
+  const float nrm = sqrtf(a);
+  const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+  for (int i = lane; i < k; i += 32) {
+    U0[(size_t)gc * k + i] = (double)(w[i] * inv);
+    V0[(size_t)gc * k + i] = (double)v[i];
+  }
+}
+
+// ---------------------------------------------------------- Phase A, 1 CTA
+
+__global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict__ W, int k, double* __restrict__ U0,
+                                                         double* __restrict__ V0, int* sweeps_out) {
+  extern __shared__ __align__(16) float s32[];
+  float* Wc = s32;                    // column-major k x k
+  float* Vc = s32 + (size_t)k * k;
+  __shared__ int rotated;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Wc[(size_t)j * k + i] = (float)W[e];
+    Vc[e] = (i == j) ? 1.f : 0.f;
+  }
+  if (tid == 0) rotated = 0;
+  __syncthreads();
+  const int kk = k + (k & 1);
+  int sweep = 0;
+  bool conv = k < 2;
+  while (!conv && sweep < kMaxSweepsA) {
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = warp; pr < kk / 2; pr += nwarps) {
+        int p, q;
+        rr_pair(round, pr, kk, p, q);
+        if (q >= k) continue;
+        if (rotate_pair_f32(Wc + (size_t)p * k, Wc + (size_t)q * k, Vc + (size_t)p * k, Vc + (size_t)q * k, k, lane) &&
+            lane == 0)
+          rotated = 1;
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    const int any = rotated;
+    __syncthreads();
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    conv = any == 0;
+  }
+  for (int j = warp; j < k; j += nwarps) emit_column(Wc + (size_t)j * k, Vc + (size_t)j * k, k, j, lane, U0, V0);
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// ------------------------------------------------------- Phase A, cluster
+
+constexpr int kClusterThreads = 512;
+
+// Cluster of NC CTAs; CTA c holds blocks top[c], bot[c] of b columns each.
+// Round-robin over the 2 NC blocks: block slot top[0] stays, the others move
+// one place around the circle each round.
+__global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const double* __restrict__ W, int k, int b,
+                                                                        double* __restrict__ U0,
+                                                                        double* __restrict__ V0, int* sweeps_out) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int NC = (int)cluster.num_blocks();
+  const int c = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(16) float cs[];
+  const size_t blk = (size_t)b * k;  // floats per block of W (and of V)
+  // buffers[2]: each holds [W top | W bot | V top | V bot]
+  float* buf0 = cs;
+  float* buf1 = cs + 4 * blk;
+  __shared__ int rot_flag[2];
+  __shared__ int top_id[32], bot_id[32];
+  if (tid < NC) {
+    top_id[tid] = tid;
+    bot_id[tid] = 2 * NC - 1 - tid;
+  }
+  if (tid < 2) rot_flag[tid] = 0;
+  __syncthreads();
+  // load my two blocks into buf0
+  for (int slot = 0; slot < 2; ++slot) {
+    const int B = slot == 0 ? top_id[c] : bot_id[c];
+    float* w = buf0 + slot * blk;
+    float* v = buf0 + (2 + slot) * blk;
+    for (int e = tid; e < (int)blk; e += blockDim.x) {
+      const int j = e / k, i = e - j * k;
+      const int gc = B * b + j;
+      w[e] = gc < k ? (float)W[(size_t)i * k + gc] : 0.f;
+      v[e] = (gc < k && i == gc) ? 1.f : 0.f;
+    }
+  }
+  cluster.sync();
+  float* cur = buf0;
+  float* nxt = buf1;
+  int sweep = 0;
+  bool conv = false;
+  while (!conv && sweep < kMaxSweepsA) {
+    int my_rot = 0;
+    for (int round = 0; round < 2 * NC - 1; ++round) {
+      float* Wt = cur;
+      float* Wb = cur + blk;
+      float* Vt = cur + 2 * blk;
+      float* Vb = cur + 3 * blk;
+      if (round == 0) {
+        // pairs inside each block (each block sits in exactly one CTA in round 0)
+        const int bb = b + (b & 1);
+        for (int r = 0; r < bb - 1; ++r) {
+          for (int t = warp; t < bb; t += nwarps) {  // bb/2 pairs per slot, two slots
+            const int slot = t / (bb / 2), pr = t % (bb / 2);
+            int p, q;
+            rr_pair(r, pr, bb, p, q);
+            if (q >= b) continue;
+            float* w = slot == 0 ? Wt : Wb;
+            float* v = slot == 0 ? Vt : Vb;
+            my_rot |= rotate_pair_f32(w + (size_t)p * k, w + (size_t)q * k, v + (size_t)p * k, v + (size_t)q * k, k,
+                                      lane);
+          }
+          __syncthreads();
+        }
+      }
+      // every column of the top block against every column of the bottom block
+      for (int s = 0; s < b; ++s) {
+        for (int j = warp; j < b; j += nwarps) {
+          const int q = (j + s) % b;
+          my_rot |= rotate_pair_f32(Wt + (size_t)j * k, Wb + (size_t)q * k, Vt + (size_t)j * k, Vb + (size_t)q * k, k,
+                                    lane);
+        }
+        __syncthreads();
+      }
+      // move blocks one step around the circle (into the destinations' next buffers)
+      {
+        const int dst_top = (c == 0) ? 0 : (c == NC - 1 ? NC - 1 : c + 1);
+        const int dst_top_slot = (c == 0) ? 0 : (c == NC - 1 ? 1 : 0);
+        const int dst_bot = (c == 0) ? 1 : c - 1;
+        const int dst_bot_slot = (c == 0) ? 0 : 1;
+        float* rt = cluster.map_shared_rank(nxt, dst_top);
+        float* rb = cluster.map_shared_rank(nxt, dst_bot);
+        const float4* srcWt = (const float4*)Wt;
+        const float4* srcVt = (const float4*)Vt;
+        const float4* srcWb = (const float4*)Wb;
+        const float4* srcVb = (const float4*)Vb;
+        float4* dWt = (float4*)(rt + dst_top_slot * blk);
+        float4* dVt = (float4*)(rt + (2 + dst_top_slot) * blk);
+        float4* dWb = (float4*)(rb + dst_bot_slot * blk);
+        float4* dVb = (float4*)(rb + (2 + dst_bot_slot) * blk);
+        const int n4 = (int)(blk / 4);
+        for (int e = tid; e < n4; e += blockDim.x) {
+          dWt[e] = srcWt[e];
+          dVt[e] = srcVt[e];
+          dWb[e] = srcWb[e];
+          dVb[e] = srcVb[e];
+        }
+        if (tid == 0) {
+          // every CTA updates its replica of the block placement identically
+          int nt[32], nb[32];
+          for (int i = 0; i < NC; ++i) {
+            nt[i] = top_id[i];
+            nb[i] = bot_id[i];
+          }
+          for (int i = 0; i < NC; ++i) {
+            const int dt = (i == 0) ? 0 : (i == NC - 1 ? NC - 1 : i + 1);
+            const int dts = (i == 0) ? 0 : (i == NC - 1 ? 1 : 0);
+            const int db = (i == 0) ? 1 : i - 1;
+            const int dbs = (i == 0) ? 0 : 1;
+            if (dts == 0) nt[dt] = top_id[i]; else nb[dt] = top_id[i];
+            if (dbs == 0) nt[db] = bot_id[i]; else nb[db] = bot_id[i];
+          }
+          for (int i = 0; i < NC; ++i) {
+            top_id[i] = nt[i];
+            bot_id[i] = nb[i];
+          }
+        }
+      }
+      cluster.sync();
+      // every CTA has read last sweep's flags before arriving here, so the
+      // slot of the next sweep can be cleared now
+      if (round == 0 && tid == 0) rot_flag[(sweep + 1) & 1] = 0;
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    // cluster-wide "any rotation in this sweep"
+    if (my_rot) atomicOr(&rot_flag[sweep & 1], 1);
+    cluster.sync();
+    int any = 0;
+    for (int r = 0; r < NC; ++r) any |= *cluster.map_shared_rank(&rot_flag[sweep & 1], r);
+    conv = any == 0;
+    ++sweep;
+  }
+  // write out my two blocks
+  const int ids[2] = {top_id[c], bot_id[c]};
+  for (int slot = 0; slot < 2; ++slot) {
+    for (int j = warp; j < b; j += nwarps) {
+      const int gc = ids[slot] * b + j;
+      if (gc < k) emit_column(cur + slot * blk + (size_t)j * k, cur + (2 + slot) * blk + (size_t)j * k, k, gc, lane, U0, V0);
+    }
+  }
+  if (c == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
+  cluster.sync();
+}
+
+// ------------------------------------------------------------- Phase B
+
+constexpr int kGT = 16, kGK = 16;
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__global__ void svd_flags_init_kernel(unsigned long long* maxoff, int iters, int* done_iter, GridBarrier* bar) {
+  if (threadIdx.x < iters) maxoff[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) {
+    *done_iter = kNotDone;
+    bar->count = 0u;
+    bar->gen = 0u;
+    bar->err = 0;
+  }
+}
+
+// ---------------------------------------------------- grid barrier, bounded
+// All CTAs of a cooperative launch arrive on a counter; the last one bumps a
+// generation word the others wait on. The wait gives up after ~2^24 polls
+// (about a second), raising bar->err so every CTA can leave the kernel.
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &bar->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      bar->count = 0u;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1ll << 24) || *(volatile int*)&bar->err) {
+          atomicOr(&bar->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One 16 x 16 tile of C = op(A) B (+ Cadd); k x k column-major; 256 threads.
+__device__ __forceinline__ void gemm_tile(int k, int ti, int tj, const double* __restrict__ A, int transA,
+                                          const double* __restrict__ B, const double* __restrict__ Cadd,
+                                          double* __restrict__ Cout, double (*As)[kGT + 1], double (*Bs)[kGT + 1]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = ti * kGT, j0 = tj * kGT;
+  double acc = 0.0;
+  for (int p0 = 0; p0 < k; p0 += kGK) {
+    const int gi = i0 + tx, gp = p0 + ty;
+    double v = 0.0;
+    if (gi < k && gp < k) v = transA ? A[(size_t)gi * k + gp] : A[(size_t)gp * k + gi];
+    As[ty][tx] = v;
+    const int gj = j0 + tx;
+    Bs[ty][tx] = (gp < k && gj < k) ? B[(size_t)gj * k + gp] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kGK; ++p) acc = fma(As[p][ty], Bs[p][tx], acc);
+    __syncthreads();
+  }
+  const int gi = i0 + ty, gj = j0 + tx;
+  if (gi < k && gj < k) {
+    const size_t o = (size_t)gj * k + gi;
+    Cout[o] = Cadd ? Cadd[o] + acc : acc;
+  }
+}
+
+struct RefineArgs {
+  int k;
+  const double* W;  // row-major k x k (= W^T column-major)
+  double *U0, *U1, *V0, *V1, *P, *T, *UtU, *VtV, *F, *G, *d;
+  unsigned long long* maxoff;
+  int* done_iter;
+  GridBarrier* bar;
+  int* status;
+};
+
+// Phase B in one launch: every iteration's GEMMs are spread over the CTAs as
+// 16 x 16 tiles, with a grid barrier between dependent phases; all CTAs read
+// the same convergence measure after a barrier, so they stop together.
+__global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
+  __shared__ double As[kGK][kGT + 1];
+  __shared__ double Bs[kGK][kGT + 1];
+  __shared__ double dsh[CABS_MAX_K];
+  __shared__ double dmax2;
+  const int k = a.k;
+  const unsigned nb = gridDim.x;
+  const int nt = (k + kGT - 1) / kGT;
+  const int tiles = nt * nt;
+  double prev = 0.0;
+  for (int t = 0; t < kItersB; ++t) {
+    const double* U = (t & 1) ? a.U1 : a.U0;
+    const double* V = (t & 1) ? a.V1 : a.V0;
+    double* Un = (t & 1) ? a.U0 : a.U1;
+    double* Vn = (t & 1) ? a.V0 : a.V1;
+    for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
+    if (!grid_sync(a.bar, nb)) return;
+    for (int x = blockIdx.x; x < 3 * tiles; x += nb) {
+      const int which = x / tiles, y = x - which * tiles;
+      if (which == 0) gemm_tile(k, y % nt, y / nt, U, 1, a.P, nullptr, a.T, As, Bs);
+      else if (which == 1) gemm_tile(k, y % nt, y / nt, U, 1, U, nullptr, a.UtU, As, Bs);
+      else gemm_tile(k, y % nt, y / nt, V, 1, V, nullptr, a.VtV, As, Bs);
+    }
+    if (!grid_sync(a.bar, nb)) return;
+    // coefficients F, G and singular value estimates d
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const size_t ii = (size_t)i * k + i;
+      dsh[i] = a.T[ii] / (1.0 - 0.5 * ((1.0 - a.UtU[ii]) + (1.0 - a.VtV[ii])));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int i = 0; i < k; ++i) m = fmax(m, fabs(dsh[i]));
+      dmax2 = m * m;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < k; i += blockDim.x) a.d[i] = dsh[i];
+    double local = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
+         e += (long long)nb * blockDim.x) {
+      const int j = (int)(e / k), i = (int)(e - (long long)j * k);
+      const size_t ij = (size_t)j * k + i, ji = (size_t)i * k + j;
+      const double Rij = (i == j ? 1.0 : 0.0) - a.UtU[ij];
+      const double Sij = (i == j ? 1.0 : 0.0) - a.VtV[ij];
+      double f, g;
+      if (i == j) {
+        f = 0.5 * Rij;
+        g = 0.5 * Sij;
+      } else {
+        const double di = dsh[i], dj = dsh[j];
+        const double den = dj * dj - di * di;
+        if (fabs(den) <= 1e-13 * dmax2) {
+          f = 0.5 * Rij;
+          g = 0.5 * Sij;
+        } else {
+          const double al = a.T[ij] + dj * Rij;
+          const double be = a.T[ji] + dj * Sij;
+          f = (al * dj + be * di) / den;
+          g = (al * di + be * dj) / den;
+        }
+        local = fmax(local, fmax(fabs(f), fabs(g)));
+      }
+      a.F[ij] = f;
+      a.G[ij] = g;
+    }
+    local = warp_max(local);
+    if ((threadIdx.x & 31) == 0 && local > 0.0) atomicMax(a.maxoff + t, dbits(local));
+    if (!grid_sync(a.bar, nb)) return;
+    for (int x = blockIdx.x; x < 2 * tiles; x += nb) {
+      const int which = x / tiles, y = x - which * tiles;
+      if (which == 0) gemm_tile(k, y % nt, y / nt, U, 0, a.F, U, Un, As, Bs);
+      else gemm_tile(k, y % nt, y / nt, V, 0, a.G, V, Vn, As, Bs);
+    }
+    // quadratic convergence, or a plateau at the rounding floor
+    const double m = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + t));
+    const bool conv = m < 1e-10 || (t >= 1 && m < 1e-7 && m > 0.25 * prev);
+    prev = m;
+    if (!grid_sync(a.bar, nb)) return;
+    if (conv) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) *a.done_iter = t;
+      return;
+    }
+  }
+}
+
+// Sort, sign-fix, truncate, and write sig (desc), Uw, Vw (row-major, column r
+// = r-th singular vector). Runs unless the FP64 Jacobi fallback is needed.
+__global__ void __launch_bounds__(256) refine_final_kernel(int k, double trunc_rtol, const double* __restrict__ Ubuf0,
+                                                           const double* __restrict__ Ubuf1,
+                                                           const double* __restrict__ Vbuf0,
+                                                           const double* __restrict__ Vbuf1, const double* __restrict__ d,
+                                                           const int* __restrict__ done_iter, int iters,
+                                                           double* __restrict__ sig_out, double* __restrict__ Uw_out,
+                                                           double* __restrict__ Vw_out, int* rank_out, int* status,
+                                                           const GridBarrier* __restrict__ bar) {
+  const int done = *done_iter;
+  if (threadIdx.x == 0 && status && bar->err) atomicOr(status, 4);
+  if (done == kNotDone) {
+    if (threadIdx.x == 0 && status) atomicOr(status, 2);
+    return;  // the FP64 Jacobi fallback writes the outputs
+  }
+  const int last = done;  // U, V after iteration `done` live in buffer (done + 1) % 2
+  const double* U = ((last + 1) & 1) ? Ubuf1 : Ubuf0;
+  const double* V = ((last + 1) & 1) ? Vbuf1 : Vbuf0;
+  __shared__ double sg[CABS_MAX_K];
+  __shared__ int pos[CABS_MAX_K];
+  __shared__ int rank_s;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = fabs(d[i]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    int r = 0;
+    for (int i = 0; i < k; ++i) r += (sg[i] > sg[j]) || (sg[i] == sg[j] && i < j);
+    pos[j] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int j = 0; j < k; ++j) smax = fmax(smax, sg[j]);
+    int r = 0;
+    if (smax > 0.0) {
+      const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
+      for (int j = 0; j < k; ++j) r += sg[j] > tol;
+    }
+    rank_s = r;
+    if (rank_out) *rank_out = r;
+  }
+  __syncthreads();
+  const int rank = rank_s;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) sig_out[pos[j]] = sg[j];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int j = e / k, i = e - j * k;  // column j, row i of U / V (column-major)
+    const int r = pos[j];
+    const bool keep = r < rank;
+    const double sgn = d[j] < 0.0 ? -1.0 : 1.0;
+    Uw_out[(size_t)i * k + r] = keep ? sgn * U[e] : 0.0;
+    Vw_out[(size_t)i * k + r] = keep ? V[e] : 0.0;
+  }
+}
+
+// ------------------------------------------------ FP64 Jacobi (fallback)
+
+constexpr int kSvdThreads = 1024;
+constexpr int kMaxSweeps = 40;
+constexpr double kJacobiTol = 1e-15;
+constexpr size_t kSvdSmemLimit = 200 * 1024;
+
+__device__ __forceinline__ void pair_of_f64(int round, int pr, int kk, int& p, int& q) {
+  if (pr == 0) {
+    p = round;
+    q = kk - 1;
+  } else {
+    p = (round + pr) % (kk - 1);
+    q = (round - pr + kk - 1) % (kk - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// One CTA. W (k x k, row-major). Wc/Vc: column-major scratch (shared memory
+// when use_smem, else the given global buffers). Outputs: sig (k, descending),
+// Uw, Vw (k x k row-major, column r = r-th singular vector, zero beyond rank).
+__global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double* __restrict__ W, int k,
+                                                                  double trunc_rtol, int use_smem,
+                                                                  double* Wc_g, double* Vc_g,
+                                                                  double* __restrict__ sig_out,
+                                                                  double* __restrict__ Uw_out,
+                                                                  double* __restrict__ Vw_out, int* rank_out,
+                                                                  int* sweeps_out, int* status,
+                                                                  const int* __restrict__ done_iter) {
+  if (done_iter && *done_iter != 0x7fffffff) return;
+  extern __shared__ __align__(16) double svd_smem[];
+  __shared__ double sig[CABS_MAX_K];
+  __shared__ int pos[CABS_MAX_K];
+  __shared__ int rotated;
+  __shared__ int rank_s;
+  double* Wc = use_smem ? svd_smem : Wc_g;
+  double* Vc = use_smem ? svd_smem + (size_t)k * k : Vc_g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int kk2 = k * k;
+  for (int e = tid; e < kk2; e += blockDim.x) {
+    const int i = e / k, j = e - i * k;
+    Wc[(size_t)j * k + i] = W[e];
+    Vc[e] = (i == j) ? 1.0 : 0.0;
+  }
+  if (tid == 0) rotated = 0;
+  __syncthreads();
+
+  const int kk = k + (k & 1);
+  const int npairs = kk / 2;
+  int sweep = 0;
+  bool converged = (k < 2);
+  while (!converged && sweep < kMaxSweeps) {
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = warp; pr < npairs; pr += nwarps) {
+        int p, q;
+        pair_of_f64(round, pr, kk, p, q);
+        if (q >= k) continue;
+        double* wp = Wc + (size_t)p * k;
+        double* wq = Wc + (size_t)q * k;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wp[i], y = wq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > kJacobiTol * sqrt(a) * sqrt(b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = fabs(zeta) > 1e150 ? 0.5 / zeta
+                                              : copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = 1.0 / sqrt(fma(t, t, 1.0));
+          const double s = c * t;
+          double* vp = Vc + (size_t)p * k;
+          double* vq = Vc + (size_t)q * k;
+          for (int i = lane; i < k; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = c * x - s * y;
+            wq[i] = s * x + c * y;
+            const double u = vp[i], v = vq[i];
+            vp[i] = c * u - s * v;
+            vq[i] = s * u + c * v;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    const int any = rotated;
+    __syncthreads();
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    converged = (any == 0);
+  }
+
+  // singular values = column norms, then a rank sort (descending, stable)
+  for (int j = warp; j < k; j += nwarps) {
+    const double* wj = Wc + (size_t)j * k;
+    double a = 0.0;
+    for (int i = lane; i < k; i += 32) a = fma(wj[i], wj[i], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[j] = sqrt(a);
+  }
+  __syncthreads();
+  for (int j = tid; j < k; j += blockDim.x) {
+    const double sj = sig[j];
+    int r = 0;
+    for (int i = 0; i < k; ++i) r += (sig[i] > sj) || (sig[i] == sj && i < j);
+    pos[j] = r;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double smax = 0.0;
+    for (int j = 0; j < k; ++j) smax = fmax(smax, sig[j]);
+    int r = 0;
+    if (smax > 0.0) {
+      const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
+      for (int j = 0; j < k; ++j) r += sig[j] > tol;
+    }
+    rank_s = r;
+    if (rank_out) *rank_out = r;
+    if (sweeps_out) *sweeps_out = sweep;
+    if (status && !converged) atomicOr(status, 1);
+  }
+  __syncthreads();
+  const int rank = rank_s;
+  for (int j = tid; j < k; j += blockDim.x) sig_out[pos[j]] = sig[j];
+  for (int e = tid; e < kk2; e += blockDim.x) {
+    const int j = e / k, i = e - j * k;  // column j, row i (column-major walk)
+    const int r = pos[j];
+    const bool keep = r < rank;
+    Vw_out[(size_t)i * k + r] = keep ? Vc[e] : 0.0;
+    Uw_out[(size_t)i * k + r] = keep ? Wc[e] / sig[j] : 0.0;
+  }
+}
+
+}  // namespace
+
+cabs_status launch_svd_jacobi_f64(const double* W, int k, double trunc_rtol, const int* done_iter, double* Wc,
+                                  double* Vc, double* sig, double* Uw, double* Vw, int* rank, int* sweeps, int* status,
+                                  cudaStream_t stream) {
+  const size_t smem_need = (size_t)2 * k * k * sizeof(double);
+  const int use_smem = smem_need <= kSvdSmemLimit;
+  const size_t smem = use_smem ? smem_need : 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(svd_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  CABS_LAUNCH(stream, "svd_jacobi_kernel",
+              svd_jacobi_kernel<<<1, kSvdThreads, smem, stream>>>(W, k, trunc_rtol, use_smem, Wc, Vc, sig, Uw, Vw, rank,
+                                                                  sweeps, status, done_iter));
+  return CABS_OK;
+}
+
+SvdWs carve_svd(Carve& cv, int k) {
+  SvdWs w;
+  const size_t kk = (size_t)k * k;
+  for (int t = 0; t < 2; ++t) {
+    w.U[t] = cv.take<double>(kk);
+    w.V[t] = cv.take<double>(kk);
+  }
+  w.P = cv.take<double>(kk);
+  w.T = cv.take<double>(kk);
+  w.UtU = cv.take<double>(kk);
+  w.VtV = cv.take<double>(kk);
+  w.F = cv.take<double>(kk);
+  w.G = cv.take<double>(kk);
+  w.d = cv.take<double>(k);
+  w.maxoff = cv.take<unsigned long long>(kItersB);
+  w.done_iter = cv.take<int>(1);
+  w.bar = cv.take<GridBarrier>(1);
+  w.Wc = cv.take<double>(kk);
+  w.Vc = cv.take<double>(kk);
+  return w;
+}
+
+static int cluster_size_for(int k) {
+  static int cached = -1;
+  if (cached < 0) {
+    cached = 8;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int nc : {16}) {
+      const int b = (CABS_MAX_K + 2 * nc - 1) / (2 * nc);
+      const size_t smem = (size_t)8 * b * CABS_MAX_K * sizeof(float);
+      cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nc);
+      cfg.blockDim = dim3(kClusterThreads);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = nc;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, svd32_cluster_kernel, &cfg) == cudaSuccess && clusters > 0)
+        cached = nc;
+      cudaGetLastError();
+    }
+  }
+  (void)k;
+  return cached;
+}
+
+cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
+                       int* sweeps, int* status, const SvdWs& w, cudaStream_t stream) {
+  // ---- Phase A: FP32 Jacobi -> U[0], V[0]
+  if (k <= kCtaMaxK) {
+    const size_t smem = (size_t)2 * k * k * sizeof(float);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(svd32_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CABS_LAUNCH(stream, "svd32_cta_kernel",
+                svd32_cta_kernel<<<1, 512, smem, stream>>>(W, k, w.U[0], w.V[0], sweeps));
+  } else {
+    const int nc = cluster_size_for(k);
+    int b = (k + 2 * nc - 1) / (2 * nc);
+    b = (b + 3) & ~3;  // float4 block copies
+    const size_t smem = (size_t)8 * b * k * sizeof(float);
+    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nc);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CABS_LAUNCH(stream, "svd32_cluster_kernel",
+                cudaLaunchKernelEx(&cfg, svd32_cluster_kernel, W, k, b, w.U[0], w.V[0], sweeps));
+  }
+  // ---- Phase B: FP64 refinement, one cooperative launch
+  CABS_LAUNCH(stream, "svd_flags_init",
+              svd_flags_init_kernel<<<1, 32, 0, stream>>>(w.maxoff, kItersB, w.done_iter, w.bar));
+  {
+    const int tiles = ceil_div(k, kGT) * ceil_div(k, kGT);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_persistent_kernel, 256, 0);
+    const int grid = std::max(1, std::min(tiles, sm_count() * std::max(per_sm, 1)));
+    RefineArgs ra{k, W, w.U[0], w.U[1], w.V[0], w.V[1], w.P, w.T, w.UtU, w.VtV, w.F, w.G, w.d, w.maxoff,
+                  w.done_iter, w.bar, status};
+    void* args[] = {&ra};
+    CABS_LAUNCH(stream, "refine_persistent_kernel",
+                cudaLaunchCooperativeKernel((const void*)refine_persistent_kernel, dim3(grid), dim3(256), args, 0,
+                                            stream));
+  }
+  CABS_LAUNCH(stream, "refine_final_kernel",
+              refine_final_kernel<<<1, 256, 0, stream>>>(k, trunc_rtol, w.U[0], w.U[1], w.V[0], w.V[1], w.d,
+                                                         w.done_iter, kItersB, sig, Uw, Vw, rank, status, w.bar));
+  // ---- fallback: FP64 Jacobi (exits at once when Phase B converged)
+  return launch_svd_jacobi_f64(W, k, trunc_rtol, w.done_iter, w.Wc, w.Vc, sig, Uw, Vw, rank, sweeps, status, stream);
+}
+
+}  // namespace cabs

@@ -1,0 +1,38 @@
+// FP64-accurate SVD of the k x k core matrix (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace cabs {
+
+// Grid barrier state for cooperative kernels (zeroed before each launch).
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+};
+
+struct SvdWs {
+  double *U[2], *V[2];                 // column-major iterates
+  double *P, *T, *UtU, *VtV, *F, *G;   // k x k scratch
+  double* d;                           // current singular value estimates
+  unsigned long long* maxoff;          // per-iteration max |F|, |G| (as ordered bits)
+  int* done_iter;                      // first converged iteration, or INT_MAX
+  GridBarrier* bar;
+  double *Wc, *Vc;                     // FP64 Jacobi fallback scratch
+};
+
+SvdWs carve_svd(Carve& cv, int k);
+
+// W (k x k row-major, FP64) -> sig (k, descending), Uw, Vw (k x k row-major,
+// column r = r-th singular vector, zero beyond the kept rank), *rank, *sweeps.
+cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
+                       int* sweeps, int* status, const SvdWs& w, cudaStream_t stream);
+
+// One-CTA FP64 one-sided Jacobi; does nothing if *done_iter != INT_MAX
+// (done_iter may be NULL: always run).
+cabs_status launch_svd_jacobi_f64(const double* W, int k, double trunc_rtol, const int* done_iter, double* Wc,
+                                  double* Vc, double* sig, double* Uw, double* Vw, int* rank, int* sweeps, int* status,
+                                  cudaStream_t stream);
+
+}  // namespace cabs

@@ -1,18 +1,260 @@
-// Tensor-core k-means assignment (TF32 / BF16 modes). Not yet available in
-// this build: the launcher reports CABS_EINVAL instead of computing anything,
-// so no reduced-precision request silently runs another path.
+// Step a5 on tensor cores -- the k-means assignment of Eq. (wkmeans) for the
+// BF16 and TF32 modes.
+//
+// The distance contraction x . z for all points x (rows of P or Q) and all
+// k2 <= 256 centres z is one tcgen05 MMA chain per 128-point tile: points
+// stream through a TMA ring, the centres (BF16, or TF32 when k <= 128) stay
+// resident in shared memory, and a 128 x 256 FP32 accumulator sits in TMEM
+// (two of them, so the epilogue of one tile overlaps the MMAs of the next).
+// Epilogue warps read a row of accumulators per thread and form
+// |z|^2 - 2 x . z, keeping the best and second-best centre; warps holding
+// the two column halves of a row merge through shared memory. When the two
+// best are closer than the rounding bound of the operands
+// (2^-6 |x| (|z_a| + |z_b|) for BF16, 2^-8 for TF32), both distances are
+// recomputed in FP32 by direct differences and the smaller wins (ties to the
+// lower centre index). The weighted encoding error uses the winner's direct
+// FP32 distance and is summed per CTA in FP64.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+#include "profile.cuh"
 #include "tc_assign.cuh"
+#include "tc_gemm.cuh"
 
 namespace cabs {
+namespace {
 
-int tc_assign_blocks(int64_t M) { return ceil_div(M, 128); }
+constexpr int kBN = 256;
 
-void tc_assign_carve(Carve& cv, int64_t M, int d, int k2) { (void)cv; (void)M; (void)d; (void)k2; }
+template <bool kTF32>
+struct AsgCfg {
+  static constexpr int KC = kTF32 ? 32 : 64;
+  static constexpr int ES = kTF32 ? 4 : 2;
+};
 
-cabs_status tc_assign_launch(const float*, int64_t, int, const float*, const float*, int, const float*,
-                             const float*, int*, double*, int*, bool, void*, cudaStream_t) {
-  set_error("TF32/BF16 tensor-core assignment is not available in this build");
-  return CABS_EINVAL;
+template <bool kTF32>
+__global__ void to_operand_kernel(const float* __restrict__ X, long long rows, int d, int Kp, void* __restrict__ out) {
+  const long long total = rows * Kp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / Kp;
+    const int q = (int)(e - r * Kp);
+    const float v = q < d ? X[r * d + q] : 0.f;
+    if constexpr (kTF32)
+      ((float*)out)[e] = v;
+    else
+      ((__nv_bfloat16*)out)[e] = __float2bfloat16_rn(v);
+  }
+}
+
+__device__ __forceinline__ float direct_dist(const float* __restrict__ x, const float* __restrict__ z, int d) {
+  float s = 0.f;
+  for (int q = 0; q < d; ++q) {
+    const float t = x[q] - z[q];
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
+struct Best2 {
+  float b1, b2;
+  int j1, j2;
+};
+
+__device__ __forceinline__ void best2_push(Best2& s, float v, int j) {
+  if (v < s.b1 || (v == s.b1 && j < s.j1)) {
+    s.b2 = s.b1;
+    s.j2 = s.j1;
+    s.b1 = v;
+    s.j1 = j;
+  } else if (v < s.b2 || (v == s.b2 && j < s.j2)) {
+    s.b2 = v;
+    s.j2 = j;
+  }
+}
+
+template <bool kTF32>
+__global__ void __launch_bounds__(tc::kThreads, 1)
+    tc_assign_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const float* __restrict__ zn, const float* __restrict__ xn, const float* __restrict__ w,
+                     const float* __restrict__ X, const float* __restrict__ Z, int d, int M, int k2, int nch,
+                     int units, int* __restrict__ labels, double* __restrict__ part_e, int* rechecks, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ tc::Barriers bars;
+  __shared__ Best2 xchg[4][32];
+  __shared__ double red[tc::kEpiWarps];
+  uint8_t *Bres, *Aring;
+  tc::setup<kBN>(smem_raw, nch, Bres, Aring, &bars);
+  const int MT = units;  // one column block: every unit is a row tile
+  const int u0 = (int)((long long)units * blockIdx.x / gridDim.x);
+  const int u1 = (int)((long long)units * (blockIdx.x + 1) / gridDim.x);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::prefetch_tmap(&tmA);
+      tc::prefetch_tmap(&tmB);
+      tc::producer_loop<kBN>(&tmA, &tmB, Bres, Aring, &bars, u0, u1, MT, nch, AsgCfg<kTF32>::KC);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) tc::mma_loop<kTF32, kBN>(Bres, Aring, &bars, u0, u1, MT, nch);
+  } else if (warp >= tc::kEpiWarp0) {
+    const int e = warp - tc::kEpiWarp0;
+    const int sub = warp & 3, half = e >> 2;
+    const int row = sub * 32 + lane;
+    const float rel = kTF32 ? 0.00390625f : 0.015625f;  // 2^-8 (TF32), 2^-6 (BF16)
+    double esum = 0.0;
+    int nre = 0;
+    int ab = 0;
+    uint32_t accph[2] = {0, 0};
+    for (int u = u0; u < u1; ++u) {
+      // every epilogue warp must leave together: they share named barrier 1
+      const int fail = tc::mbar_wait(&bars.accfull[ab], accph[ab], &bars.abort) ? 0 : 1;
+      int anyfail;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
+          "bar.red.or.pred p, 1, %2, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+          : "=r"(anyfail)
+          : "r"(fail), "n"(tc::kEpiWarps * 32));
+      if (anyfail) break;
+      accph[ab] ^= 1;
+      tc::fence_after_sync();
+      Best2 s{__int_as_float(0x7f800000), __int_as_float(0x7f800000), 0x7fffffff, 0x7fffffff};
+#pragma unroll 1
+      for (int j = 0; j < kBN / 2 / 32; ++j) {
+        const int c0 = half * (kBN / 2) + j * 32;
+        if (c0 >= k2) break;  // warp-uniform
+        float v[32];
+        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * kBN + c0) + ((uint32_t)(sub * 32) << 16), v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int jj = c0 + q;
+          if (jj < k2) best2_push(s, fmaf(-2.f, v[q], __ldg(zn + jj)), jj);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bars.accempty[ab]);
+      ab ^= 1;
+      // merge the two column halves of each row (warps w and w + 4)
+      if (half == 1) xchg[sub][lane] = s;
+      asm volatile("bar.sync 1, %0;" ::"n"(tc::kEpiWarps * 32));
+      if (half == 0) {
+        const Best2 o = xchg[sub][lane];
+        best2_push(s, o.b1, o.j1);
+        best2_push(s, o.b2, o.j2);
+        const long long l = (long long)u * tc::kBM + row;
+        if (l < M) {
+          const float xl = xn[l];
+          float best = s.b1;
+          int bj = s.j1;
+          if (s.j2 < k2) {
+            const float bound = rel * sqrtf(fmaxf(xl, 0.f)) * (sqrtf(fmaxf(zn[s.j1], 0.f)) + sqrtf(fmaxf(zn[s.j2], 0.f)));
+            if (s.b2 - s.b1 <= bound) {
+              const float d1 = direct_dist(X + l * d, Z + (size_t)s.j1 * d, d);
+              const float d2 = direct_dist(X + l * d, Z + (size_t)s.j2 * d, d);
+              ++nre;
+              if (d2 < d1 || (d2 == d1 && s.j2 < s.j1)) {
+                bj = s.j2;
+                best = d2 - xl;
+              } else {
+                best = d1 - xl;
+              }
+            }
+          }
+          labels[l] = bj;
+          // the energy uses the winner's distance by direct differences (the
+          // expansion form loses relative accuracy when the distance is small)
+          (void)best;
+          esum += (double)w[l] * (double)direct_dist(X + l * d, Z + (size_t)bj * d, d);
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(tc::kEpiWarps * 32));
+    }
+    esum = warp_sum(esum);
+    nre = warp_sum(nre);
+    if (lane == 0) {
+      red[e] = esum;
+      if (nre && rechecks) atomicAdd(rechecks, nre);
+    }
+  }
+  tc::teardown<kBN>(&bars, err);
+  if (threadIdx.x == 0) {
+    double sacc = 0.0;
+    for (int i = 0; i < tc::kEpiWarps; ++i) sacc += red[i];
+    part_e[blockIdx.x] = (err && *err) ? __longlong_as_double(0x7ff8000000000000ll) : sacc;
+  }
+}
+
+struct TcWs {
+  void *Pp, *Zp;
+  int* err;
+};
+
+int kp_of(int d, bool tf32) {
+  const int KC = tf32 ? 32 : 64;
+  return (d + KC - 1) / KC * KC;
+}
+
+TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
+  const int Kp = kp_of(d, tf32);
+  const int es = tf32 ? 4 : 2;
+  TcWs w;
+  w.Pp = cv.take<char>((size_t)M * Kp * es);
+  w.Zp = cv.take<char>((size_t)kBN * Kp * es);
+  w.err = cv.take<int>(1);
+  return w;
+}
+
+template <bool kTF32>
+cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2, const float* xn,
+                            const float* w, int* labels, double* part_e, int* d_recheck, bool prep_points, void* tcws,
+                            cudaStream_t stream) {
+  Carve cv(tcws, (size_t)-1);
+  TcWs t = carve_tc(cv, M, d, k2, kTF32);
+  const int Kp = kp_of(d, kTF32);
+  const int nch = Kp / AsgCfg<kTF32>::KC;
+  if (kTF32 && nch * kBN * 128 > 128 * 1024) {
+    set_error("TF32 k-means assignment supports embedding widths up to 128 (got %d); use BF16", d);
+    return CABS_EINVAL;
+  }
+  const int sms = sm_count();
+  if (prep_points)
+    CABS_LAUNCH(stream, "tc_assign_points_prep",
+                to_operand_kernel<kTF32><<<std::max(1, std::min(ceil_div(M * Kp, 256), sms * 8)), 256, 0, stream>>>(
+                    X, M, d, Kp, t.Pp));
+  CABS_LAUNCH(stream, "tc_assign_centres_prep",
+              to_operand_kernel<kTF32><<<std::max(1, ceil_div((int64_t)kBN * Kp, 256)), 256, 0, stream>>>(
+                  Z, k2, d, Kp, t.Zp));
+  if (cudaMemsetAsync(t.err, 0, sizeof(int), stream) != cudaSuccess) return check_cuda("tc_assign err clear");
+  CUtensorMap tmA, tmB;
+  const int dt = kTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CABS_TRY(make_tmap_2d(&tmA, t.Pp, dt, M, Kp, (uint64_t)Kp * AsgCfg<kTF32>::ES, AsgCfg<kTF32>::KC, tc::kBM));
+  CABS_TRY(make_tmap_2d(&tmB, t.Zp, dt, k2, Kp, (uint64_t)Kp * AsgCfg<kTF32>::ES, AsgCfg<kTF32>::KC, kBN));
+  const int units = ceil_div(M, tc::kBM);
+  const int grid = tc_assign_blocks(M);
+  const size_t smem = tc::smem_bytes(nch, kBN);
+  cudaFuncSetAttribute(tc_assign_kernel<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  CABS_LAUNCH(stream, "tc_assign_kernel",
+              tc_assign_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(
+                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, part_e, d_recheck, t.err));
+  return CABS_OK;
+}
+
+}  // namespace
+
+int tc_assign_blocks(int64_t M) { return std::max(1, std::min(ceil_div(M, tc::kBM), sm_count())); }
+
+void tc_assign_carve(Carve& cv, int64_t M, int d, int k2) {
+  // sized for the wider (TF32) operands so either mode fits
+  carve_tc(cv, M, d, k2, true);
+}
+
+cabs_status tc_assign_launch(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2,
+                             const float* xn, const float* w, int* labels, double* part_e, int* d_recheck, bool bf16,
+                             bool prep_points, void* tcws, cudaStream_t stream) {
+  if (bf16)
+    return tc_assign_typed<false>(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prep_points, tcws, stream);
+  return tc_assign_typed<true>(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prep_points, tcws, stream);
 }
 
 }  // namespace cabs

@@ -306,3 +306,34 @@ def test_fp32_sketch_error_close_to_fp64(ctx, C):
     assert to_np(sk.pilot_rows).tolist() == ref.pilot_rows.tolist()
     e = C.cabs_error(ctx, C.dense_source(Ad), p, sk)
     assert e / e_ref - 1 <= 1e-3, (e, e_ref)
+
+
+# ------------------------------------------------- a3: the FP64 core SVD alone
+
+def _svd_case(k, kind):
+    g = np.random.default_rng(1000 + k)
+    if kind == "rand":
+        return g.standard_normal((k, k))
+    if kind == "graded":
+        Uq, _ = np.linalg.qr(g.standard_normal((k, k)))
+        Vq, _ = np.linalg.qr(g.standard_normal((k, k)))
+        return (Uq * 10.0 ** (-8.0 * np.arange(k) / max(k - 1, 1))) @ Vq.T
+    r = max(1, k // 3)
+    return g.integers(-3, 4, (k, r)).astype(float) @ g.integers(-3, 4, (k, r)).astype(float).T
+
+
+@pytest.mark.parametrize("k,kind", [(1, "rand"), (2, "rand"), (20, "rand"), (64, "rand"), (65, "rand"),
+                                    (128, "graded"), (200, "rand"), (256, "graded"), (256, "rankdef"),
+                                    (97, "rankdef")])
+def test_core_svd_fp64(ctx, C, k, kind):
+    W = _svd_case(k, kind)
+    out = C.cabs_sketching(ctx, dev(W), dev(W.T), dev(W), k, k, prec="fp64", core="pinv")
+    sig, Uw, Vw = to_np(out["sig"]), to_np(out["Uw"]), to_np(out["Vw"])
+    r = int(out["rank"].item())
+    ref = np.linalg.svd(W, compute_uv=False)
+    assert r == int(np.count_nonzero(ref > k * 2.220446049250313e-16 * ref[0]))
+    assert np.abs(sig - ref).max() <= 1e-12 * ref[0]
+    assert np.abs(Uw[:, :r].T @ Uw[:, :r] - np.eye(r)).max() <= 1e-12
+    assert np.abs(Vw[:, :r].T @ Vw[:, :r] - np.eye(r)).max() <= 1e-12
+    rec = (Uw[:, :r] * sig[:r]) @ Vw[:, :r].T
+    assert np.linalg.norm(rec - W) <= 1e-12 * np.linalg.norm(W)

@@ -1,0 +1,98 @@
+"""Tensor-core (tcgen05) paths against the FP64 oracle: the fused residual,
+the k-means assignment, and whole sketches in BF16 / TF32 mode.
+
+Tolerances follow the operand rounding: BF16 operands carry 2^-9 relative
+error, TF32 2^-12; the residual's relative error on a sketch with error >= 0.05
+moves by far less than 1e-3 of itself; assignments differ from FP64 only on
+rows the re-check cannot separate (counted, must be rare)."""
+import numpy as np
+import pytest
+
+from oracle import cabs_ref as o
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_1607_07395_gb300 import cabs
+    return cabs
+
+
+@pytest.fixture(scope="module")
+def ctx(C):
+    assert torch.cuda.is_available()
+    return C.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def fake_result(C, U, S, V, p):
+    sk = C.alloc_result(p)
+    sk.U.copy_(dev(U.astype(np.float32)))
+    sk.S.copy_(dev(S.astype(np.float64)))
+    sk.V.copy_(dev(V.astype(np.float32)))
+    return sk
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("m,n,lda,k", [(1000, 700, 700, 20), (4096, 2048, 2048, 256), (777, 1333, 1400, 100),
+                                       (130, 300, 304, 65), (5000, 257, 257, 128)])
+def test_tc_residual_matches_exact(ctx, C, prec, m, n, lda, k):
+    if prec == "tf32" and k > 256:
+        pytest.skip()
+    g = np.random.default_rng(m + n + k)
+    r = min(k, 40)
+    L = g.standard_normal((m, r)) @ g.standard_normal((r, n)) / np.sqrt(r)
+    full = np.zeros((m, lda), dtype=np.float32)
+    full[:, :n] = (L + 0.3 * g.standard_normal((m, n))).astype(np.float32)
+    A = full[:, :n].astype(np.float64)
+    U = g.standard_normal((m, k))
+    V = g.standard_normal((n, k))
+    U /= np.linalg.norm(U, axis=0)
+    V /= np.linalg.norm(V, axis=0)
+    S = np.abs(g.standard_normal(k)) * np.sqrt(m * n) / k
+    p = C.make_params(m, n, k, prec=prec)
+    sk = fake_result(C, U, S, V, p)
+    Ad = dev(full)[:, :n]
+    got = C.cabs_error(ctx, C.dense_source(Ad), p, sk)
+    want = o.rel_fro_error_dense(A, U.astype(np.float32).astype(np.float64), S,
+                                 V.astype(np.float32).astype(np.float64))
+    assert abs(got / want - 1) <= 1e-3, (got, want)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("M,d,k2", [(2000, 20, 20), (9000, 64, 64), (4099, 128, 100), (70000, 64, 256)])
+def test_tc_assign_matches_oracle(ctx, C, prec, M, d, k2):
+    g = np.random.default_rng(M + d)
+    centers = 3.0 * g.standard_normal((50, d))
+    X = centers[g.integers(0, 50, M)] + g.standard_normal((M, d))
+    init = g.choice(M, k2, replace=False)
+    ref = o.weighted_kmeans(X.astype(np.float32).astype(np.float64), init, 3, 0.0)
+    out = C.cabs_kmeans(ctx, dev(X.astype(np.float32)), dev(init.astype(np.int32)), k2, 3, prec=prec)
+    lab = out["labels"].cpu().numpy()
+    # iteration 0 sees the same centres on both sides: labels agree except unresolved near-ties
+    mism = (lab[0] != ref.labels[0]).mean()
+    assert mism <= 1e-3, mism
+    e = out["energy"].cpu().numpy()
+    assert np.all(np.abs(e / np.array(ref.energy) - 1) <= 1e-3), (e, ref.energy)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_sketch_reduced_precision_excess_small(ctx, C, prec):
+    A, _, _, _ = synth.decaying_lowrank_host(4096, 2048, rank=256, decay=30, noise_std=1e-4, seed=1607)
+    k = 64 if prec == "tf32" else 128
+    ref = o.cabs(o.DenseSource(A), k, iters=5, seed=1607, mode="stabilized")
+    e_ref = o.rel_fro_error_dense(A, ref.final.U, ref.final.S, ref.final.V)
+    p = C.make_params(4096, 2048, k, iters=5, seed=1607, prec=prec, core="stabilized")
+    Ad = dev(A)
+    sk = C.cabs_sketch(ctx, C.dense_source(Ad), p)
+    e = C.cabs_error(ctx, C.dense_source(Ad), p, sk)
+    assert sk.pilot_rows.cpu().numpy().tolist() == ref.pilot_rows.tolist()
+    assert e / e_ref - 1 <= 1e-3, (e, e_ref)
+    d = sk.diag()
+    assert d.status == 0
