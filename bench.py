@@ -394,7 +394,7 @@ def run_cabs(args):
                                                               int(math.ceil(0.99 * len(per_step))) - 1)], 4)),
                rel_fro_error=errs[-1], gpu_launches=int(launches),
                diag=dict(svd_sweeps=sweeps, svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
-                         snap_fallbacks=int(diag.snap_fallbacks)), roofline=roof, kernels=table, gather=gather,
+                         snap_fallbacks=int(diag.snap_fallbacks), rechecked=int(diag.rechecked)), roofline=roof, kernels=table, gather=gather,
                e2e=e2e, clocks=clocks)
     if not args.no_cpu:
         res["cpu_baseline"] = run_cpu_baseline(args.workload, args.cpu_steps)

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
     }
     __syncthreads();
   }
-  double sq[4] = {0.0, 0.0, 0.0, 0.0};
+  T sq[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const long long gm = m0 + ty * 4 + i;
@@ -84,13 +84,12 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
       const int gn = n0 + tx * 4 + j;
       if (gn < N) {
         out[gm * N + gn] = acc[i][j];
-        const double v = (double)acc[i][j];
-        sq[j] = fma(v, v, sq[j]);
+        sq[j] = fma(acc[i][j], acc[i][j], sq[j]);
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) colsq[ty][tx * 4 + j] = sq[j];
+  for (int j = 0; j < 4; ++j) colsq[ty][tx * 4 + j] = (double)sq[j];
   __syncthreads();
   if (tid < kGBN) {
     double s = 0.0;

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(256) rowblock_error_kernel(const T* __restrict
       }
       __syncthreads();
     }
+    T tn = T(0), td = T(0);
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const long long gi = i0 + ty * 4 + x;
@@ -114,12 +115,14 @@ __global__ void __launch_bounds__(256) rowblock_error_kernel(const T* __restrict
       for (int y = 0; y < 4; ++y) {
         const long long gj = j0 + tx * 4 + y;
         if (gj >= n) continue;
-        const double a = a_f64 ? ((const double*)A)[gi * lda + gj] : (double)((const float*)A)[gi * lda + gj];
-        const double dlt = a - (double)acc[x][y];
-        num = fma(dlt, dlt, num);
-        den = fma(a, a, den);
+        const T a = a_f64 ? (T)((const double*)A)[gi * lda + gj] : (T)((const float*)A)[gi * lda + gj];
+        const T dlt = a - acc[x][y];
+        tn = fma(dlt, dlt, tn);
+        td = fma(a, a, td);
       }
     }
+    num += (double)tn;
+    den += (double)td;
   }
   num = warp_sum(num);
   den = warp_sum(den);
@@ -165,12 +168,12 @@ __global__ void __launch_bounds__(256) sampled_error_kernel(cabs_source src, lon
     const U64x4 r = philox4x64_10((uint64_t)t, 0, 0, 0, seed, 2);
     const long long i = (long long)mulhi64(r.v[0], (uint64_t)m);
     const long long j = (long long)mulhi64(r.v[1], (uint64_t)n);
-    const double a = noalloc_entry<T>(src, i, j);
-    double ah = 0.0;
-    for (int c = 0; c < k; ++c) ah = fma((double)U[i * k + c] * S[c], (double)V[j * k + c], ah);
-    const double dl = a - ah;
-    num = fma(dl, dl, num);
-    den = fma(a, a, den);
+    const T a = (T)noalloc_entry<T>(src, i, j);
+    T ah = T(0);
+    for (int c = 0; c < k; ++c) ah = fma(U[i * k + c] * (T)S[c], V[j * k + c], ah);
+    const T dl = a - ah;
+    num += (double)(dl * dl);
+    den += (double)(a * a);
   }
   num = warp_sum(num);
   den = warp_sum(den);

@@ -15,9 +15,10 @@
 //         warp-shuffle reduction over the 32 lanes that share a point row.
 //   TF32/BF16: tensor-core contraction (separate kernel file), with near ties
 //         re-checked in FP32.
-// Update kernel: one CTA per centre; each warp scans a fixed slice of the
-// labels and sums its members in index order; the 8 warp sums are added in
-// a fixed order, so the centres do not depend on scheduling.
+// Update kernel: one CTA per centre; each of its 16 warps scans a fixed slice
+// of the labels (four loads in flight) and sums its members in index order;
+// the warp sums are added in a fixed order, so the centres do not depend on
+// scheduling.
 // Energies (weighted encoding errors) are per-CTA FP64 partials summed in a
 // fixed order.
 #include "common.cuh"
@@ -75,14 +76,10 @@ constexpr int kAN = 256;  // centres per CTA (all of them)
 
 __global__ void __launch_bounds__(256) assign_f32_kernel(const float* __restrict__ X, long long M, int d,
                                                          const float* __restrict__ Z, const float* __restrict__ zn,
-                                                         int k2, const float* __restrict__ xn,
-                                                         const float* __restrict__ w, int* __restrict__ labels,
-                                                         double* __restrict__ part_e) {
+                                                         int k2, int* __restrict__ labels) {
   __shared__ __align__(16) float xs[kAK][kAM + 4];
   __shared__ __align__(16) float zs[kAK][kAN + 4];
-  __shared__ double esum[8];
   const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
-  double e_local = 0.0;
   const long long m0 = (long long)blockIdx.x * kAM;
   float acc[8][8];
 #pragma unroll
@@ -141,17 +138,7 @@ __global__ void __launch_bounds__(256) assign_f32_kernel(const float* __restrict
       }
     }
     warp_argmin(best, bj);
-    if (tx == 0 && l < M) {
-      labels[l] = bj;
-      e_local += (double)w[l] * fmax(0.0, (double)best + (double)xn[l]);
-    }
-  }
-  if (tx == 0) esum[ty] = e_local;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < 8; ++i) s += esum[i];
-    part_e[blockIdx.x] = s;
+    if (tx == 0 && l < M) labels[l] = bj;
   }
 }
 
@@ -226,16 +213,101 @@ __global__ void __launch_bounds__(256) assign_f64_kernel(const double* __restric
   }
 }
 
+// ---------------------------------------------------- exact energies
+// Weighted encoding error sum_l w_l |x_l - z_s(l)|^2 by direct differences,
+// one warp per point (lanes over dimensions); CTA b sums a fixed contiguous
+// range of points, so the partial sums do not depend on scheduling.
+
+template <typename T>
+__global__ void __launch_bounds__(256) energy_exact_kernel(const T* __restrict__ X, long long M, int d,
+                                                           const T* __restrict__ Z, int k2,
+                                                           const int* __restrict__ labels, const T* __restrict__ w,
+                                                           double* __restrict__ part) {
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const long long lo = M * blockIdx.x / gridDim.x, hi = M * (blockIdx.x + 1) / gridDim.x;
+  double acc = 0.0;
+  for (long long l0 = lo + 4 * wi; l0 < hi; l0 += 32) {
+    T s4[4];
+    int j4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      j4[u] = l0 + u < hi ? min(max(labels[l0 + u], 0), k2 - 1) : 0;
+      s4[u] = T(0);
+    }
+    for (int q = lane; q < d; q += 32) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (l0 + u < hi) {
+          const T t = X[(l0 + u) * d + q] - Z[(size_t)j4[u] * d + q];
+          s4[u] = fma(t, t, s4[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T sv = warp_sum(s4[u]);
+      if (lane == 0 && l0 + u < hi) acc += (double)w[l0 + u] * (double)sv;
+    }
+  }
+  if (lane == 0) red[wi] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    part[blockIdx.x] = t;
+  }
+}
+
 // ------------------------------------------------------------- update
 
-constexpr int kUWarps = 8;
+constexpr int kUWarps = 16;
 constexpr int kUMaxPerLane = CABS_MAX_K / 32;
 
 template <typename T>
-__global__ void __launch_bounds__(256) update_kernel(const T* __restrict__ X, long long M, int d,
-                                                     const int* __restrict__ labels, const T* __restrict__ w,
-                                                     const T* __restrict__ Zcur, T* __restrict__ Znext,
-                                                     int* __restrict__ counts) {
+__device__ __forceinline__ void accumulate_members(unsigned mask, long long base, const T* __restrict__ X, int d,
+                                                   const T* __restrict__ w, int lane, T (&acc)[kUMaxPerLane], T& wsum,
+                                                   int& cnt) {
+  while (mask) {
+    long long ls[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        ls[u] = base + b;
+      } else {
+        ls[u] = -1;
+      }
+    }
+    T xv[4][kUMaxPerLane];
+    T wv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      wv[u] = ls[u] >= 0 ? w[ls[u]] : T(0);
+#pragma unroll
+      for (int s = 0; s < kUMaxPerLane; ++s) {
+        const int q = lane + 32 * s;
+        xv[u][s] = (ls[u] >= 0 && q < d) ? X[ls[u] * d + q] : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (ls[u] >= 0) {
+#pragma unroll
+        for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = fma(wv[u], xv[u][s], acc[s]);
+        wsum += wv[u];
+        ++cnt;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kUWarps * 32) update_kernel(const T* __restrict__ X, long long M, int d,
+                                                              const int* __restrict__ labels, const T* __restrict__ w,
+                                                              const T* __restrict__ Zcur, T* __restrict__ Znext,
+                                                              int* __restrict__ counts) {
   __shared__ T accs[kUWarps][CABS_MAX_K];
   __shared__ T wsums[kUWarps];
   __shared__ int cnts[kUWarps];
@@ -247,49 +319,22 @@ __global__ void __launch_bounds__(256) update_kernel(const T* __restrict__ X, lo
   for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = T(0);
   T wsum = T(0);
   int cnt = 0;
-  for (long long base = lo; base < hi; base += 32) {
-    const long long l = base + lane;
-    const int lab = l < hi ? labels[l] : -1;
-    unsigned mask = __ballot_sync(0xffffffffu, lab == j);
-    while (mask) {
-      long long ls[4];
+  // four label loads in flight per lane; members are summed in index order
+  for (long long base = lo; base < hi; base += 128) {
+    int lab[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (mask) {
-          const int b = __ffs(mask) - 1;
-          mask &= mask - 1;
-          ls[u] = base + b;
-        } else {
-          ls[u] = -1;
-        }
-      }
-      T xv[4][kUMaxPerLane];
-      T wv[4];
+    for (int u = 0; u < 4; ++u) {
+      const long long l = base + 32 * u + lane;
+      lab[u] = l < hi ? __ldg(labels + l) : -1;
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        wv[u] = ls[u] >= 0 ? w[ls[u]] : T(0);
-#pragma unroll
-        for (int s = 0; s < kUMaxPerLane; ++s) {
-          const int q = lane + 32 * s;
-          xv[u][s] = (ls[u] >= 0 && q < d) ? X[ls[u] * d + q] : T(0);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (ls[u] >= 0) {
-#pragma unroll
-          for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = fma(wv[u], xv[u][s], acc[s]);
-          wsum += wv[u];
-          ++cnt;
-        }
-      }
+    for (int u = 0; u < 4; ++u) {
+      const unsigned mask = __ballot_sync(0xffffffffu, lab[u] == j);
+      accumulate_members<T>(mask, base + 32 * u, X, d, w, lane, acc, wsum, cnt);
     }
   }
 #pragma unroll
-  for (int s = 0; s < kUMaxPerLane; ++s) {
-    const int q = lane + 32 * s;
-    if (q < CABS_MAX_K) accs[wi][q] = acc[s];
-  }
+  for (int s = 0; s < kUMaxPerLane; ++s) accs[wi][lane + 32 * s] = acc[s];
   if (lane == 0) {
     wsums[wi] = wsum;
     cnts[wi] = cnt;
@@ -344,10 +389,11 @@ struct KmWs {
   double *part_e, *energy;
 };
 
+// CTAs whose partial energies are summed: the FP64 assignment kernel's own
+// grid, else the exact-energy kernel's.
 int assign_blocks(int64_t M, int prec) {
   if (prec == CABS_PREC_FP64) return ceil_div(M, kDM);
-  if (prec == CABS_PREC_FP32) return ceil_div(M, kAM);
-  return tc_assign_blocks(M);
+  return std::max(1, std::min(ceil_div(M, 64), sm_count() * 4));
 }
 
 KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
@@ -393,11 +439,15 @@ cabs_status assign_once<float>(const float* X, int64_t M, int d, const float* Z,
                                void* tcws, cudaStream_t stream) {
   CABS_LAUNCH(stream, "centre_norms_kernel", centre_norms_kernel<float><<<ceil_div(k2, 8), 256, 0, stream>>>(Z, k2, d, zn));
   if (prec == CABS_PREC_FP32) {
-    CABS_LAUNCH(stream, "assign_f32_kernel", assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, xn, w, labels, part_e));
-    return CABS_OK;
+    CABS_LAUNCH(stream, "assign_f32_kernel",
+                assign_f32_kernel<<<ceil_div(M, kAM), 256, 0, stream>>>(X, M, d, Z, zn, k2, labels));
+  } else {
+    CABS_TRY(tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, d_recheck, prec == CABS_PREC_BF16, first, tcws,
+                              stream));
   }
-  return tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prec == CABS_PREC_BF16, first, tcws,
-                          stream);
+  CABS_LAUNCH(stream, "energy_exact_kernel",
+              energy_exact_kernel<float><<<assign_blocks(M, prec), 256, 0, stream>>>(X, M, d, Z, k2, labels, w, part_e));
+  return CABS_OK;
 }
 
 template <typename T>
@@ -423,7 +473,7 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
     int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
     CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, w.part_e + (size_t)t * nb, d_recheck,
                             t == 0, tcws, stream));
-    CABS_LAUNCH(stream, "update_kernel", update_kernel<T><<<k2, 256, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts));
+    CABS_LAUNCH(stream, "update_kernel", update_kernel<T><<<k2, kUWarps * 32, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts));
     T* tmp = Zc;
     Zc = Zn;
     Zn = tmp;

@@ -3,11 +3,13 @@
 //
 // Exact (dense A): a fused tiled pass. Each CTA forms a 64 x 64 tile of
 // A_hat = (U diag(S)) V^T from the k-wide factors in shared memory, reads the
-// same tile of A once, and accumulates sum (a - a_hat)^2 and sum a^2 in FP64.
+// same tile of A once, and accumulates sum (a - a_hat)^2 and sum a^2 (per
+// thread in the working precision, across threads in FP64).
 // A is read exactly once; A_hat is never stored.
 // Sampled (dense or implicit RBF): `samples` entries (i, j) drawn with
 // replacement from Philox key (seed, 2), counter (t, 0, 0, 0): i = hi64(w0 m),
-// j = hi64(w1 n); a_hat = sum_r U[i,r] S[r] V[j,r] in FP64.
+// j = hi64(w1 n); a_hat = sum_r U[i,r] S[r] V[j,r] in the working precision,
+// squares summed in FP64.
 // Per-CTA partial sums are added in a fixed order (deterministic).
 #include "common.cuh"
 #include "kernels.cuh"
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(256) residual_dense_kernel(const T* __restrict
     }
     __syncthreads();
   }
-  double num = 0.0, den = 0.0;
+  // T-precision sums over this thread's 16 entries, FP64 across threads
+  T tn = T(0), td = T(0);
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const long long gi = i0 + ty * 4 + x;
@@ -67,12 +70,13 @@ __global__ void __launch_bounds__(256) residual_dense_kernel(const T* __restrict
     for (int y = 0; y < 4; ++y) {
       const long long gj = j0 + tx * 4 + y;
       if (gj >= n) continue;
-      const double a = a_f64 ? ((const double*)A)[gi * lda + gj] : (double)((const float*)A)[gi * lda + gj];
-      const double dlt = a - (double)acc[x][y];
-      num = fma(dlt, dlt, num);
-      den = fma(a, a, den);
+      const T a = a_f64 ? (T)((const double*)A)[gi * lda + gj] : (T)((const float*)A)[gi * lda + gj];
+      const T dlt = a - acc[x][y];
+      tn = fma(dlt, dlt, tn);
+      td = fma(a, a, td);
     }
   }
+  double num = (double)tn, den = (double)td;
   num = warp_sum(num);
   den = warp_sum(den);
   if ((tid & 31) == 0) {
@@ -120,12 +124,13 @@ __global__ void __launch_bounds__(256) residual_sampled_kernel(cabs_source src, 
     const U64x4 r = philox4x64_10((uint64_t)t, 0, 0, 0, seed, 2);
     const long long i = (long long)mulhi64(r.v[0], (uint64_t)m);
     const long long j = (long long)mulhi64(r.v[1], (uint64_t)n);
-    const double a = entry_of<T>(src, i, j);
-    double ah = 0.0;
-    for (int c = 0; c < k; ++c) ah = fma((double)U[i * k + c] * S[c], (double)V[j * k + c], ah);
-    const double dl = a - ah;
-    num = fma(dl, dl, num);
-    den = fma(a, a, den);
+    // a_hat in the working precision (FP64 arithmetic is 1/64 of FP32 here)
+    const T a = (T)entry_of<T>(src, i, j);
+    T ah = T(0);
+    for (int c = 0; c < k; ++c) ah = fma(U[i * k + c] * (T)S[c], V[j * k + c], ah);
+    const T dl = a - ah;
+    num += (double)(dl * dl);
+    den += (double)(a * a);
   }
   num = warp_sum(num);
   den = warp_sum(den);

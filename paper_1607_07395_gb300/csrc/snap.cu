@@ -12,11 +12,12 @@
 //     8 x 8 per thread) and keeps, per centre, its 8 nearest rows of the tile.
 //  2. snap_merge_kernel: one CTA per centre merges the tile lists into the
 //     centre's global 8 nearest rows, ordered by (distance, row).
-//  3. snap_greedy_kernel: one CTA walks the centres in order; warp 0 picks the
-//     first candidate not taken (a bitmap of taken rows in shared memory);
-//     only if all 8 are taken does the whole CTA scan every row for that
-//     centre. The picks are then sorted ascending.
+//  3. snap_greedy_kernel (cooperative): CTA 0's warp 0 walks the centres in
+//     order and picks the first candidate not taken (a bitmap of taken rows);
+//     only if all 8 are taken do all CTAs scan every row for that centre.
+//     The picks are then sorted ascending.
 #include "common.cuh"
+#include "grid_sync.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
 
@@ -25,8 +26,7 @@ namespace {
 
 constexpr int kTop = 8;
 constexpr int kSM = 64, kSK = 16, kSN = 256;
-constexpr int kGreedyThreads = 1024;
-constexpr size_t kBitmapSmemLimit = 160 * 1024;
+constexpr int kGreedyThreads = 512;
 
 template <typename T>
 __device__ __forceinline__ void top_insert(T (&d)[kTop], int (&r)[kTop], T v, int row) {
@@ -179,62 +179,78 @@ __global__ void __launch_bounds__(256) snap_merge_kernel(const T* __restrict__ c
   }
 }
 
+// Cooperative greedy pass. CTA 0's warp 0 walks the centres in order and
+// takes the first candidate not taken yet; when a centre's 8 candidates are
+// all taken, every CTA scans its slice of rows for that centre (one warp per
+// row, lanes over dimensions), CTA 0 reduces the per-CTA minima in a fixed
+// order, and the walk continues. The taken-row bitmap lives in global memory.
 template <typename T>
-__global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(const T* __restrict__ X, long long M, int d,
-                                                                      const T* __restrict__ Z, int k2,
-                                                                      const int* __restrict__ top_r, int use_smem,
-                                                                      unsigned* bitmap_g, int* __restrict__ order,
-                                                                      int* __restrict__ sorted, int* fallbacks) {
-  extern __shared__ __align__(16) unsigned bm_smem[];
-  __shared__ int picks[CABS_MAX_K];
-  __shared__ int fb_j;
-  __shared__ T wd[32];
-  __shared__ int wr[32];
-  unsigned* taken = use_smem ? bm_smem : bitmap_g;
+__global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
+    const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
+    unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row, GridBarrier* bar, int* __restrict__ order,
+    int* __restrict__ sorted, int* fallbacks) {
+  __shared__ T wd[kGreedyThreads / 32];
+  __shared__ int wr[kGreedyThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
+  const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
-  for (long long e = tid; e < words; e += blockDim.x) taken[e] = 0u;
-  __syncthreads();
+  for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < words; e += (long long)G * blockDim.x)
+    taken[e] = 0u;
+  if (!grid_sync(bar, G)) return;
   int j = 0;
-  while (j < k2) {
-    if (wi == 0) {
-      // warp 0 resolves centres from its candidate lists until one needs a full scan
+  while (true) {
+    if (blockIdx.x == 0 && wi == 0) {
       int jj = j;
       for (; jj < k2; ++jj) {
         const int r = lane < kTop ? top_r[(size_t)jj * kTop + lane] : 0x7fffffff;
-        const bool ok = lane < kTop && r >= 0 && r < M && !((taken[r >> 5] >> (r & 31)) & 1u);
+        const bool ok = lane < kTop && r >= 0 && r < M && !((((volatile unsigned*)taken)[r >> 5] >> (r & 31)) & 1u);
         const unsigned good = __ballot_sync(0xffffffffu, ok);
         if (!good) break;
-        const int first = __ffs(good) - 1;
-        const int pick = __shfl_sync(0xffffffffu, r, first);
+        const int pick = __shfl_sync(0xffffffffu, r, __ffs(good) - 1);
         if (lane == 0) {
           taken[pick >> 5] |= 1u << (pick & 31);
           picks[jj] = pick;
         }
         __syncwarp();
       }
-      if (lane == 0) fb_j = jj;
+      if (lane == 0) *next_fb = jj;
     }
-    __syncthreads();
-    j = fb_j;
+    if (!grid_sync(bar, G)) return;
+    j = *(volatile int*)next_fb;
     if (j >= k2) break;
-    // full scan for centre j over the rows not taken yet
+    // every CTA: nearest untaken row of its slice for centre j
+    const long long lo = M * blockIdx.x / G, hi = M * (blockIdx.x + 1) / G;
     T best = pos_inf<T>();
     int brow = 0x7fffffff;
     const T* z = Z + (size_t)j * d;
-    for (long long l = tid; l < M; l += blockDim.x) {
-      if ((taken[l >> 5] >> (l & 31)) & 1u) continue;
-      T s = T(0);
-      for (int q = 0; q < d; ++q) {
-        const T t = X[l * d + q] - z[q];
-        s = fma(t, t, s);
+    for (long long l0 = lo + (long long)wi * 4; l0 < hi; l0 += (long long)nw * 4) {
+      bool skip[4];
+      T s4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long l = l0 + u;
+        skip[u] = l >= hi || ((((volatile unsigned*)taken)[l >> 5] >> (l & 31)) & 1u);
+        s4[u] = T(0);
       }
-      if (lex_less(s, (int)l, best, brow)) {
-        best = s;
-        brow = (int)l;
+      for (int q = lane; q < d; q += 32) {
+        const T zq = z[q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!skip[u]) {
+            const T t = X[(l0 + u) * d + q] - zq;
+            s4[u] = fma(t, t, s4[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T sv = warp_sum(s4[u]);
+        if (!skip[u] && lex_less(sv, (int)(l0 + u), best, brow)) {
+          best = sv;
+          brow = (int)(l0 + u);
+        }
       }
     }
-    warp_argmin(best, brow);
     if (lane == 0) {
       wd[wi] = best;
       wr[wi] = brow;
@@ -248,22 +264,43 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(const T* __
           bv = wd[i];
           bi = wr[i];
         }
+      cta_best[blockIdx.x] = bv;
+      cta_row[blockIdx.x] = bi;
+    }
+    if (!grid_sync(bar, G)) return;
+    if (blockIdx.x == 0 && tid == 0) {
+      T bv = cta_best[0];
+      int bi = cta_row[0];
+      for (unsigned b = 1; b < G; ++b)
+        if (lex_less(cta_best[b], cta_row[b], bv, bi)) {
+          bv = cta_best[b];
+          bi = cta_row[b];
+        }
       if (bi >= 0 && bi < M) taken[bi >> 5] |= 1u << (bi & 31);
       picks[j] = bi;
       if (fallbacks) atomicAdd(fallbacks, 1);
+      __threadfence();
     }
+    __syncthreads();  // warp 0 of CTA 0 sees the pick before it resumes
+    ++j;  // CTA 0's warp 0 resumes at the next centre; the others wait at the next barrier
+  }
+  if (blockIdx.x == 0) {
     __syncthreads();
-    ++j;
+    for (int i = tid; i < k2; i += blockDim.x) order[i] = ((volatile int*)picks)[i];
+    for (int i = tid; i < k2; i += blockDim.x) {
+      const int v = ((volatile int*)picks)[i];
+      int r = 0;
+      for (int t = 0; t < k2; ++t) r += ((volatile int*)picks)[t] < v;
+      sorted[r] = v;
+    }
   }
-  __syncthreads();
-  for (int i = tid; i < k2; i += blockDim.x) order[i] = picks[i];
-  // rank sort of the distinct picks
-  for (int i = tid; i < k2; i += blockDim.x) {
-    const int v = picks[i];
-    int r = 0;
-    for (int t = 0; t < k2; ++t) r += picks[t] < v;
-    sorted[r] = v;
-  }
+}
+
+__global__ void snap_state_init_kernel(GridBarrier* bar, int* next_fb) {
+  bar->count = 0u;
+  bar->gen = 0u;
+  bar->err = 0;
+  *next_fb = 0;
 }
 
 struct SnapWs {
@@ -272,6 +309,9 @@ struct SnapWs {
   void* top_d;
   int* top_r;
   unsigned* bitmap;
+  int *picks, *next_fb, *cta_row;
+  void* cta_best;
+  GridBarrier* bar;
 };
 
 SnapWs carve_snap(Carve& cv, int64_t M, int k2, size_t eb) {
@@ -282,6 +322,11 @@ SnapWs carve_snap(Carve& cv, int64_t M, int k2, size_t eb) {
   w.top_d = cv.take<char>((size_t)k2 * kTop * eb);
   w.top_r = cv.take<int>((size_t)k2 * kTop);
   w.bitmap = cv.take<unsigned>((size_t)(M + 31) / 32);
+  w.picks = cv.take<int>(CABS_MAX_K);
+  w.next_fb = cv.take<int>(1);
+  w.cta_row = cv.take<int>(1024);
+  w.cta_best = cv.take<char>(1024 * eb);
+  w.bar = cv.take<GridBarrier>(1);
   return w;
 }
 
@@ -301,13 +346,24 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* or
   cudaFuncSetAttribute(snap_cand_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
   CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
-  const size_t bm_bytes = (size_t)((M + 31) / 32) * 4;
-  const int use_smem = bm_bytes <= kBitmapSmemLimit;
-  const size_t gsm = use_smem ? bm_bytes : 0;
-  if (gsm > 48 * 1024)
-    cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-  CABS_LAUNCH(stream, "snap_greedy_kernel", snap_greedy_kernel<T><<<1, kGreedyThreads, gsm, stream>>>(X, M, d, Z, k2, w.top_r, use_smem, w.bitmap, order,
-                                                            sorted, fallbacks));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
+  const int G = std::max(1, std::min({(int)ceil_div(M, 2048), sm_count() * std::max(per_sm, 1), 1024}));
+  CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb));
+  const T* Xc = X;
+  const T* Zc = Z;
+  const int* topr = w.top_r;
+  unsigned* bm = w.bitmap;
+  int* picks = w.picks;
+  int* nfb = w.next_fb;
+  T* cb = (T*)w.cta_best;
+  int* cr = w.cta_row;
+  GridBarrier* bar = w.bar;
+  long long Ml = M;
+  void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &bm, &picks, &nfb, &cb, &cr, &bar, &order, &sorted, &fallbacks};
+  CABS_LAUNCH(stream, "snap_greedy_kernel",
+              cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args, 0,
+                                          stream));
   return CABS_OK;
 }
 

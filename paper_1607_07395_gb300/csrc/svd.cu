@@ -31,6 +31,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
+#include "grid_sync.cuh"
 #include "svd.cuh"
 
 namespace cg = cooperative_groups;
@@ -86,6 +87,66 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
     const float p = vx[i], q = vy[i];
     vx[i] = c * p - s * q;
     vy[i] = s * p + c * q;
+  }
+  return true;
+}
+
+// Same rotation with each lane owning R contiguous rows of a column padded to
+// 32 R entries (R a multiple of 4): the two columns are read once with
+// 16-byte loads, rotated in registers and written back once.
+template <int R>
+__device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, float* vy, int lane) {
+  float xr[R], yr[R];
+  const float4* x4 = (const float4*)(x + lane * R);
+  const float4* y4 = (const float4*)(y + lane * R);
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) {
+    const float4 a = x4[i], b = y4[i];
+    xr[4 * i] = a.x; xr[4 * i + 1] = a.y; xr[4 * i + 2] = a.z; xr[4 * i + 3] = a.w;
+    yr[4 * i] = b.x; yr[4 * i + 1] = b.y; yr[4 * i + 2] = b.z; yr[4 * i + 3] = b.w;
+  }
+  float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    a = fmaf(xr[i], xr[i], a);
+    b = fmaf(yr[i], yr[i], b);
+    g = fmaf(xr[i], yr[i], g);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    g += __shfl_xor_sync(0xffffffffu, g, off);
+  }
+  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) return false;
+  const float zeta = (b - a) / (2.f * g);
+  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  const float c = rsqrtf(fmaf(t, t, 1.f));
+  const float s = c * t;
+  float4* xo = (float4*)(x + lane * R);
+  float4* yo = (float4*)(y + lane * R);
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) {
+    float4 p, q;
+    p.x = c * xr[4 * i] - s * yr[4 * i];         q.x = s * xr[4 * i] + c * yr[4 * i];
+    p.y = c * xr[4 * i + 1] - s * yr[4 * i + 1]; q.y = s * xr[4 * i + 1] + c * yr[4 * i + 1];
+    p.z = c * xr[4 * i + 2] - s * yr[4 * i + 2]; q.z = s * xr[4 * i + 2] + c * yr[4 * i + 2];
+    p.w = c * xr[4 * i + 3] - s * yr[4 * i + 3]; q.w = s * xr[4 * i + 3] + c * yr[4 * i + 3];
+    xo[i] = p;
+    yo[i] = q;
+  }
+  float4* vxo = (float4*)(vx + lane * R);
+  float4* vyo = (float4*)(vy + lane * R);
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) {
+    const float4 p = vxo[i], q = vyo[i];
+    float4 p2, q2;
+    p2.x = c * p.x - s * q.x; q2.x = s * p.x + c * q.x;
+    p2.y = c * p.y - s * q.y; q2.y = s * p.y + c * q.y;
+    p2.z = c * p.z - s * q.z; q2.z = s * p.z + c * q.z;
+    p2.w = c * p.w - s * q.w; q2.w = s * p.w + c * q.w;
+    vxo[i] = p2;
+    vyo[i] = q2;
   }
   return true;
 }
@@ -153,15 +214,17 @@ constexpr int kClusterThreads = 512;
 // Cluster of NC CTAs; CTA c holds blocks top[c], bot[c] of b columns each.
 // Round-robin over the 2 NC blocks: block slot top[0] stays, the others move
 // one place around the circle each round.
+template <int R>
 __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const double* __restrict__ W, int k, int b,
                                                                         double* __restrict__ U0,
                                                                         double* __restrict__ V0, int* sweeps_out) {
+  constexpr int kp = 32 * R;  // padded column length
   cg::cluster_group cluster = cg::this_cluster();
   const int NC = (int)cluster.num_blocks();
   const int c = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   extern __shared__ __align__(16) float cs[];
-  const size_t blk = (size_t)b * k;  // floats per block of W (and of V)
+  const size_t blk = (size_t)b * kp;  // floats per block of W (and of V)
   // buffers[2]: each holds [W top | W bot | V top | V bot]
   float* buf0 = cs;
   float* buf1 = cs + 4 * blk;
@@ -179,9 +242,9 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
     float* w = buf0 + slot * blk;
     float* v = buf0 + (2 + slot) * blk;
     for (int e = tid; e < (int)blk; e += blockDim.x) {
-      const int j = e / k, i = e - j * k;
+      const int j = e / kp, i = e - j * kp;
       const int gc = B * b + j;
-      w[e] = gc < k ? (float)W[(size_t)i * k + gc] : 0.f;
+      w[e] = (gc < k && i < k) ? (float)W[(size_t)i * k + gc] : 0.f;
       v[e] = (gc < k && i == gc) ? 1.f : 0.f;
     }
   }
@@ -208,8 +271,8 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
             if (q >= b) continue;
             float* w = slot == 0 ? Wt : Wb;
             float* v = slot == 0 ? Vt : Vb;
-            my_rot |= rotate_pair_f32(w + (size_t)p * k, w + (size_t)q * k, v + (size_t)p * k, v + (size_t)q * k, k,
-                                      lane);
+            my_rot |= rotate_pair_reg<R>(w + (size_t)p * kp, w + (size_t)q * kp, v + (size_t)p * kp,
+                                         v + (size_t)q * kp, lane);
           }
           __syncthreads();
         }
@@ -218,8 +281,8 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
       for (int s = 0; s < b; ++s) {
         for (int j = warp; j < b; j += nwarps) {
           const int q = (j + s) % b;
-          my_rot |= rotate_pair_f32(Wt + (size_t)j * k, Wb + (size_t)q * k, Vt + (size_t)j * k, Vb + (size_t)q * k, k,
-                                    lane);
+          my_rot |= rotate_pair_reg<R>(Wt + (size_t)j * kp, Wb + (size_t)q * kp, Vt + (size_t)j * kp,
+                                       Vb + (size_t)q * kp, lane);
         }
         __syncthreads();
       }
@@ -288,7 +351,7 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   for (int slot = 0; slot < 2; ++slot) {
     for (int j = warp; j < b; j += nwarps) {
       const int gc = ids[slot] * b + j;
-      if (gc < k) emit_column(cur + slot * blk + (size_t)j * k, cur + (2 + slot) * blk + (size_t)j * k, k, gc, lane, U0, V0);
+      if (gc < k) emit_column(cur + slot * blk + (size_t)j * kp, cur + (2 + slot) * blk + (size_t)j * kp, k, gc, lane, U0, V0);
     }
   }
   if (c == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
@@ -309,40 +372,6 @@ __global__ void svd_flags_init_kernel(unsigned long long* maxoff, int iters, int
     bar->gen = 0u;
     bar->err = 0;
   }
-}
-
-// ---------------------------------------------------- grid barrier, bounded
-// All CTAs of a cooperative launch arrive on a counter; the last one bumps a
-// generation word the others wait on. The wait gives up after ~2^24 polls
-// (about a second), raising bar->err so every CTA can leave the kernel.
-
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &bar->gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    ok = 1;
-    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      bar->count = 0u;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1ll << 24) || *(volatile int*)&bar->err) {
-          atomicOr(&bar->err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
 }
 
 // One 16 x 16 tile of C = op(A) B (+ Cadd); k x k column-major; 256 threads.
@@ -705,36 +734,59 @@ SvdWs carve_svd(Carve& cv, int k) {
   return w;
 }
 
-static int cluster_size_for(int k) {
-  static int cached = -1;
-  if (cached < 0) {
-    cached = 8;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    for (int nc : {16}) {
-      const int b = (CABS_MAX_K + 2 * nc - 1) / (2 * nc);
-      const size_t smem = (size_t)8 * b * CABS_MAX_K * sizeof(float);
-      cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+#ifndef CABS_SVD_CLUSTER
+#define CABS_SVD_CLUSTER 16
+#endif
+
+template <int R>
+static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0, int* sweeps, cudaStream_t stream) {
+  static int nc = -1;  // cluster size actually schedulable on this device
+  const int want = CABS_SVD_CLUSTER;
+  auto smem_for = [&](int c) {
+    int b = (k + 2 * c - 1) / (2 * c);
+    return (size_t)8 * b * 32 * R * sizeof(float);
+  };
+  if (nc < 0) {
+    nc = 8;
+    if (want > 8) {
+      cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      const size_t sm = smem_for(want);
+      cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(nc);
+      cfg.gridDim = dim3(want);
       cfg.blockDim = dim3(kClusterThreads);
-      cfg.dynamicSmemBytes = smem;
+      cfg.dynamicSmemBytes = sm;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = nc;
+      at[0].val.clusterDim.x = want;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int clusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&clusters, svd32_cluster_kernel, &cfg) == cudaSuccess && clusters > 0)
-        cached = nc;
+      if (cudaOccupancyMaxActiveClusters(&clusters, svd32_cluster_kernel<R>, &cfg) == cudaSuccess && clusters > 0)
+        nc = want;
       cudaGetLastError();
     }
   }
-  (void)k;
-  return cached;
+  const int b = (k + 2 * nc - 1) / (2 * nc);
+  const size_t smem = smem_for(nc);
+  cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CABS_LAUNCH(stream, "svd32_cluster_kernel", cudaLaunchKernelEx(&cfg, svd32_cluster_kernel<R>, W, k, b, U0, V0, sweeps));
+  return CABS_OK;
 }
 
 cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
@@ -746,27 +798,10 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
       cudaFuncSetAttribute(svd32_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     CABS_LAUNCH(stream, "svd32_cta_kernel",
                 svd32_cta_kernel<<<1, 512, smem, stream>>>(W, k, w.U[0], w.V[0], sweeps));
+  } else if (k <= 128) {
+    CABS_TRY(launch_cluster<4>(W, k, w.U[0], w.V[0], sweeps, stream));
   } else {
-    const int nc = cluster_size_for(k);
-    int b = (k + 2 * nc - 1) / (2 * nc);
-    b = (b + 3) & ~3;  // float4 block copies
-    const size_t smem = (size_t)8 * b * k * sizeof(float);
-    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(svd32_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nc);
-    cfg.blockDim = dim3(kClusterThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = nc;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    CABS_LAUNCH(stream, "svd32_cluster_kernel",
-                cudaLaunchKernelEx(&cfg, svd32_cluster_kernel, W, k, b, w.U[0], w.V[0], sweeps));
+    CABS_TRY(launch_cluster<8>(W, k, w.U[0], w.V[0], sweeps, stream));
   }
   // ---- Phase B: FP64 refinement, one cooperative launch
   CABS_LAUNCH(stream, "svd_flags_init",

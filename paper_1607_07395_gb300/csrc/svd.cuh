@@ -2,15 +2,9 @@
 #pragma once
 
 #include "common.cuh"
+#include "grid_sync.cuh"
 
 namespace cabs {
-
-// Grid barrier state for cooperative kernels (zeroed before each launch).
-struct GridBarrier {
-  unsigned count;
-  unsigned gen;
-  int err;
-};
 
 struct SvdWs {
   double *U[2], *V[2];                 // column-major iterates

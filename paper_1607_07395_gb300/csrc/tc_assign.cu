@@ -10,10 +10,10 @@
 // |z|^2 - 2 x . z, keeping the best and second-best centre; warps holding
 // the two column halves of a row merge through shared memory. When the two
 // best are closer than the rounding bound of the operands
-// (2^-6 |x| (|z_a| + |z_b|) for BF16, 2^-8 for TF32), both distances are
+// (1.25 * 4u |x| (|z_a| + |z_b|), u = 2^-9 for BF16, 2^-12 for TF32), both distances are
 // recomputed in FP32 by direct differences and the smaller wins (ties to the
-// lower centre index). The weighted encoding error uses the winner's direct
-// FP32 distance and is summed per CTA in FP64.
+// lower centre index). The weighted encoding error is computed afterwards by
+// a separate pass with direct differences (k-means kernel file).
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -47,13 +47,23 @@ __global__ void to_operand_kernel(const float* __restrict__ X, long long rows, i
   }
 }
 
+// FP32 squared distance by direct differences, four independent partial sums.
 __device__ __forceinline__ float direct_dist(const float* __restrict__ x, const float* __restrict__ z, int d) {
-  float s = 0.f;
-  for (int q = 0; q < d; ++q) {
-    const float t = x[q] - z[q];
-    s = fmaf(t, t, s);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int q = 0;
+  for (; q + 4 <= d; q += 4) {
+    const float t0 = __ldg(x + q) - __ldg(z + q), t1 = __ldg(x + q + 1) - __ldg(z + q + 1);
+    const float t2 = __ldg(x + q + 2) - __ldg(z + q + 2), t3 = __ldg(x + q + 3) - __ldg(z + q + 3);
+    s0 = fmaf(t0, t0, s0);
+    s1 = fmaf(t1, t1, s1);
+    s2 = fmaf(t2, t2, s2);
+    s3 = fmaf(t3, t3, s3);
   }
-  return s;
+  for (; q < d; ++q) {
+    const float t = __ldg(x + q) - __ldg(z + q);
+    s0 = fmaf(t, t, s0);
+  }
+  return (s0 + s1) + (s2 + s3);
 }
 
 struct Best2 {
@@ -78,11 +88,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_assign_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const float* __restrict__ zn, const float* __restrict__ xn, const float* __restrict__ w,
                      const float* __restrict__ X, const float* __restrict__ Z, int d, int M, int k2, int nch,
-                     int units, int* __restrict__ labels, double* __restrict__ part_e, int* rechecks, int* err) {
+                     int units, int* __restrict__ labels, int* rechecks, int* err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ tc::Barriers bars;
   __shared__ Best2 xchg[4][32];
-  __shared__ double red[tc::kEpiWarps];
   uint8_t *Bres, *Aring;
   tc::setup<kBN>(smem_raw, nch, Bres, Aring, &bars);
   const int MT = units;  // one column block: every unit is a row tile
@@ -101,8 +110,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const int e = warp - tc::kEpiWarp0;
     const int sub = warp & 3, half = e >> 2;
     const int row = sub * 32 + lane;
-    const float rel = kTF32 ? 0.00390625f : 0.015625f;  // 2^-8 (TF32), 2^-6 (BF16)
-    double esum = 0.0;
+    // |error of |z|^2 - 2 x.z| <= 4 u |x| |z| for operand rounding u (2^-9 BF16,
+    // 2^-12 TF32); a 1.25x margin covers the FP32 accumulation
+    const float rel = kTF32 ? 0.0012207f : 0.0097656f;
     int nre = 0;
     int ab = 0;
     uint32_t accph[2] = {0, 0};
@@ -161,28 +171,16 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
               }
             }
           }
-          labels[l] = bj;
-          // the energy uses the winner's distance by direct differences (the
-          // expansion form loses relative accuracy when the distance is small)
           (void)best;
-          esum += (double)w[l] * (double)direct_dist(X + l * d, Z + (size_t)bj * d, d);
+          labels[l] = bj;
         }
       }
       asm volatile("bar.sync 1, %0;" ::"n"(tc::kEpiWarps * 32));
     }
-    esum = warp_sum(esum);
     nre = warp_sum(nre);
-    if (lane == 0) {
-      red[e] = esum;
-      if (nre && rechecks) atomicAdd(rechecks, nre);
-    }
+    if (lane == 0 && nre && rechecks) atomicAdd(rechecks, nre);
   }
   tc::teardown<kBN>(&bars, err);
-  if (threadIdx.x == 0) {
-    double sacc = 0.0;
-    for (int i = 0; i < tc::kEpiWarps; ++i) sacc += red[i];
-    part_e[blockIdx.x] = (err && *err) ? __longlong_as_double(0x7ff8000000000000ll) : sacc;
-  }
 }
 
 struct TcWs {
@@ -207,7 +205,7 @@ TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
 
 template <bool kTF32>
 cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2, const float* xn,
-                            const float* w, int* labels, double* part_e, int* d_recheck, bool prep_points, void* tcws,
+                            const float* w, int* labels, int* d_recheck, bool prep_points, void* tcws,
                             cudaStream_t stream) {
   Carve cv(tcws, (size_t)-1);
   TcWs t = carve_tc(cv, M, d, k2, kTF32);
@@ -236,7 +234,7 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
   cudaFuncSetAttribute(tc_assign_kernel<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   CABS_LAUNCH(stream, "tc_assign_kernel",
               tc_assign_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(
-                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, part_e, d_recheck, t.err));
+                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, d_recheck, t.err));
   return CABS_OK;
 }
 
@@ -250,11 +248,10 @@ void tc_assign_carve(Carve& cv, int64_t M, int d, int k2) {
 }
 
 cabs_status tc_assign_launch(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2,
-                             const float* xn, const float* w, int* labels, double* part_e, int* d_recheck, bool bf16,
+                             const float* xn, const float* w, int* labels, int* d_recheck, bool bf16,
                              bool prep_points, void* tcws, cudaStream_t stream) {
-  if (bf16)
-    return tc_assign_typed<false>(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prep_points, tcws, stream);
-  return tc_assign_typed<true>(X, M, d, Z, zn, k2, xn, w, labels, part_e, d_recheck, prep_points, tcws, stream);
+  if (bf16) return tc_assign_typed<false>(X, M, d, Z, zn, k2, xn, w, labels, d_recheck, prep_points, tcws, stream);
+  return tc_assign_typed<true>(X, M, d, Z, zn, k2, xn, w, labels, d_recheck, prep_points, tcws, stream);
 }
 
 }  // namespace cabs

@@ -6,16 +6,16 @@
 
 namespace cabs {
 
-// CTAs of the assignment grid for M points (size of the energy partials).
+// CTAs of the assignment grid for M points.
 int tc_assign_blocks(int64_t M);
 // Extra workspace (operand copies, re-check flags) carved after the FP32 k-means slices.
 void tc_assign_carve(Carve& cv, int64_t M, int d, int k2);
 // labels[l] = argmin_j |z_j|^2 - 2 x_l.z_j with the contraction on tensor cores;
 // rows whose two best distances are within the operand rounding bound are
-// recomputed in FP32. part_e[cta] = sum of w_l |x_l - z_s(l)|^2 over its rows.
+// recomputed in FP32 (counted in *d_recheck).
 // prep_points: convert the points to the operand format (once per k-means run).
 cabs_status tc_assign_launch(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2,
-                             const float* xn, const float* w, int* labels, double* part_e, int* d_recheck, bool bf16,
+                             const float* xn, const float* w, int* labels, int* d_recheck, bool bf16,
                              bool prep_points, void* tcws, cudaStream_t stream);
 
 }  // namespace cabs

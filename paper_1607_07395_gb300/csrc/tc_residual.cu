@@ -6,7 +6,8 @@
 // with zeros to a multiple of the 128-byte swizzle width) are staged by TMA,
 // a 128 x 256 (BF16) or 128 x 128 (TF32) tile of A_hat accumulates in TMEM,
 // and the epilogue warps read it back with tcgen05.ld while they stream the
-// same tile of A from HBM once, summing (a - a_hat)^2 and a^2 in FP64. A_hat
+// same tile of A from HBM once, summing (a - a_hat)^2 and a^2 (FP32 within a
+// tile, FP64 across tiles: FP64 runs at 1/64 of the FP32 rate here). A_hat
 // is never written. A CTA keeps one column block of V resident and walks the
 // row tiles of that block, so V is read from L2 once per CTA and U diag(S)
 // once per column block. Per-CTA sums are added in a fixed order.
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       const long long gi = (long long)rt * tc::kBM + row;
       const bool row_ok = gi < m;
       const float* arow = Amat + (row_ok ? gi : 0) * lda;
+      float tn = 0.f, td = 0.f;  // FP32 within a tile (<= 128 terms), FP64 across tiles
 #pragma unroll 1
       for (int j = 0; j < BN / 2 / 32; ++j) {
         const int c0 = half * (BN / 2) + j * 32;
@@ -114,14 +116,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             if (gc0 + q < n) {
-              const double ad = (double)a[q];
-              const double dl = ad - (double)v[q];
-              num = fma(dl, dl, num);
-              den = fma(ad, ad, den);
+              const float dl = a[q] - v[q];
+              tn = fmaf(dl, dl, tn);
+              td = fmaf(a[q], a[q], td);
             }
           }
         }
       }
+      num += (double)tn;
+      den += (double)td;
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bars.accempty[ab]);
