@@ -90,30 +90,45 @@ def make_source(cabs, wl, inp):
 # ------------------------------------------------------- algorithmic units
 
 def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps):
-    """(bound, per-step algorithmic amount, unit, launches per step) of a kernel."""
+    """(bound, algorithmic amount per step, unit, launches per step) of a kernel.
+
+    Per-unit figures: gathers read one 32-byte DRAM sector per scattered
+    element of C plus the coalesced row reads, and write C and Rt; the exact
+    residual reads A once (m n 4 bytes); contractions count 2 flops per
+    multiply-add (k-means: 2 (m + n) k^2 per iteration; extrapolation
+    2 (m + n) k^2 per round; snap candidates 3 (m + n) k^2); the FP32 Jacobi
+    sweep counts 18 k flops per column pair."""
     m, n = wl["m"], wl["n"]
     d = k
+    kp = (k + 63) // 64 * 64
     if name == "residual_dense_kernel":
         return "alu", 2.0 * m * n * k, "TFLOP/s", 1
+    if name == "tc_residual_kernel":
+        return "hbm", float(m) * n * 4, "GB/s", 1
     if name == "gather_cols_kernel":
-        # one 32-byte DRAM sector per scattered element + the coalesced C write
         return "hbm", 2 * m * k * (32 + elem_bytes), "GB/s", 2
     if name == "gather_rows_t_kernel":
         return "hbm", 2 * 2 * n * k * elem_bytes, "GB/s", 2
+    if name in ("svd32_cluster_kernel", "svd32_cta_kernel"):
+        fl = sum(s * (k * (k - 1) / 2) * 18.0 * k for s in svd_sweeps)
+        return "alu", fl, "TFLOP/s", 2
     if name == "svd_jacobi_kernel":
         fl = sum(s * (k * (k - 1) / 2) * 18.0 * k for s in svd_sweeps)
         return "alu", fl, "TFLOP/s", 2
-    if name in ("assign_f32_kernel", "assign_f64_kernel", "tc_assign_kernel"):
-        return ("tensor" if name == "tc_assign_kernel" else "alu"), iters * 2.0 * (m + n) * k * d, "TFLOP/s", 2 * iters
+    if name in ("assign_f32_kernel", "assign_f64_kernel"):
+        return "alu", iters * 2.0 * (m + n) * k * d, "TFLOP/s", 2 * iters
+    if name == "tc_assign_kernel":
+        return "tensor", iters * 2.0 * (m + n) * k * kp, "TFLOP/s", 2 * iters
     if name == "snap_cand_kernel":
         return "alu", 3.0 * (m + n) * k * d, "TFLOP/s", 2
-    if name == "extrap_gemm_kernel":
-        return "alu", 2 * 2.0 * (m + n) * k * k, "TFLOP/s", 4
-    if name == "rbf_block_kernel(C)" or name == "rbf_block_kernel(Rt)":
+    if name.startswith("extrap_gemm_kernel"):
+        side = m if "C V_w" in name else n
+        return "alu", 2 * 2.0 * side * k * k, "TFLOP/s", 2
+    if name in ("rbf_block_kernel(C)", "rbf_block_kernel(Rt)"):
         side = m if name.endswith("(C)") else n
         return "alu", 2 * side * k * (3.0 * wl.get("d", 16) + 20), "TFLOP/s", 2
     if name == "update_kernel":
-        return "hbm", iters * k * 0 + iters * (m + n) * d * elem_bytes, "GB/s", 2 * iters
+        return "hbm", iters * (m + n) * d * elem_bytes, "GB/s", 2 * iters
     return None
 
 
@@ -136,7 +151,8 @@ def roofline(prof, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec):
         peak = peaks["bf16_tflops_sustained"] if prec == "bf16" else peaks["bf16_tflops_sustained"] / 2
         src = peaks["source"] + (" bf16 sustained" if prec == "bf16" else " bf16 sustained / 2 (tf32 nominal ratio)")
     else:
-        peak = FP64_PEAK_TFLOPS if (name == "svd_jacobi_kernel" or prec == "fp64") else FP32_PEAK_TFLOPS
+        fp64 = name in ("svd_jacobi_kernel", "refine_persistent_kernel") or (prec == "fp64" and not name.startswith("svd32"))
+        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         src = "derived from unit counts x 2.07 GHz"
     return dict(kernel=name, bound=bound, achieved=round(achieved, 4), peak=round(peak, 3), unit=unit,
                 frac=round(achieved / peak, 5), traffic=None, peak_source=src,

@@ -10,9 +10,9 @@
 // |z|^2 - 2 x . z, keeping the best and second-best centre; warps holding
 // the two column halves of a row merge through shared memory. When the two
 // best are closer than the rounding bound of the operands
-// (1.25 * 4u |x| (|z_a| + |z_b|), u = 2^-9 for BF16, 2^-12 for TF32), both distances are
-// recomputed in FP32 by direct differences and the smaller wins (ties to the
-// lower centre index). The weighted encoding error is computed afterwards by
+// (1.25 * 4u |x| (|z_a| + |z_b|), u = 2^-9 for BF16, 2^-12 for TF32), the
+// row is flagged and a separate coalesced pass recomputes both distances in
+// FP32 by direct differences; the smaller wins (ties to the lower index). The weighted encoding error is computed afterwards by
 // a separate pass with direct differences (k-means kernel file).
 #include <cuda_bf16.h>
 
@@ -47,25 +47,6 @@ __global__ void to_operand_kernel(const float* __restrict__ X, long long rows, i
   }
 }
 
-// FP32 squared distance by direct differences, four independent partial sums.
-__device__ __forceinline__ float direct_dist(const float* __restrict__ x, const float* __restrict__ z, int d) {
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int q = 0;
-  for (; q + 4 <= d; q += 4) {
-    const float t0 = __ldg(x + q) - __ldg(z + q), t1 = __ldg(x + q + 1) - __ldg(z + q + 1);
-    const float t2 = __ldg(x + q + 2) - __ldg(z + q + 2), t3 = __ldg(x + q + 3) - __ldg(z + q + 3);
-    s0 = fmaf(t0, t0, s0);
-    s1 = fmaf(t1, t1, s1);
-    s2 = fmaf(t2, t2, s2);
-    s3 = fmaf(t3, t3, s3);
-  }
-  for (; q < d; ++q) {
-    const float t = __ldg(x + q) - __ldg(z + q);
-    s0 = fmaf(t, t, s0);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
 struct Best2 {
   float b1, b2;
   int j1, j2;
@@ -88,7 +69,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_assign_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const float* __restrict__ zn, const float* __restrict__ xn, const float* __restrict__ w,
                      const float* __restrict__ X, const float* __restrict__ Z, int d, int M, int k2, int nch,
-                     int units, int* __restrict__ labels, int* rechecks, int* err) {
+                     int units, int* __restrict__ labels, int* __restrict__ alt, int* err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ tc::Barriers bars;
   __shared__ Best2 xchg[4][32];
@@ -113,7 +94,6 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     // |error of |z|^2 - 2 x.z| <= 4 u |x| |z| for operand rounding u (2^-9 BF16,
     // 2^-12 TF32); a 1.25x margin covers the FP32 accumulation
     const float rel = kTF32 ? 0.0012207f : 0.0097656f;
-    int nre = 0;
     int ab = 0;
     uint32_t accph[2] = {0, 0};
     for (int u = u0; u < u1; ++u) {
@@ -154,38 +134,64 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         best2_push(s, o.b2, o.j2);
         const long long l = (long long)u * tc::kBM + row;
         if (l < M) {
-          const float xl = xn[l];
-          float best = s.b1;
-          int bj = s.j1;
+          int a2 = -1;
           if (s.j2 < k2) {
+            const float xl = xn[l];
             const float bound = rel * sqrtf(fmaxf(xl, 0.f)) * (sqrtf(fmaxf(zn[s.j1], 0.f)) + sqrtf(fmaxf(zn[s.j2], 0.f)));
-            if (s.b2 - s.b1 <= bound) {
-              const float d1 = direct_dist(X + l * d, Z + (size_t)s.j1 * d, d);
-              const float d2 = direct_dist(X + l * d, Z + (size_t)s.j2 * d, d);
-              ++nre;
-              if (d2 < d1 || (d2 == d1 && s.j2 < s.j1)) {
-                bj = s.j2;
-                best = d2 - xl;
-              } else {
-                best = d1 - xl;
-              }
-            }
+            if (s.b2 - s.b1 <= bound) a2 = s.j2;
           }
-          (void)best;
-          labels[l] = bj;
+          labels[l] = s.j1;
+          alt[l] = a2;
         }
       }
       asm volatile("bar.sync 1, %0;" ::"n"(tc::kEpiWarps * 32));
     }
-    nre = warp_sum(nre);
-    if (lane == 0 && nre && rechecks) atomicAdd(rechecks, nre);
   }
   tc::teardown<kBN>(&bars, err);
 }
 
+// Rows whose two best centres were closer than the operand rounding bound:
+// both distances again in FP32 by direct differences (one warp per row, lanes
+// over dimensions, coalesced); the smaller wins, ties to the lower index.
+__global__ void __launch_bounds__(256) assign_resolve_kernel(const float* __restrict__ X, long long M, int d,
+                                                             const float* __restrict__ Z, int* __restrict__ labels,
+                                                             const int* __restrict__ alt, int* rechecks) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  int nre = 0;
+  for (long long base = warp * 32; base < M; base += nwarps * 32) {
+    const long long l = base + lane;
+    const int a2 = l < M ? alt[l] : -1;
+    unsigned mask = __ballot_sync(0xffffffffu, a2 >= 0);
+    while (mask) {
+      const int b = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const long long r = base + b;
+      const int j1 = __shfl_sync(0xffffffffu, l < M ? labels[l] : 0, b);
+      const int j2 = __shfl_sync(0xffffffffu, a2, b);
+      float s1 = 0.f, s2 = 0.f;
+      for (int q = lane; q < d; q += 32) {
+        const float x = __ldg(X + r * d + q);
+        const float t1 = x - __ldg(Z + (size_t)j1 * d + q);
+        const float t2 = x - __ldg(Z + (size_t)j2 * d + q);
+        s1 = fmaf(t1, t1, s1);
+        s2 = fmaf(t2, t2, s2);
+      }
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        ++nre;
+        if (s2 < s1 || (s2 == s1 && j2 < j1)) labels[r] = j2;
+      }
+    }
+  }
+  if (lane == 0 && nre && rechecks) atomicAdd(rechecks, nre);
+}
+
 struct TcWs {
   void *Pp, *Zp;
-  int* err;
+  int *alt, *err;
 };
 
 int kp_of(int d, bool tf32) {
@@ -199,6 +205,7 @@ TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
   TcWs w;
   w.Pp = cv.take<char>((size_t)M * Kp * es);
   w.Zp = cv.take<char>((size_t)kBN * Kp * es);
+  w.alt = cv.take<int>(M);
   w.err = cv.take<int>(1);
   return w;
 }
@@ -234,7 +241,10 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
   cudaFuncSetAttribute(tc_assign_kernel<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   CABS_LAUNCH(stream, "tc_assign_kernel",
               tc_assign_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(
-                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, d_recheck, t.err));
+                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, t.alt, t.err));
+  CABS_LAUNCH(stream, "assign_resolve_kernel",
+              assign_resolve_kernel<<<std::max(1, std::min(ceil_div(M, 256), sms * 8)), 256, 0, stream>>>(
+                  X, M, d, Z, labels, t.alt, d_recheck));
   return CABS_OK;
 }
 

@@ -91,34 +91,41 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       const bool row_ok = gi < m;
       const float* arow = Amat + (row_ok ? gi : 0) * lda;
       float tn = 0.f, td = 0.f;  // FP32 within a tile (<= 128 terms), FP64 across tiles
-#pragma unroll 1
-      for (int j = 0; j < BN / 2 / 32; ++j) {
-        const int c0 = half * (BN / 2) + j * 32;
-        const long long gc0 = (long long)cb * BN + c0;
-        float a[32];
+      constexpr int NJ = BN / 2 / 32;
+      float a[2][32];
+      auto load_chunk = [&](int j, float (&dst)[32]) {
+        const long long gc0 = (long long)cb * BN + half * (BN / 2) + j * 32;
         if (row_ok && vec && gc0 + 32 <= n) {
           const float4* p4 = (const float4*)(arow + gc0);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float4 t = __ldg(p4 + q);
-            a[4 * q] = t.x;
-            a[4 * q + 1] = t.y;
-            a[4 * q + 2] = t.z;
-            a[4 * q + 3] = t.w;
+            dst[4 * q] = t.x;
+            dst[4 * q + 1] = t.y;
+            dst[4 * q + 2] = t.z;
+            dst[4 * q + 3] = t.w;
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) a[q] = (row_ok && gc0 + q < n) ? __ldg(arow + gc0 + q) : 0.f;
+          for (int q = 0; q < 32; ++q) dst[q] = (row_ok && gc0 + q < n) ? __ldg(arow + gc0 + q) : 0.f;
         }
+      };
+      load_chunk(0, a[0]);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (j + 1 < NJ) load_chunk(j + 1, a[(j + 1) & 1]);  // next chunk's loads in flight
+        const int c0 = half * (BN / 2) + j * 32;
+        const long long gc0 = (long long)cb * BN + c0;
         float v[32];
         tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * BN + c0) + ((uint32_t)(sub * 32) << 16), v);
         if (row_ok) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             if (gc0 + q < n) {
-              const float dl = a[q] - v[q];
+              const float x = a[j & 1][q];
+              const float dl = x - v[q];
               tn = fmaf(dl, dl, tn);
-              td = fmaf(a[q], a[q], td);
+              td = fmaf(x, x, td);
             }
           }
         }
