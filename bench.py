@@ -1,12 +1,21 @@
-"""Benchmark of the CABS hot path (one sketch + its error per step) on GB300.
+"""Benchmark of the CABS hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cabs|reference]
-                    [--workload dense|rbf|plain] [--prec fp32|tf32|bf16|fp64]
+                    [--workload dense|rbf|plain] [--prec bf16|tf32|fp32|fp64]
+                    [--form batched|plain] [--batch B] [--lanes L]
 
-A step is one pass of the whole hot path over one synthetic input: pilot
+One sketch is one pass of the whole hot path over one synthetic input: pilot
 draw, gathers, FP64 core, embeddings, weighted k-means on both sides, snap,
 follow-up gather and core (Algorithm 2), then the relative Frobenius error
 (exact for dense inputs, 10^6 sampled entries for the implicit RBF matrix).
+
+A step is B independent sketches of the same matrix (seeds differ) and their
+errors. The default (batched) form enqueues them over L streams as one
+captured CUDA graph, so that one sketch's narrow phases (the core SVD runs on
+one thread-block cluster) overlap another's bandwidth-bound ones; --form plain
+runs one sketch per step. The same line also carries the plain FP32 form (one
+sketch at a time, no graph) for comparison.
+
 Inputs are resident in HBM before the timed region; the dense workload's A
 (8 GiB) is larger than L2, so no flush is needed between steps.
 
@@ -71,14 +80,59 @@ def make_inputs(wl, device, seed=1607):
 
     from workloads import synth
     if wl["kind"] == "dense":
-        A, _, _, _ = synth.decaying_lowrank_device(wl["m"], wl["n"], rank=wl["rank"], seed=seed, device=device)
-        return dict(A=A)
+        A, U, sv, V = synth.decaying_lowrank_device(wl["m"], wl["n"], rank=wl["rank"], seed=seed, device=device)
+        return dict(A=A, L=(U, sv, V))
     if wl["kind"] == "rbf":
         X, Y, sig = synth.rbf_mixture(wl["m"], wl["n"], d=wl["d"], seed=seed)
         return dict(X=torch.from_numpy(X).to(device), Y=torch.from_numpy(Y).to(device), sigma=float(sig),
                     X_host=X, Y_host=Y)
     A = synth.plain_lowrank(wl["m"], wl["n"], seed=seed)
     return dict(A=torch.from_numpy(np.ascontiguousarray(A)).to(device))
+
+
+def noiseless_error(L, sk):
+    """|L - U_bar S_bar V_bar^T|_F / |L|_F against the noiseless part L = U_L diag(s) V_L^T
+    of the dense input, by k x k algebra in FP64 (U_L, V_L orthonormal):
+    <L, X> = sum_ab s_a (U_L^T U_bar)_ab S_b (V_L^T V_bar)_ab,
+    |X|^2 = sum_bc S_b S_c (U_bar^T U_bar)_bc (V_bar^T V_bar)_bc. A diagnostic outside
+    the timed region (torch arithmetic, not the product path)."""
+    import torch
+    UL, s, VL = L
+    U, S, V = sk.U.double(), sk.S.double(), sk.V.double()
+    M1, M2 = UL.T @ U, VL.T @ V
+    lx = ((s[:, None] * M1) * (M2 * S[None, :])).sum()
+    xx = (S[:, None] * (U.T @ U) * S[None, :] * (V.T @ V)).sum()
+    ll = (s * s).sum()
+    return float(torch.sqrt(torch.clamp(ll - 2 * lx + xx, min=0.0) / ll))
+
+
+def precision_excess(cabs, ctx, wl, device):
+    """Relative error of each precision mode on the oracle-sized slice of the
+    workload (same recipe and seed as the CPU baseline's first oracle step), and
+    its relative excess over the FP64 mode (which matches the oracle to 1e-10)."""
+    import numpy as np
+    import torch
+
+    from workloads import synth
+    s = cpu_sample(wl)
+    if wl["kind"] == "dense":
+        A = synth.decaying_lowrank_host(s["m"], s["n"], rank=wl["rank"], seed=1607)[0]
+        src = cabs.dense_source(torch.from_numpy(A).to(device))
+        samples = 0
+    else:
+        X, Y, sig = synth.rbf_mixture(s["m"], s["n"], d=wl["d"], seed=1607)
+        src = cabs.rbf_source(torch.from_numpy(X).to(device), torch.from_numpy(Y).to(device), sig)
+        samples = s["samples"]
+    errs = {}
+    for prec in ("fp64", "fp32", "tf32", "bf16"):
+        p = cabs.make_params(s["m"], s["n"], s["k"], iters=s["iters"], seed=1607, prec=prec, core=wl["core"],
+                             err_samples=samples, err_seed=3)
+        sk = cabs.cabs_sketch(ctx, src, p)
+        errs[prec] = float(sk.err.cpu().item())
+    torch.cuda.synchronize()
+    return dict(slice=f"{s['m']}x{s['n']}, k={s['k']}, c={s['iters']}, seed 1607", errors=errs,
+                excess_over_fp64={p_: errs[p_] / errs["fp64"] - 1.0 for p_ in ("fp32", "tf32", "bf16")},
+                bar=1e-3)
 
 
 def make_source(cabs, wl, inp):
@@ -178,10 +232,18 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the first sample marks the sampler as running; the timed region starts after it
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.lines_before = sum(1 for _ in open(self.path))
 
     def stop(self):
         if not self.proc:
@@ -192,7 +254,9 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         rows = []
-        for ln in open(self.path):
+        for i, ln in enumerate(open(self.path)):
+            if i < getattr(self, "lines_before", 0):
+                continue
             p = [x.strip() for x in ln.split(",")]
             if len(p) >= 9:
                 rows.append(p)
@@ -208,6 +272,9 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- CPU oracle
+
+CPU_BUDGET_S = 90.0  # wall-clock cap on the oracle repeats of one baseline
+
 
 def cpu_sample(wl):
     """The bounded oracle sample of a workload and how to scale its time.
@@ -246,7 +313,10 @@ def cpu_worker(workload, steps):
         A = synth.plain_lowrank(s["m"], s["n"], seed=1607)
         src = o.DenseSource(A)
     times = []
+    start = time.perf_counter()
     for step in range(steps):
+        if step > 0 and time.perf_counter() - start > CPU_BUDGET_S:
+            break  # bounded: the remaining repeats would not change the median much
         t0 = time.perf_counter()
         r = o.cabs(src, s["k"], iters=s["iters"], seed=1607 + step, mode=wl["core"])
         t1 = time.perf_counter()
@@ -256,7 +326,9 @@ def cpu_worker(workload, steps):
             err = o.rel_fro_error_dense(src.A, r.final.U, r.final.S, r.final.V)
         t2 = time.perf_counter()
         times.append((t1 - t0) * s["scale_sketch"] + (t2 - t1) * s["scale_err"])
-    print(json.dumps(dict(times=times, err=err, sample=s)))
+        if step == 0:
+            err0 = err
+    print(json.dumps(dict(times=times, err=err, err0=err0, sample=s)))
 
 
 def run_cpu_baseline(workload, steps):
@@ -271,10 +343,31 @@ def run_cpu_baseline(workload, steps):
     desc = (f"oracle on the same recipe at {s['m']}x{s['n']}, k={s['k']}, c={s['iters']}; sketch time x"
             f"{s['scale_sketch']:.3g} (m+n), error time x{s['scale_err']:.3g}; median of {len(res['times'])}")
     return dict(value=1.0 / per, unit="sketches/s", cores=1, kind="oracle", sample=desc,
-                seconds_per_sketch_extrapolated=per)
+                seconds_per_sketch_extrapolated=per, oracle_error=res.get("err0"))
 
 
 # --------------------------------------------------------------- GPU arm
+
+def timed_steps(ctx, cabs, step, steps, stream, world, barrier):
+    """Runs `steps` steps between barriers; returns (per-step ms, total ms max over ranks, errors)."""
+    import torch
+    import torch.distributed as dist
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    errs = []
+    for i in range(steps):
+        errs.append(step())
+        ev[i + 1].record(stream)
+    barrier()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return per_step, total, errs
+
 
 def run_cabs(args):
     import torch
@@ -286,63 +379,89 @@ def run_cabs(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local)) if "device_id" in \
-            dist.init_process_group.__code__.co_varnames else dist.init_process_group("nccl")
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    wl = WORKLOADS[args.workload]
-    prec = "fp64" if args.workload == "plain" else args.prec
+    wl = dict(WORKLOADS[args.workload])
+    if args.m or args.n:
+        # smaller shapes of the same recipe, for profiler captures
+        wl["m"], wl["n"] = args.m or wl["m"], args.n or wl["n"]
+        wl["desc"] += f" (shape overridden to {wl['m']}x{wl['n']})"
     k, iters = wl["k"], wl["iters"]
     ctx = cabs.Context(local)
     inp = make_inputs(wl, device, seed=1607 + rank)
     src = make_source(cabs, wl, inp)
-    p = cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank, prec=prec, core=wl["core"])
-    ws = torch.empty(cabs.cabs_workspace_size(src, p) + 512, dtype=torch.uint8, device=device)
-    out = cabs.alloc_result(p, device)
     samples = wl.get("samples", 0)
-    stream = torch.cuda.current_stream()
-
-    def step():
-        sk = cabs.cabs_sketch(ctx, src, p, ws=ws, out=out, stream=stream)
-        return cabs.cabs_error(ctx, src, p, sk, samples=samples, seed=3, stream=stream)
-
-    for _ in range(args.warmup):
-        err = step()
-    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=device)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---- the chosen form: B concurrent sketches per step in reduced precision,
+    # launched as one captured graph over `lanes` streams, plus each error
+    prec = "fp64" if args.workload == "plain" else args.prec
+    B = 1 if args.form == "plain" else args.batch
+    params = [cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank * 1000 + b, prec=prec,
+                               core=wl["core"], err_samples=samples, err_seed=3) for b in range(B)]
+    srcs = [src] * B
+    outs = [cabs.alloc_result(p, device) for p in params]
+    offs, tot = cabs.batched_layout(srcs, params)
+    ws = torch.empty(tot + 512, dtype=torch.uint8, device=device)
+
+    def run_batch(lanes, use_graph):
+        # every sketch computes its own relative error (CABS_FLAG_ERROR) on its
+        # lane; the B errors are read back to the host once per step
+        with torch.cuda.stream(stream):
+            if B == 1:
+                cabs.cabs_sketch(ctx, src, params[0], ws=ws, out=outs[0], stream=stream)
+            else:
+                cabs.cabs_sketch_batched(ctx, srcs, params, outs, ws, offs, lanes=lanes, use_graph=use_graph,
+                                         stream=stream)
+            return torch.cat([o.err for o in outs]).cpu().tolist()
+
+    def step():
+        return run_batch(args.lanes, True)
+
+    for _ in range(args.warmup):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if args.steps <= 0:
+        # about two seconds of timed work (enough clock samples), 5 to 2000 steps
+        est = max(e0.elapsed_time(e1), 1e-3) if args.warmup > 0 else 50.0
+        args.steps = int(min(2000, max(5, math.ceil(2000.0 / est))))
+        if world > 1:
+            t = torch.tensor([args.steps], dtype=torch.int64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            args.steps = int(t.item())
     sampler = ClockSampler(local)
-    cabs.cabs_profile_read(ctx, reset=True)
-    cabs.cabs_profile_enable(ctx, True)
     launches0 = cabs.cabs_launch_count()
-    barrier()
+    if B == 1:
+        cabs.cabs_profile_read(ctx, reset=True)
+        cabs.cabs_profile_enable(ctx, True)
     sampler.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ev[0].record(stream)
-    errs = []
-    for i in range(args.steps):
-        errs.append(step())
-        ev[i + 1].record(stream)
-    barrier()
+    per_step, total_ms, errs = timed_steps(ctx, cabs, step, args.steps, stream, world, barrier)
     clocks = sampler.stop()
     launches = cabs.cabs_launch_count() - launches0
+    if B > 1:
+        # Per-kernel launch durations of the same batch run serially (one lane,
+        # no graph): under concurrent lanes an event pair would also bracket the
+        # time a kernel queues behind the other lanes' kernels.
+        cabs.cabs_profile_read(ctx, reset=True)
+        cabs.cabs_profile_enable(ctx, True)
+        timed_steps(ctx, cabs, lambda: run_batch(1, False), args.steps, stream, world, barrier)
     cabs.cabs_profile_enable(ctx, False)
     prof = cabs.cabs_profile_read(ctx, reset=True)
-    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    diag = out.diag()
+    diag = outs[0].diag()
     sweeps = [diag.sweeps_pilot, diag.sweeps_final]
+    all_errs = [e for es in errs for e in es]
 
-    # end to end through the C ABI with host buffers: pinned H2D of the
-    # step's inputs, the sketch and its error, D2H of the factors and indices
+    # ---- end to end through the C ABI with host buffers: pinned H2D of the
+    # step's inputs, the sketches and their errors, D2H of factors and indices
     e2e = None
     if not args.no_e2e:
         if wl["kind"] == "rbf":
@@ -353,30 +472,48 @@ def run_cabs(args):
             hA = torch.empty(inp["A"].shape, dtype=inp["A"].dtype, pin_memory=True)
             hA.copy_(inp["A"])
             h2d = hA.numel() * hA.element_size()
-        outs_host = [torch.empty(t_.shape, dtype=t_.dtype, pin_memory=True)
-                     for t_ in (out.U, out.S, out.V, out.rows, out.cols)]
-        d2h = sum(x.numel() * x.element_size() for x in outs_host) + 8
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            if wl["kind"] == "rbf":
-                inp["X"].copy_(hx, non_blocking=True)
-                inp["Y"].copy_(hy, non_blocking=True)
-            else:
-                inp["A"].copy_(hA, non_blocking=True)
-            step()  # the error is read back to the host inside cabs_error
-            for hdst, dsrc in zip(outs_host, (out.U, out.S, out.V, out.rows, out.cols)):
-                hdst.copy_(dsrc, non_blocking=True)
-        e1.record(stream)
-        barrier()
-        e2e_ms = e0.elapsed_time(e1)
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=device)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = dict(value=round(world * args.steps / (float(te.item()) / 1e3), 4), unit="sketches/s",
+        outs_host = [[torch.empty(t_.shape, dtype=t_.dtype, pin_memory=True)
+                      for t_ in (o.U, o.S, o.V, o.rows, o.cols)] for o in outs]
+        d2h = sum(x.numel() * x.element_size() for oh in outs_host for x in oh) + 8 * B  # + the errors
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                if wl["kind"] == "rbf":
+                    inp["X"].copy_(hx, non_blocking=True)
+                    inp["Y"].copy_(hy, non_blocking=True)
+                else:
+                    inp["A"].copy_(hA, non_blocking=True)
+            errs_ = step()  # the step's errors are read back to the host
+            with torch.cuda.stream(stream):
+                for oh, o in zip(outs_host, outs):
+                    for hdst, dsrc in zip(oh, (o.U, o.S, o.V, o.rows, o.cols)):
+                        hdst.copy_(dsrc, non_blocking=True)
+            return errs_
+
+        _, e2e_ms, _ = timed_steps(ctx, cabs, e2e_step, args.steps, stream, world, barrier)
+        e2e = dict(value=round(world * B * args.steps / (e2e_ms / 1e3), 4), unit="sketches/s",
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+
+    # ---- the plain FP32 form on the same GPU, one sketch at a time (comparison)
+    plain = None
+    if args.form != "plain" and not args.no_plain and args.workload != "plain":
+        pp = cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank * 1000, prec="fp32", core=wl["core"],
+                              err_samples=samples, err_seed=3)
+        wsp = torch.empty(cabs.cabs_workspace_size(src, pp) + 512, dtype=torch.uint8, device=device)
+        outp = cabs.alloc_result(pp, device)
+
+        def pstep():
+            with torch.cuda.stream(stream):
+                cabs.cabs_sketch(ctx, src, pp, ws=wsp, out=outp, stream=stream)
+                return float(outp.err.cpu().item())
+
+        for _ in range(2):
+            pstep()
+        psteps = max(2, args.steps // 2)
+        pper, ptot, perrs = timed_steps(ctx, cabs, pstep, psteps, stream, world, barrier)
+        plain = dict(value=round(world * psteps / (ptot / 1e3), 4), unit="sketches/s",
+                     ms_per_sketch=round(ptot / psteps, 4), rel_fro_error=perrs[-1], prec="fp32",
+                     form="one sketch per launch sequence, one stream, no graph")
 
     if rank != 0:
         if world > 1:
@@ -384,36 +521,49 @@ def run_cabs(args):
         return None
     peaks = load_peaks()
     eb = 8 if prec == "fp64" else 4
-    roof, table = roofline(prof, wl, k, iters, eb, sweeps, args.steps, peaks, prec)
+    roof, table = roofline(prof, wl, k, iters, eb, sweeps, args.steps * B, peaks, prec)
     gather = None
     if wl["kind"] in ("dense", "plain") and "gather_cols_kernel" in prof:
         gl, gms = prof["gather_cols_kernel"]
         rl, rms = prof.get("gather_rows_t_kernel", (0, 0.0))
         m, n = wl["m"], wl["n"]
-        useful = args.steps * 2 * ((m * k + n * k) * eb + k * k * eb)
-        sectors = args.steps * 2 * (m * k * 32 + n * k * eb)
+        nsk = args.steps * B
+        useful = nsk * 2 * ((m * k + n * k) * eb + k * k * eb)
+        sectors = nsk * 2 * (m * k * 32 + n * k * eb)
         secs = (gms + rms) / 1e3
         gather = dict(useful_gbs=round(useful / secs / 1e9, 2), dram_sector_gbs=round(sectors / secs / 1e9, 2),
-                      frac_of_hbm=round(sectors / secs / 1e9 / peaks["hbm_gbs"], 4), ms_per_step=round(
-                          (gms + rms) / args.steps, 4))
-    res = dict(metric=METRIC, value=round(world * args.steps / (total_ms / 1e3), 4), unit="sketches/s",
+                      frac_of_hbm=round(sectors / secs / 1e9 / peaks["hbm_gbs"], 4),
+                      ms_per_sketch=round((gms + rms) / nsk, 4))
+    lat = sorted(per_step)
+    res = dict(metric=METRIC, value=round(world * B * args.steps / (total_ms / 1e3), 4), unit="sketches/s",
                n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4),
                higher_is_better=True, scaling="weak", vs_baseline=None,
                dtype={"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[prec] + "+f64core",
                data="synthetic",
                config=dict(workload=args.workload, desc=wl["desc"], m=wl["m"], n=wl["n"], k=k, iters=iters,
-                           prec=prec, core=wl["core"], parallelism=f"replicas x{world}",
+                           prec=prec, core=wl["core"], form=args.form, sketches_per_step=B,
+                           lanes=args.lanes if B > 1 else 1, graph=B > 1,
+                           parallelism=f"replicas x{world}",
                            l2="inputs larger than L2 (dense A 8 GiB)" if wl["kind"] == "dense" else
                            "entries generated on the fly; factors and points re-read each step"),
-               latency_ms=dict(p50=round(statistics.median(per_step), 4),
-                               p99=round(sorted(per_step)[min(len(per_step) - 1,
-                                                              int(math.ceil(0.99 * len(per_step))) - 1)], 4)),
-               rel_fro_error=errs[-1], gpu_launches=int(launches),
+               latency_ms=dict(step_p50=round(statistics.median(per_step), 4),
+                               step_p99=round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 4)),
+               rel_fro_error=dict(median=statistics.median(all_errs), max=max(all_errs)),
+               gpu_launches=int(launches),
                diag=dict(svd_sweeps=sweeps, svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
-                         snap_fallbacks=int(diag.snap_fallbacks), rechecked=int(diag.rechecked)), roofline=roof, kernels=table, gather=gather,
-               e2e=e2e, clocks=clocks)
+                         snap_fallbacks=int(diag.snap_fallbacks), rechecked=int(diag.rechecked)),
+               roofline=roof, kernels=table,
+               kernel_timing=("serial profiled pass of the same batch after the timed region" if B > 1
+                              else "timed region"),
+               gather=gather, plain_fp32=plain, e2e=e2e, clocks=clocks)
+    if wl["kind"] == "dense" and "L" in inp:
+        res["rel_fro_error_noiseless"] = noiseless_error(inp["L"], outs[0])
+    if wl["kind"] != "plain" and not (args.m or args.n):
+        res["precision"] = precision_excess(cabs, ctx, wl, device)
     if not args.no_cpu:
         res["cpu_baseline"] = run_cpu_baseline(args.workload, args.cpu_steps)
+        if "precision" in res and res["cpu_baseline"].get("oracle_error") is not None:
+            res["precision"]["oracle_fp64"] = res["cpu_baseline"]["oracle_error"]
     if world > 1:
         dist.destroy_process_group()
     return res
@@ -438,11 +588,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: about 2 s of timed work)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cabs", choices=["cabs", "reference"])
     ap.add_argument("--workload", default="dense", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "tf32", "bf16", "fp64"])
+    ap.add_argument("--form", default="batched", choices=["batched", "plain"],
+                    help="batched: --batch concurrent sketches per step over --lanes streams (captured graph)")
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--m", type=int, default=0, help="override the workload's rows (profiler captures)")
+    ap.add_argument("--n", type=int, default=0, help="override the workload's columns (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=1)

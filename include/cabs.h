@@ -108,9 +108,15 @@ typedef struct {
   float upsilon_pow;  /* Upsilon(t) = t^p of Eq. wkmeans; 0 = unweighted */
   double trunc_rtol;  /* keep sigma_i > max(trunc_rtol, k 2^-52) sigma_1 */
   int32_t flags;      /* CABS_FLAG_* */
+  /* With CABS_FLAG_ERROR: the relative error of the sketch (as cabs_error,
+   * Section 5) over err_samples sampled entries drawn with key (err_seed, 2),
+   * or exactly over every entry when err_samples == 0 (dense sources only). */
+  int64_t err_samples;
+  uint64_t err_seed;
 } cabs_params;
 
 #define CABS_FLAG_FOLLOW_ERR 1 /* also compute the follow-up encoding errors e_f */
+#define CABS_FLAG_ERROR 2      /* also compute the relative error into cabs_result.err */
 
 /* Device-side diagnostics, written by the kernels of one sketch. */
 typedef struct {
@@ -138,6 +144,7 @@ typedef struct {
   int32_t* pilot_rows;  /* k1: pilot row indices I^r, ascending */
   int32_t* pilot_cols;  /* k1: pilot column indices I^c, ascending */
   cabs_diag* diag;      /* optional (may be NULL) */
+  double* err;          /* 1 double; required with CABS_FLAG_ERROR, else unused (may be NULL) */
 } cabs_result;
 
 /* ---------------------------------------------------------------- context */
@@ -158,10 +165,14 @@ const char* cabs_version(void);
 cabs_status cabs_workspace_size(const cabs_source* src, const cabs_params* p, size_t* bytes);
 
 /* One CABS sketch (Algorithm 2): pilot draw, gather, sketching and embedding,
- * weighted k-means on both embeddings, snap, follow-up gather and sketching.
+ * weighted k-means on both embeddings, snap, follow-up gather and sketching;
+ * with CABS_FLAG_ERROR also the relative error of the result, enqueued on the
+ * same stream and equal bit for bit to what cabs_error returns for the same
+ * samples and seed.
  * ws: device workspace of at least cabs_workspace_size() bytes, 256-byte
  * aligned, owned by the caller and not used by anything else until the
- * stream has passed this sketch. */
+ * stream has passed this sketch. Returns CABS_EINVAL for CABS_FLAG_ERROR
+ * without out->err, or with err_samples == 0 on an implicit source. */
 cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
                         void* ws, size_t ws_bytes, cabs_stream stream, const cabs_result* out);
 
@@ -291,7 +302,10 @@ cabs_status cabs_profile_enable(cabs_ctx* ctx, int32_t on);
  * clears the accumulated totals. */
 int32_t cabs_profile_read(cabs_ctx* ctx, char* names, int32_t name_len, int64_t* launches, double* total_ms,
                           int32_t max, int32_t reset);
-/* Number of kernel launches libcabs has issued in this process. */
+/* Number of kernel launches libcabs has issued in this process; each replay
+ * of a captured batch graph counts the kernels the graph holds. Launches made
+ * while a graph is being captured are not counted until it is replayed.
+ * Profiling (cabs_profile_enable) skips captured launches. */
 int64_t cabs_launch_count(void);
 
 /* ------------------------------------------------------------- serving */

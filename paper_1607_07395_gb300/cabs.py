@@ -22,6 +22,7 @@ SRC_DENSE, SRC_RBF = 0, 1
 TAG_ROWS, TAG_COLS, TAG_EVAL = 0, 1, 2
 MAX_K, MAX_D, MAX_ITERS = 256, 64, 64
 FLAG_FOLLOW_ERR = 1
+FLAG_ERROR = 2
 PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16}
 CORES = {"pinv": CORE_PINV, "stabilized": CORE_STABILIZED}
 
@@ -40,7 +41,8 @@ class cabs_source(C.Structure):
 class cabs_params(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("k1", C.c_int32), ("k2", C.c_int32), ("iters", C.c_int32),
                 ("seed", C.c_uint64), ("prec", C.c_int32), ("core", C.c_int32), ("upsilon_pow", C.c_float),
-                ("trunc_rtol", C.c_double), ("flags", C.c_int32)]
+                ("trunc_rtol", C.c_double), ("flags", C.c_int32), ("err_samples", C.c_int64),
+                ("err_seed", C.c_uint64)]
 
 
 class cabs_diag(C.Structure):
@@ -54,7 +56,7 @@ class cabs_diag(C.Structure):
 class cabs_result(C.Structure):
     _fields_ = [("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p), ("rows", C.c_void_p),
                 ("cols", C.c_void_p), ("pilot_rows", C.c_void_p), ("pilot_cols", C.c_void_p),
-                ("diag", C.c_void_p)]
+                ("diag", C.c_void_p), ("err", C.c_void_p)]
 
 
 _lib = None
@@ -205,11 +207,14 @@ def rbf_source(X, Y, sigma):
 
 
 def make_params(m, n, k1, k2=None, iters=5, seed=1607, prec="fp64", core="pinv", upsilon_pow=0.0, trunc_rtol=0.0,
-                flags=0):
+                flags=0, err_samples=None, err_seed=1607):
+    """cabs_params; err_samples (0 = exact, > 0 = sampled) also sets CABS_FLAG_ERROR."""
+    if err_samples is not None:
+        flags |= FLAG_ERROR
     return cabs_params(m=m, n=n, k1=k1, k2=k1 if k2 is None else k2, iters=iters, seed=seed,
                        prec=PRECS[prec] if isinstance(prec, str) else prec,
                        core=CORES[core] if isinstance(core, str) else core, upsilon_pow=upsilon_pow,
-                       trunc_rtol=trunc_rtol, flags=flags)
+                       trunc_rtol=trunc_rtol, flags=flags, err_samples=err_samples or 0, err_seed=err_seed)
 
 
 def elem_dtype(prec):
@@ -232,6 +237,7 @@ class Sketch:
     diag_buf: object
     params: cabs_params
     result: cabs_result = None
+    err: object = None  # 1 FP64 device scalar: the relative error (CABS_FLAG_ERROR)
 
     def diag(self) -> cabs_diag:
         """Copies the device diagnostics to the host (synchronises)."""
@@ -249,9 +255,11 @@ def alloc_result(p: cabs_params, device="cuda"):
     rows, cols = torch.empty(p.k2, **i32), torch.empty(p.k2, **i32)
     prow, pcol = torch.empty(p.k1, **i32), torch.empty(p.k1, **i32)
     diag = torch.zeros(C.sizeof(cabs_diag), dtype=torch.uint8, device=device)
+    err = torch.zeros(1, dtype=torch.float64, device=device)
     res = cabs_result(U=U.data_ptr(), S=S.data_ptr(), V=V.data_ptr(), rows=rows.data_ptr(), cols=cols.data_ptr(),
-                      pilot_rows=prow.data_ptr(), pilot_cols=pcol.data_ptr(), diag=diag.data_ptr())
-    return Sketch(U, S, V, rows, cols, prow, pcol, diag, p, res)
+                      pilot_rows=prow.data_ptr(), pilot_cols=pcol.data_ptr(), diag=diag.data_ptr(),
+                      err=err.data_ptr())
+    return Sketch(U, S, V, rows, cols, prow, pcol, diag, p, res, err)
 
 
 def cabs_workspace_size(src: Source, p: cabs_params) -> int:

@@ -93,12 +93,23 @@ cabs_status validate_params(const cabs_params* p) {
   CABS_REQUIRE(p->core == CABS_CORE_PINV || p->core == CABS_CORE_STABILIZED, "unknown core %d", p->core);
   CABS_REQUIRE(finite(p->upsilon_pow), "upsilon_pow must be finite");
   CABS_REQUIRE(finite(p->trunc_rtol) && p->trunc_rtol >= 0.0, "trunc_rtol must be finite and >= 0");
+  CABS_REQUIRE((p->flags & ~(CABS_FLAG_FOLLOW_ERR | CABS_FLAG_ERROR)) == 0, "unknown flags 0x%x", p->flags);
+  if (p->flags & CABS_FLAG_ERROR) CABS_REQUIRE(p->err_samples >= 0, "err_samples must be >= 0");
+  return CABS_OK;
+}
+
+// A sketch that also computes its error needs somewhere to put it, and the
+// exact error needs stored entries.
+cabs_status validate_error_request(const cabs_source* src, const cabs_params* p, const cabs_result* out) {
+  if (!(p->flags & CABS_FLAG_ERROR)) return CABS_OK;
+  CABS_REQUIRE(out->err != nullptr, "CABS_FLAG_ERROR needs result.err");
+  CABS_REQUIRE(p->err_samples > 0 || src->kind == CABS_SRC_DENSE, "the exact error needs a dense source");
   return CABS_OK;
 }
 
 // -------------------------------------------------------------- workspace
 
-SketchWs carve_sketch(Carve& cv, const cabs_params& p) {
+SketchWs carve_sketch(Carve& cv, const cabs_source& src, const cabs_params& p) {
   const size_t eb = elem_bytes(p.prec);
   const int64_t m = p.m, n = p.n;
   const int k1 = p.k1, k2 = p.k2;
@@ -127,13 +138,27 @@ SketchWs carve_sketch(Carve& cv, const cabs_params& p) {
   w.core = cv.take<char>(w.core_bytes);
   w.side_r = cv.take<char>(w.side_r_bytes);
   w.side_c = cv.take<char>(w.side_c_bytes);
+  w.err_out2 = nullptr;
+  w.err_ws = nullptr;
+  w.err_bytes = 0;
+  if (p.flags & CABS_FLAG_ERROR) {
+    w.err_out2 = cv.take<double>(2);
+    w.err_bytes = align256(error_ws_bytes(src, m, n, k2, p.err_samples, p.prec));
+    w.err_ws = cv.take<char>(w.err_bytes);
+  }
   return w;
 }
 
-size_t sketch_ws_bytes(const cabs_params& p) {
+size_t sketch_ws_bytes(const cabs_source& src, const cabs_params& p) {
   Carve cv;
-  carve_sketch(cv, p);
+  carve_sketch(cv, src, p);
   return cv.used;
+}
+
+// err = sqrt(num / den), the same correctly rounded operations as the host
+// side of cabs_error.
+__global__ void err_finalize_kernel(const double* out2, double* err) {
+  if (threadIdx.x == 0) err[0] = out2[1] > 0.0 ? sqrt(out2[0] / out2[1]) : 0.0;
 }
 
 __global__ void diag_clear_kernel(cabs_diag* d) {
@@ -145,7 +170,7 @@ __global__ void diag_clear_kernel(cabs_diag* d) {
 cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
                            const cabs_result& out) {
   Carve cv(ws, ws_bytes);
-  SketchWs w = carve_sketch(cv, p);
+  SketchWs w = carve_sketch(cv, src, p);
   if (!cv.fits()) {
     set_error("sketch workspace too small: need %zu bytes, got %zu", cv.used, ws_bytes);
     return CABS_ENOMEM;
@@ -182,6 +207,12 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   CABS_TRY(launch_core(m, n, k2, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, out.U, out.S, out.V,
                        &dg->rank_final, &dg->sweeps_final, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
+  // Section 5: relative Frobenius error of the result
+  if (p.flags & CABS_FLAG_ERROR) {
+    CABS_TRY(launch_error(src, m, n, k2, f64, p.prec, out.U, out.S, out.V, p.err_samples, p.err_seed, w.err_ws,
+                          w.err_bytes, w.err_out2, s));
+    CABS_LAUNCH(s, "err_finalize_kernel", err_finalize_kernel<<<1, 32, 0, s>>>(w.err_out2, out.err));
+  }
   return CABS_OK;
 }
 
@@ -244,7 +275,7 @@ cabs_status cabs_workspace_size(const cabs_source* src, const cabs_params* p, si
   CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
   CABS_TRY(validate_params(p));
   CABS_TRY(validate_source(src, p->m, p->n));
-  *bytes = sketch_ws_bytes(*p);
+  *bytes = sketch_ws_bytes(*src, *p);
   return CABS_OK;
 }
 
@@ -255,8 +286,9 @@ cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params
   CABS_TRY(validate_params(p));
   CABS_TRY(validate_source(src, p->m, p->n));
   CABS_TRY(validate_result(out));
+  CABS_TRY(validate_error_request(src, p, out));
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
-  const size_t need = sketch_ws_bytes(*p);
+  const size_t need = sketch_ws_bytes(*src, *p);
   if (ws_bytes < need) {
     set_error("workspace too small: need %zu bytes, got %zu", need, ws_bytes);
     return CABS_ENOMEM;
@@ -469,7 +501,7 @@ static cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* 
     if (cudaStreamWaitEvent(ctx->lanes[l], ctx->fork_event, 0) != cudaSuccess) return check_cuda("fork wait");
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
-    const size_t need = sketch_ws_bytes(p[i]);
+    const size_t need = sketch_ws_bytes(src[i], p[i]);
     CABS_TRY(sketch_enqueue(src[i], p[i], (char*)ws + off[i], need, ctx->lanes[t % lanes], out[i]));
   }
   for (int l = 0; l < lanes; ++l) {
@@ -494,6 +526,7 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
     CABS_TRY(validate_params(&p[i]));
     CABS_TRY(validate_source(&src[i], p[i].m, p[i].n));
     CABS_TRY(validate_result(&out[i]));
+    CABS_TRY(validate_error_request(&src[i], &p[i], &out[i]));
     CABS_REQUIRE((ws_offsets[i] & 255) == 0, "member %d: workspace offset not 256-aligned", i);
   }
   DeviceGuard g(ctx->device);
@@ -507,7 +540,10 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
   if (it == ctx->graphs.end()) {
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return check_cuda("cudaStreamBeginCapture");
+    const long long l0 = thread_launches();
     const cabs_status st = batched_enqueue(ctx, count, src, p, ws, ws_offsets, out, lanes, s);
+    const long long captured = thread_launches() - l0;
+    add_launches(-captured);  // captured, not run; counted again at every replay
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != CABS_OK) {
@@ -516,6 +552,7 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
     }
     if (ce != cudaSuccess) return check_cuda("cudaStreamEndCapture");
     GraphEntry ge;
+    ge.launches = captured;
     const cudaError_t ie = cudaGraphInstantiate(&ge.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return check_cuda("cudaGraphInstantiate");
@@ -526,5 +563,6 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
     it = ctx->graphs.emplace(key, ge).first;
   }
   if (cudaGraphLaunch(it->second.exec, s) != cudaSuccess) return check_cuda("cudaGraphLaunch");
+  add_launches(it->second.launches);
   return CABS_OK;
 }

@@ -29,16 +29,21 @@ struct SketchWs {
   cabs_diag* diag;
   void *core, *side_r, *side_c;
   size_t core_bytes, side_r_bytes, side_c_bytes;
+  double* err_out2;  // CABS_FLAG_ERROR: (num, den) of the error
+  void* err_ws;
+  size_t err_bytes;
 };
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernel launches held by the graph
 };
 
 struct ServeState;
 
-SketchWs carve_sketch(Carve& cv, const cabs_params& p);
-size_t sketch_ws_bytes(const cabs_params& p);
+SketchWs carve_sketch(Carve& cv, const cabs_source& src, const cabs_params& p);
+size_t sketch_ws_bytes(const cabs_source& src, const cabs_params& p);
+cabs_status validate_error_request(const cabs_source* src, const cabs_params* p, const cabs_result* out);
 cabs_status validate_source(const cabs_source* src, int64_t m, int64_t n);
 cabs_status validate_params(const cabs_params* p);
 cabs_status validate_result(const cabs_result* out);

@@ -3,7 +3,8 @@
 // When enabled, every kernel launch site records a CUDA event pair around the
 // launch on the launching stream; cabs_profile_read synchronises the events
 // and reports, per kernel name, the number of launches and the summed device
-// time. The launch counter is always on (a relaxed atomic increment).
+// time. The launch counter is always on (a relaxed atomic increment); a
+// captured graph adds the launches it holds each time it is replayed.
 // Profiling is process-wide and is skipped while the launching stream is
 // being captured into a CUDA graph.
 #include <atomic>
@@ -25,6 +26,7 @@ struct Pending {
 };
 
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 std::atomic<int> g_enabled{0};
 std::mutex g_mu;
 std::vector<Pending> g_pending;
@@ -92,8 +94,13 @@ ProfScope::~ProfScope() {
 
 cabs_status launched(const char* what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
   return check_cuda(what);
 }
+
+long long thread_launches() { return t_launches; }
+
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 }  // namespace cabs
 

@@ -22,6 +22,11 @@ class ProfScope {
 // Counts one kernel launch and converts a launch error into CABS_ECUDA.
 cabs_status launched(const char* what);
 
+// Launches counted on the calling thread so far (graph capture bookkeeping).
+long long thread_launches();
+// Adds n to the launch counter (n < 0 removes launches that were only captured).
+void add_launches(long long n);
+
 }  // namespace cabs
 
 // Wraps one kernel launch statement: times it (when enabled), counts it,

@@ -114,6 +114,7 @@ static size_t result_bytes(const cabs_params& p) {
   cv.take<int>(p.k1);
   cv.take<int>(p.k1);
   cv.take<cabs_diag>(1);
+  cv.take<double>(1);
   return cv.used;
 }
 
@@ -129,6 +130,7 @@ static cabs_result result_at(char* base, const cabs_params& p) {
   r.pilot_rows = cv.take<int>(p.k1);
   r.pilot_cols = cv.take<int>(p.k1);
   r.diag = cv.take<cabs_diag>(1);
+  r.err = cv.take<double>(1);
   return r;
 }
 
@@ -248,12 +250,14 @@ cabs_status cabs_serve_submit(cabs_ctx* ctx, const cabs_source* src, const cabs_
   CABS_REQUIRE(ticket != nullptr, "ticket is NULL");
   CABS_TRY(validate_params(p));
   CABS_TRY(validate_source(src, p->m, p->n));
+  CABS_REQUIRE(!(p->flags & CABS_FLAG_ERROR) || p->err_samples > 0 || src->kind == CABS_SRC_DENSE,
+               "the exact error needs a dense source");
   ServeState* st = ctx->serve;
   Request r;
   r.src = *src;
   r.p = *p;
   r.res_bytes = result_bytes(*p);
-  r.ws_bytes = sketch_ws_bytes(*p);
+  r.ws_bytes = sketch_ws_bytes(*src, *p);
   if (align256(r.res_bytes) + align256(r.ws_bytes) > st->arena_bytes) {
     set_error("request footprint %zu bytes exceeds the arena (%zu bytes)", r.res_bytes + r.ws_bytes,
               st->arena_bytes);

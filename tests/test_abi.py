@@ -51,7 +51,8 @@ int main(void) {
          sizeof(cabs_params), sizeof(cabs_diag), sizeof(cabs_result));
   F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma)
   F(cabs_params, seed) F(cabs_params, upsilon_pow) F(cabs_params, trunc_rtol) F(cabs_params, flags)
-  F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_result, diag)
+  F(cabs_params, err_samples) F(cabs_params, err_seed)
+  F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_result, diag) F(cabs_result, err)
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -96,6 +97,26 @@ def test_workspace_size_and_validation_on_host(L):
     assert L.cabs_workspace_size(C.byref(r), C.byref(p), C.byref(n)) == cabs.CABS_EINVAL
     r.d, r.sigma = 16, 0.0
     assert L.cabs_workspace_size(C.byref(r), C.byref(p), C.byref(n)) == cabs.CABS_EINVAL
+
+
+def test_error_request_on_host(L):
+    """CABS_FLAG_ERROR adds the error's workspace; bad requests are refused."""
+    n0, n1, n2 = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    p = cabs.make_params(2000, 1500, 20, prec="fp32")
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(p), C.byref(n0)) == cabs.CABS_OK
+    pe = cabs.make_params(2000, 1500, 20, prec="fp32", err_samples=0)
+    assert pe.flags == cabs.FLAG_ERROR
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(pe), C.byref(n1)) == cabs.CABS_OK
+    e = C.c_size_t()
+    assert L.cabs_error_workspace_size(C.byref(_src()), C.byref(p), 0, C.byref(e)) == cabs.CABS_OK
+    assert n1.value >= n0.value + e.value - 256
+    ps = cabs.make_params(2000, 1500, 20, prec="fp32", err_samples=10 ** 6)
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(ps), C.byref(n2)) == cabs.CABS_OK
+    bad = cabs.make_params(2000, 1500, 20, flags=4)
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(bad), C.byref(n0)) == cabs.CABS_EINVAL
+    neg = cabs.make_params(2000, 1500, 20, err_samples=0)
+    neg.err_samples = -1
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(neg), C.byref(n0)) == cabs.CABS_EINVAL
 
 
 def test_null_arguments_rejected(L):

@@ -98,17 +98,24 @@ def decaying_lowrank_device(m: int, n: int, rank: int = 256, decay: float = 30.0
                             out=None, row_block: int = 8192):
     """Device version of A = U diag(s) V^T + noise in FP32 (e.g. 65536 x 32768, 8 GiB).
 
-    U and V are Gaussian matrices orthonormalised by a QR in FP64; the product
-    is formed in FP64 one row block at a time and rounded to FP32. ``out`` may
-    be a preallocated (m x lda) FP32 device tensor whose first n columns are
+    U and V are Gaussian matrices (drawn on the device) orthonormalised by a
+    LAPACK QR in FP64 on the host (torch's device linear algebra is not needed,
+    so the generator also runs under a profiler); the product is formed in
+    FP64 one row block at a time and rounded to FP32. ``out`` may be a
+    preallocated (m x lda) FP32 device tensor whose first n columns are
     filled. Returns (A, U, s, V) with the FP64 factors on the device."""
     import torch
+
+    def orthonormal(rows):
+        g = torch.randn(rows, rank, generator=gen, device=device, dtype=torch.float64)
+        q, _ = np.linalg.qr(g.cpu().numpy())
+        return torch.from_numpy(np.ascontiguousarray(q)).to(device)
 
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed) * 1000003 + 17)
     rank = min(rank, m, n)
-    U, _ = torch.linalg.qr(torch.randn(m, rank, generator=gen, device=device, dtype=torch.float64))
-    V, _ = torch.linalg.qr(torch.randn(n, rank, generator=gen, device=device, dtype=torch.float64))
+    U = orthonormal(m)
+    V = orthonormal(n)
     s = torch.exp(-torch.arange(1, rank + 1, device=device, dtype=torch.float64) / decay)
     A = out if out is not None else torch.empty(m, n, device=device, dtype=torch.float32)
     Us = U * s
