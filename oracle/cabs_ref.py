@@ -381,6 +381,24 @@ def snap(X: np.ndarray, Z: np.ndarray):
     return out, np.sort(out)
 
 
+def hard_threshold(X: np.ndarray, k2: int):
+    """Follow-up selection by hard threshold (Section 5, follow-up variant (f)):
+    instead of clustering, keep the k2 rows whose weight Upsilon(|X_l|_2) is
+    largest. Upsilon is monotone, so this ranks rows by the embedding norm
+    itself (for a constant Upsilon every weight ties; ranking by the norm is
+    the limit of any increasing Upsilon). Squared norms are summed in FP64 in
+    dimension order; ties go to the lower row index. Returns the rows sorted."""
+    X = np.asarray(X, dtype=np.float64)
+    M = X.shape[0]
+    if not (1 <= k2 <= M):
+        raise ValueError("need 1 <= k2 <= M")
+    sq = np.zeros(M)
+    for q in range(X.shape[1]):
+        sq = sq + X[:, q] * X[:, q]
+    order = np.lexsort((np.arange(M), -sq))  # largest norm first, then lowest index
+    return np.sort(order[:k2]).astype(np.int64)
+
+
 # --------------------------------------------------------------------------
 # Algorithm 2 end to end
 # --------------------------------------------------------------------------
@@ -436,12 +454,14 @@ class CabsResult:
 
 
 def cabs(source, k1: int, k2: int = None, iters: int = 5, seed: int = 1607,
-         mode: str = "pinv", upsilon_pow: float = 0.0, trunc_rtol: float = 0.0) -> CabsResult:
+         mode: str = "pinv", upsilon_pow: float = 0.0, trunc_rtol: float = 0.0,
+         follow: str = "kmeans") -> CabsResult:
     """Cascaded bilateral sampling (Algorithm 2).
 
     1. pilot sampling of k1 random rows and columns; 2. pilot sketching and
     embeddings P, Q; 3. weighted k-means on P and on Q, centres snapped to
-    rows -> follow-up indices; 4. follow-up sketching on the new gather."""
+    rows -> follow-up indices (follow="threshold": the hard-threshold variant
+    of Section 5 instead); 4. follow-up sketching on the new gather."""
     k2 = k1 if k2 is None else k2
     m, n = source.m, source.n
     if not (1 <= k2 <= k1 <= min(m, n)):
@@ -452,10 +472,17 @@ def cabs(source, k1: int, k2: int = None, iters: int = 5, seed: int = 1607,
     pilot = sketching(C, Rt, W, m, n, mode, trunc_rtol)
     P = embed(pilot.U, pilot.S)
     Q = embed(pilot.V, pilot.S)
-    km_r = weighted_kmeans(P, Ir_drawn[:k2], iters, upsilon_pow)
-    km_c = weighted_kmeans(Q, Ic_drawn[:k2], iters, upsilon_pow)
-    rows_o, rows = snap(P, km_r.Z)
-    cols_o, cols = snap(Q, km_c.Z)
+    if follow == "threshold":
+        km_r = km_c = None
+        rows_o = rows = hard_threshold(P, k2)
+        cols_o = cols = hard_threshold(Q, k2)
+    elif follow == "kmeans":
+        km_r = weighted_kmeans(P, Ir_drawn[:k2], iters, upsilon_pow)
+        km_c = weighted_kmeans(Q, Ic_drawn[:k2], iters, upsilon_pow)
+        rows_o, rows = snap(P, km_r.Z)
+        cols_o, cols = snap(Q, km_c.Z)
+    else:
+        raise ValueError("follow must be 'kmeans' or 'threshold'")
     Cb, Rtb, Wb = source.gather(rows, cols)
     final = sketching(Cb, Rtb, Wb, m, n, mode, trunc_rtol)
     ep_r, _, Tp_r = encoding_error(P, Ir_drawn[:k2], upsilon_pow)

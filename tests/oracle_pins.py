@@ -282,6 +282,41 @@ def pin_snap_bruteforce(snap_fn, M=30, d=3, k2=6, seed=8):
     assert len(set(taken)) == k2
 
 
+# ------------------------------------------------------------ hard threshold
+
+def pin_threshold_bruteforce(thr_fn, M=40, d=5, k2=9, seed=12):
+    """The k2 rows of largest norm, found by repeated maximum extraction with
+    explicit loops (ties to the lower index); the result is sorted."""
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((M, d)) * g.uniform(0.2, 3.0, size=(M, 1))
+    X[7] = -X[3]          # equal norms: row 3 wins the tie if both are near the cut
+    left = list(range(M))
+    pick = []
+    for _ in range(k2):
+        best = None
+        for l in left:
+            v = sum(float(X[l, q]) ** 2 for q in range(d))
+            if best is None or v > best[0]:
+                best = (v, l)
+        pick.append(best[1])
+        left.remove(best[1])
+    assert thr_fn(X, k2).tolist() == sorted(pick)
+
+
+def pin_threshold_known_scales(thr_fn):
+    """Rows c_l u for a fixed unit vector u: the top k2 are the rows with the
+    largest |c_l| (signs do not matter); equal |c_l| resolve to the lower row."""
+    u = np.array([0.6, 0.0, 0.8])
+    c = np.array([1.0, -5.0, 2.0, 5.0, -0.5, 3.0, 3.0, 0.1])
+    X = c[:, None] * u[None, :]
+    assert thr_fn(X, 1).tolist() == [1]           # |-5| == |5|: the lower row
+    assert thr_fn(X, 2).tolist() == [1, 3]
+    assert thr_fn(X, 3).tolist() == [1, 3, 5]     # 3 ties with row 6: the lower row
+    assert thr_fn(X, 5).tolist() == [1, 2, 3, 5, 6]
+    assert thr_fn(X, 8).tolist() == list(range(8))
+    assert thr_fn(np.ones((5, 2)), 2).tolist() == [0, 1]   # all equal: the first rows
+
+
 # ---------------------------------------------------------------------- error
 
 def pin_error_closed_form(err_fn):

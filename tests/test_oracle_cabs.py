@@ -17,6 +17,20 @@ def test_cabs_exact_rank_recovery():
     assert len(set(res.rows.tolist())) == 10 and np.all(np.diff(res.rows) > 0)
 
 
+def test_cabs_threshold_follow_up():
+    """The hard-threshold variant (Section 5): the follow-up rows are the k2
+    largest-norm rows of P (and columns of Q), and an exactly rank-r matrix is
+    still recovered exactly by the final round (any rows and columns with
+    rank(W_bar) = r do that)."""
+    A = synth.exact_lowrank_int(120, 90, 6, seed=21)
+    res = o.cabs(o.DenseSource(A), k1=10, iters=3, seed=5, follow="threshold")
+    nP = (res.P ** 2).sum(1)
+    assert set(res.rows.tolist()) == set(np.argsort(-nP, kind="stable")[:10].tolist())
+    assert res.km_rows is None and len(set(res.cols.tolist())) == 10
+    assert res.final.rank == 6
+    assert o.rel_fro_error_dense(A, res.final.U, res.final.S, res.final.V) < 1e-10
+
+
 def test_cabs_init_uses_pilot_rows_in_draw_order():
     A = synth.plain_lowrank(200, 150, 5)
     res = o.cabs(o.DenseSource(A), k1=8, k2=5, iters=2, seed=3)

@@ -109,3 +109,17 @@ def test_error_mutant_rejected():
     bad = mutate(o.rel_fro_error_dense, "return math.sqrt(num / den) if den > 0 else 0.0",
                  "return num / den if den > 0 else 0.0")
     assert rejects(lambda: pins.pin_error_closed_form(bad))
+
+
+THRESHOLD_MUTANTS = [
+    ("order = np.lexsort((np.arange(M), -sq))", "order = np.lexsort((np.arange(M), sq))"),      # smallest
+    ("order = np.lexsort((np.arange(M), -sq))", "order = np.lexsort((-np.arange(M), -sq))"),    # ties high
+    ("sq = sq + X[:, q] * X[:, q]", "sq = sq + X[:, q]"),                                       # not a norm
+    ("return np.sort(order[:k2]).astype(np.int64)", "return order[:k2].astype(np.int64)"),      # unsorted
+]
+
+
+@pytest.mark.parametrize("old,new", THRESHOLD_MUTANTS)
+def test_threshold_mutants_rejected(old, new):
+    bad = mutate(o.hard_threshold, old, new)
+    assert rejects(lambda: (pins.pin_threshold_bruteforce(bad), pins.pin_threshold_known_scales(bad)))

@@ -107,6 +107,11 @@ def test_snap_bruteforce():
     pins.pin_snap_bruteforce(o.snap)
 
 
+def test_threshold_bruteforce_and_known_scales():
+    pins.pin_threshold_bruteforce(o.hard_threshold)
+    pins.pin_threshold_known_scales(o.hard_threshold)
+
+
 def test_error_closed_form():
     pins.pin_error_closed_form(o.rel_fro_error_dense)
 
