@@ -123,16 +123,20 @@ def precision_excess(cabs, ctx, wl, device):
         X, Y, sig = synth.rbf_mixture(s["m"], s["n"], d=wl["d"], seed=1607)
         src = cabs.rbf_source(torch.from_numpy(X).to(device), torch.from_numpy(Y).to(device), sig)
         samples = s["samples"]
-    errs = {}
+    errs, unsupported = {}, {}
     for prec in ("fp64", "fp32", "tf32", "bf16"):
         p = cabs.make_params(s["m"], s["n"], s["k"], iters=s["iters"], seed=1607, prec=prec, core=wl["core"],
                              err_samples=samples, err_seed=3)
-        sk = cabs.cabs_sketch(ctx, src, p)
+        try:
+            sk = cabs.cabs_sketch(ctx, src, p)
+        except cabs.CabsError as e:  # e.g. TF32 k-means beyond its embedding width
+            unsupported[prec] = str(e)
+            continue
         errs[prec] = float(sk.err.cpu().item())
     torch.cuda.synchronize()
     return dict(slice=f"{s['m']}x{s['n']}, k={s['k']}, c={s['iters']}, seed 1607", errors=errs,
-                excess_over_fp64={p_: errs[p_] / errs["fp64"] - 1.0 for p_ in ("fp32", "tf32", "bf16")},
-                bar=1e-3)
+                excess_over_fp64={p_: errs[p_] / errs["fp64"] - 1.0 for p_ in ("fp32", "tf32", "bf16") if p_ in errs},
+                unsupported=unsupported or None, bar=1e-3)
 
 
 def make_source(cabs, wl, inp):
@@ -348,6 +352,23 @@ def run_cpu_baseline(workload, steps):
 
 # --------------------------------------------------------------- GPU arm
 
+def rank_max(x, device=None):
+    """Maximum of x over the ranks of the default process group (x alone
+    without one): the slowest rank's time decides a whole-job number."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, sketches_per_rank_step, steps, total_ms):
+    """Whole-job throughput: every rank's sketches over the slowest rank's time."""
+    return world * sketches_per_rank_step * steps / (total_ms / 1e3)
+
+
 def timed_steps(ctx, cabs, step, steps, stream, world, barrier):
     """Runs `steps` steps between barriers; returns (per-step ms, total ms max over ranks, errors)."""
     import torch
@@ -361,11 +382,7 @@ def timed_steps(ctx, cabs, step, steps, stream, world, barrier):
         ev[i + 1].record(stream)
     barrier()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
-    total = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = rank_max(ev[0].elapsed_time(ev[-1]), torch.device("cuda", torch.cuda.current_device()))
     return per_step, total, errs
 
 
@@ -433,11 +450,7 @@ def run_cabs(args):
     if args.steps <= 0:
         # about two seconds of timed work (enough clock samples), 5 to 2000 steps
         est = max(e0.elapsed_time(e1), 1e-3) if args.warmup > 0 else 50.0
-        args.steps = int(min(2000, max(5, math.ceil(2000.0 / est))))
-        if world > 1:
-            t = torch.tensor([args.steps], dtype=torch.int64, device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            args.steps = int(t.item())
+        args.steps = int(rank_max(min(2000, max(5, math.ceil(2000.0 / est))), device))
     sampler = ClockSampler(local)
     launches0 = cabs.cabs_launch_count()
     if B == 1:
@@ -491,7 +504,7 @@ def run_cabs(args):
             return errs_
 
         _, e2e_ms, _ = timed_steps(ctx, cabs, e2e_step, args.steps, stream, world, barrier)
-        e2e = dict(value=round(world * B * args.steps / (e2e_ms / 1e3), 4), unit="sketches/s",
+        e2e = dict(value=round(job_value(world, B, args.steps, e2e_ms), 4), unit="sketches/s",
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
 
     # ---- the plain FP32 form on the same GPU, one sketch at a time (comparison)
@@ -511,7 +524,7 @@ def run_cabs(args):
             pstep()
         psteps = max(2, args.steps // 2)
         pper, ptot, perrs = timed_steps(ctx, cabs, pstep, psteps, stream, world, barrier)
-        plain = dict(value=round(world * psteps / (ptot / 1e3), 4), unit="sketches/s",
+        plain = dict(value=round(job_value(world, 1, psteps, ptot), 4), unit="sketches/s",
                      ms_per_sketch=round(ptot / psteps, 4), rel_fro_error=perrs[-1], prec="fp32",
                      form="one sketch per launch sequence, one stream, no graph")
 
@@ -535,7 +548,7 @@ def run_cabs(args):
                       frac_of_hbm=round(sectors / secs / 1e9 / peaks["hbm_gbs"], 4),
                       ms_per_sketch=round((gms + rms) / nsk, 4))
     lat = sorted(per_step)
-    res = dict(metric=METRIC, value=round(world * B * args.steps / (total_ms / 1e3), 4), unit="sketches/s",
+    res = dict(metric=METRIC, value=round(job_value(world, B, args.steps, total_ms), 4), unit="sketches/s",
                n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4),
                higher_is_better=True, scaling="weak", vs_baseline=None,
                dtype={"fp64": "f64", "fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[prec] + "+f64core",
@@ -550,7 +563,8 @@ def run_cabs(args):
                                step_p99=round(lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)], 4)),
                rel_fro_error=dict(median=statistics.median(all_errs), max=max(all_errs)),
                gpu_launches=int(launches),
-               diag=dict(svd_sweeps=sweeps, svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
+               diag=dict(svd_sweeps=sweeps, svd_refine=[diag.refine_pilot, diag.refine_final],
+                         svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
                          snap_fallbacks=int(diag.snap_fallbacks), rechecked=int(diag.rechecked)),
                roofline=roof, kernels=table,
                kernel_timing=("serial profiled pass of the same batch after the timed region" if B > 1

@@ -117,11 +117,17 @@ typedef struct {
 
 #define CABS_FLAG_FOLLOW_ERR 1 /* also compute the follow-up encoding errors e_f */
 #define CABS_FLAG_ERROR 2      /* also compute the relative error into cabs_result.err */
+/* Follow-up rows and columns by hard threshold (Section 5, follow-up variant
+ * (f)): the k2 rows of P and of Q with the largest norm (the argument of the
+ * monotone weight), ties to the lower index, instead of the weighted k-means
+ * and the snap. iters and upsilon_pow are then unused, and the k-means
+ * diagnostics (e_rows, e_cols, T_rows, T_cols) stay zero. */
+#define CABS_FLAG_HARD_THRESHOLD 4
 
 /* Device-side diagnostics, written by the kernels of one sketch. */
 typedef struct {
   int32_t rank_pilot, rank_final;         /* kept singular values of W and W_bar */
-  int32_t sweeps_pilot, sweeps_final;     /* Jacobi sweeps of the FP64 SVDs */
+  int32_t sweeps_pilot, sweeps_final;     /* FP32 Jacobi sweeps of the two SVDs of W */
   int32_t T_rows, T_cols;                 /* max cluster size (Eq. T) of the last assignment */
   int32_t status;                         /* bit 0: the FP64 Jacobi hit its sweep limit; bit 1: the
                                            * FP64 refinement did not converge and the FP64 Jacobi ran;
@@ -131,6 +137,8 @@ typedef struct {
   double e_cols[CABS_MAX_ITERS];          /*   (iteration 0 = the pilot representatives) */
   double e_follow_rows, e_follow_cols;    /* with the snapped follow-up representatives */
   int32_t snap_fallbacks;                 /* centres whose 8 nearest rows were all taken */
+  int32_t refine_pilot, refine_final;     /* FP64 refinement iterations of the two SVDs
+                                           * (-1: the FP64 Jacobi fallback ran) */
   int32_t reserved;
 } cabs_diag;
 
@@ -283,12 +291,25 @@ cabs_status cabs_kmeans(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, cons
 /* Step a6, Section 3.2 (each centre replaced by its closest in-sample point):
  * centres Z (k2 x d, elem) taken in index order, each picks the nearest row
  * of X (M x d, elem) not yet picked, ties to the lowest row index; distances
- * by direct differences in elem. d_order (k2, pick order) and d_sorted (k2,
- * ascending) are device int32. ws: cabs_snap_workspace_size() bytes. */
+ * by direct differences in elem. In the BF16 and TF32 modes (k2 <= 256) the
+ * candidates are first ranked by |x|^2 - 2 x.z on tensor cores, and each
+ * centre's 32 best are re-ranked by direct distance (computed in FP64 from
+ * the FP32 inputs) before the walk.
+ * d_order (k2, pick order) and d_sorted (k2, ascending) are device int32.
+ * ws: cabs_snap_workspace_size() bytes. */
 cabs_status cabs_snap_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t prec, size_t* bytes);
 cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const void* Z, int32_t k2,
                       int32_t prec, int32_t* d_order, int32_t* d_sorted, void* ws, size_t ws_bytes,
                       cabs_stream stream);
+
+/* Section 5, follow-up variant (f): the k2 rows of X (M x d, elem) with the
+ * largest squared norm, summed in dimension order with one rounding per
+ * multiply and per add (so FP64 keys match a sequential FP64 sum), ties to
+ * the lower row index. d_sorted (k2, ascending) is device int32.
+ * 1 <= k2 <= M, M < 2^31. ws: cabs_threshold_workspace_size() bytes. */
+cabs_status cabs_threshold_workspace_size(int64_t M, size_t* bytes);
+cabs_status cabs_threshold(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, int32_t k2, int32_t prec,
+                           int32_t* d_sorted, void* ws, size_t ws_bytes, cabs_stream stream);
 
 /* ----------------------------------------------------------- profiling */
 

@@ -23,6 +23,7 @@ TAG_ROWS, TAG_COLS, TAG_EVAL = 0, 1, 2
 MAX_K, MAX_D, MAX_ITERS = 256, 64, 64
 FLAG_FOLLOW_ERR = 1
 FLAG_ERROR = 2
+FLAG_HARD_THRESHOLD = 4
 PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16}
 CORES = {"pinv": CORE_PINV, "stabilized": CORE_STABILIZED}
 
@@ -50,7 +51,7 @@ class cabs_diag(C.Structure):
                 ("sweeps_final", C.c_int32), ("T_rows", C.c_int32), ("T_cols", C.c_int32), ("status", C.c_int32),
                 ("rechecked", C.c_int32), ("e_rows", C.c_double * MAX_ITERS), ("e_cols", C.c_double * MAX_ITERS),
                 ("e_follow_rows", C.c_double), ("e_follow_cols", C.c_double), ("snap_fallbacks", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("refine_pilot", C.c_int32), ("refine_final", C.c_int32), ("reserved", C.c_int32)]
 
 
 class cabs_result(C.Structure):
@@ -93,6 +94,8 @@ def lib():
         "cabs_kmeans": ([vp, vp, i64, i32, vp, i32, i32, i32, f32, vp, vp, vp, vp, vp, sz, vp], i32),
         "cabs_snap_workspace_size": ([i64, i32, i32, i32, P(sz)], i32),
         "cabs_snap": ([vp, vp, i64, i32, vp, i32, i32, vp, vp, vp, sz, vp], i32),
+        "cabs_threshold_workspace_size": ([i64, P(sz)], i32),
+        "cabs_threshold": ([vp, vp, i64, i32, i32, i32, vp, vp, sz, vp], i32),
         "cabs_serve_start": ([vp, vp, sz, i32], i32),
         "cabs_serve_submit": ([vp, P(cabs_source), P(cabs_params), P(u64)], i32),
         "cabs_serve_poll": ([vp, u64, P(cabs_result), P(f64), i32], i32),
@@ -115,7 +118,8 @@ def exported_names():
     return ["cabs_create", "cabs_destroy", "cabs_last_error", "cabs_version", "cabs_workspace_size", "cabs_sketch",
             "cabs_sketch_batched", "cabs_error_workspace_size", "cabs_error", "cabs_draw_indices", "cabs_gather",
             "cabs_sketching_workspace_size", "cabs_sketching", "cabs_kmeans_workspace_size", "cabs_kmeans",
-            "cabs_snap_workspace_size", "cabs_snap", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
+            "cabs_snap_workspace_size", "cabs_snap", "cabs_threshold_workspace_size", "cabs_threshold",
+            "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
             "cabs_launch_count", "cabs_error_noalloc"]
 
@@ -408,6 +412,21 @@ def cabs_snap(ctx: Context, X, Z, prec="fp64", stream=None):
     _check(lib().cabs_snap(ctx.h, _ptr(X), M, d, _ptr(Z), k2, p, _ptr(order), _ptr(srt), wp, wn, _stream(stream)),
            ctx.h)
     return order, srt
+
+
+def cabs_threshold(ctx: Context, X, k2, prec="fp64", stream=None):
+    """Section 5 follow-up variant (f): the k2 largest-norm rows of X, sorted (device int32)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    M, d = X.shape
+    p = PRECS[prec] if isinstance(prec, str) else prec
+    nb = C.c_size_t()
+    _check(lib().cabs_threshold_workspace_size(M, C.byref(nb)))
+    ws = _ws(nb.value, dev)
+    wp, wn = _aligned(ws)
+    srt = torch.empty(k2, dtype=torch.int32, device=dev)
+    _check(lib().cabs_threshold(ctx.h, _ptr(X), M, d, k2, p, _ptr(srt), wp, wn, _stream(stream)), ctx.h)
+    return srt
 
 
 # -------------------------------------------------------------- profiling

@@ -51,6 +51,13 @@ int sm_count() {
   return cache[dev];
 }
 
+static thread_local int t_sharers = 1;
+
+SharersScope::SharersScope(int sharers) : prev(t_sharers) { t_sharers = sharers < 1 ? 1 : sharers; }
+SharersScope::~SharersScope() { t_sharers = prev; }
+
+int coop_grid_cap(int full) { return std::max(16, full / t_sharers); }
+
 DeviceGuard::DeviceGuard(int dev) {
   ok = cudaGetDevice(&prev) == cudaSuccess;
   if (ok && prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
@@ -93,7 +100,8 @@ cabs_status validate_params(const cabs_params* p) {
   CABS_REQUIRE(p->core == CABS_CORE_PINV || p->core == CABS_CORE_STABILIZED, "unknown core %d", p->core);
   CABS_REQUIRE(finite(p->upsilon_pow), "upsilon_pow must be finite");
   CABS_REQUIRE(finite(p->trunc_rtol) && p->trunc_rtol >= 0.0, "trunc_rtol must be finite and >= 0");
-  CABS_REQUIRE((p->flags & ~(CABS_FLAG_FOLLOW_ERR | CABS_FLAG_ERROR)) == 0, "unknown flags 0x%x", p->flags);
+  CABS_REQUIRE((p->flags & ~(CABS_FLAG_FOLLOW_ERR | CABS_FLAG_ERROR | CABS_FLAG_HARD_THRESHOLD)) == 0,
+               "unknown flags 0x%x", p->flags);
   if (p->flags & CABS_FLAG_ERROR) CABS_REQUIRE(p->err_samples >= 0, "err_samples must be >= 0");
   return CABS_OK;
 }
@@ -130,8 +138,8 @@ SketchWs carve_sketch(Carve& cv, const cabs_source& src, const cabs_params& p) {
   const size_t core_b = std::max(core_ws_bytes(m, n, k1, eb == 8), core_ws_bytes(m, n, k2, eb == 8));
   size_t side_r = std::max(kmeans_ws_bytes(m, k1, k2, p.iters, p.prec), snap_ws_bytes(m, k1, k2, p.prec));
   size_t side_c = std::max(kmeans_ws_bytes(n, k1, k2, p.iters, p.prec), snap_ws_bytes(n, k1, k2, p.prec));
-  side_r = std::max(side_r, kmeans_ws_bytes(m, k1, k2, 1, p.prec));
-  side_c = std::max(side_c, kmeans_ws_bytes(n, k1, k2, 1, p.prec));
+  side_r = std::max({side_r, kmeans_ws_bytes(m, k1, k2, 1, p.prec), threshold_ws_bytes(m)});
+  side_c = std::max({side_c, kmeans_ws_bytes(n, k1, k2, 1, p.prec), threshold_ws_bytes(n)});
   w.core_bytes = align256(core_b);
   w.side_r_bytes = align256(side_r);
   w.side_c_bytes = align256(side_c);
@@ -185,17 +193,23 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   CABS_TRY(launch_gather(src, m, n, out.pilot_rows, k1, out.pilot_cols, k1, f64, w.C, w.Rt, w.W, s));
   // step 2: pilot sketching and embeddings P, Q
   CABS_TRY(launch_core(m, n, k1, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, true, w.P, w.S_pilot, w.Q,
-                       &dg->rank_pilot, &dg->sweeps_pilot, &dg->status, nullptr, nullptr, nullptr, w.core,
+                       &dg->rank_pilot, &dg->sweeps_pilot, &dg->refine_pilot, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
-  // step 3: weighted k-means on P and Q, snap to rows
-  CABS_TRY(launch_kmeans(w.P, m, k1, w.pr_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zr, dg->e_rows,
-                         &dg->T_rows, &dg->rechecked, w.side_r, w.side_r_bytes, s));
-  CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
-                         &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, s));
-  CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes,
-                       &dg->snap_fallbacks, s));
-  CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
-                       &dg->snap_fallbacks, s));
+  if (p.flags & CABS_FLAG_HARD_THRESHOLD) {
+    // step 3, hard-threshold variant (Section 5): largest-norm rows of P and Q
+    CABS_TRY(launch_threshold(w.P, m, k1, k2, p.prec, out.rows, w.side_r, w.side_r_bytes, s));
+    CABS_TRY(launch_threshold(w.Q, n, k1, k2, p.prec, out.cols, w.side_c, w.side_c_bytes, s));
+  } else {
+    // step 3: weighted k-means on P and Q, snap to rows
+    CABS_TRY(launch_kmeans(w.P, m, k1, w.pr_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zr, dg->e_rows,
+                           &dg->T_rows, &dg->rechecked, w.side_r, w.side_r_bytes, s));
+    CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
+                           &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, s));
+    CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes,
+                         &dg->snap_fallbacks, s));
+    CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
+                         &dg->snap_fallbacks, s));
+  }
   if (p.flags & CABS_FLAG_FOLLOW_ERR) {
     CABS_TRY(launch_encoding_error(w.P, m, k1, out.rows, k2, p.prec, p.upsilon_pow, &dg->e_follow_rows, w.side_r,
                                    w.side_r_bytes, s));
@@ -205,7 +219,7 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   // steps 3-4: follow-up gather and sketching
   CABS_TRY(launch_gather(src, m, n, out.rows, k2, out.cols, k2, f64, w.C, w.Rt, w.W, s));
   CABS_TRY(launch_core(m, n, k2, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, out.U, out.S, out.V,
-                       &dg->rank_final, &dg->sweeps_final, &dg->status, nullptr, nullptr, nullptr, w.core,
+                       &dg->rank_final, &dg->sweeps_final, &dg->refine_final, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
   // Section 5: relative Frobenius error of the result
   if (p.flags & CABS_FLAG_ERROR) {
@@ -394,7 +408,7 @@ cabs_status cabs_sketching(cabs_ctx* ctx, int64_t m, int64_t n, int32_t k, int32
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
   return launch_core(m, n, k, prec == CABS_PREC_FP64, core, trunc_rtol, C, Rt, W, embed != 0, out1, S, out2, d_rank,
-                     d_sweeps, nullptr, d_sig, d_Uw, d_Vw, ws, ws_bytes, (cudaStream_t)stream);
+                     d_sweeps, nullptr, nullptr, d_sig, d_Uw, d_Vw, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 cabs_status cabs_kmeans_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t iters, int32_t prec, size_t* bytes) {
@@ -444,6 +458,26 @@ cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const 
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
   return launch_snap(X, M, d, Z, k2, prec, d_order, d_sorted, ws, ws_bytes, nullptr, (cudaStream_t)stream);
+}
+
+cabs_status cabs_threshold_workspace_size(int64_t M, size_t* bytes) {
+  clear_error();
+  CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
+  CABS_REQUIRE(M >= 1 && M < INT32_MAX, "M outside [1, 2^31)");
+  *bytes = threshold_ws_bytes(M);
+  return CABS_OK;
+}
+
+cabs_status cabs_threshold(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, int32_t k2, int32_t prec,
+                           int32_t* d_sorted, void* ws, size_t ws_bytes, cabs_stream stream) {
+  clear_error();
+  CABS_REQUIRE(ctx != nullptr, "ctx is NULL");
+  CABS_REQUIRE(M >= 1 && M < INT32_MAX && d >= 1 && k2 >= 1 && k2 <= M, "bad M, d, k2");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
+  CABS_REQUIRE(X && d_sorted, "NULL input or output");
+  CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
+  DeviceGuard g(ctx->device);
+  return launch_threshold(X, M, d, k2, prec, d_sorted, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -499,6 +533,7 @@ static cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* 
   if (cudaEventRecord(ctx->fork_event, s) != cudaSuccess) return check_cuda("fork record");
   for (int l = 0; l < lanes; ++l)
     if (cudaStreamWaitEvent(ctx->lanes[l], ctx->fork_event, 0) != cudaSuccess) return check_cuda("fork wait");
+  SharersScope sharing(std::min(lanes, count));
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
     const size_t need = sketch_ws_bytes(src[i], p[i]);

@@ -169,4 +169,17 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Largest grid for a kernel whose CTAs wait on one another (a cooperative
+// launch with a grid barrier). Alone, such a kernel may fill the GPU; while
+// `sharers` sketches run concurrently (batched lanes, serving slots), its CTAs
+// would otherwise sit at the barrier holding SMs until the other sketches'
+// kernels drain, so the grid is divided among the sharers. The work split
+// does not change any result.
+int coop_grid_cap(int full);
+struct SharersScope {
+  explicit SharersScope(int sharers);
+  ~SharersScope();
+  int prev;
+};
+
 }  // namespace cabs

@@ -160,7 +160,7 @@ CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
 template <typename T>
 cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol, const T* C, const T* Rt,
                        const double* W, bool embed, T* out1, double* S, T* out2, int* d_rank, int* d_sweeps,
-                       int* d_status, double* d_sig, double* d_Uw, double* d_Vw, void* ws, size_t ws_bytes,
+                       int* d_refine, int* d_status, double* d_sig, double* d_Uw, double* d_Vw, void* ws, size_t ws_bytes,
                        cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
   CoreWs w = carve_core(cv, m, n, k);
@@ -173,7 +173,7 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   double* Vw = d_Vw ? d_Vw : w.Vw;
   int* rank = d_rank ? d_rank : w.rank;
   int* sweeps = d_sweeps ? d_sweeps : w.sweeps;
-  CABS_TRY(launch_svd(W, k, trunc_rtol, sig, Uw, Vw, rank, sweeps, d_status, w.svd, stream));
+  CABS_TRY(launch_svd(W, k, trunc_rtol, sig, Uw, Vw, rank, sweeps, d_refine, d_status, w.svd, stream));
   const int nb1 = ceil_div(m, kGBM), nb2 = ceil_div(n, kGBM);
   dim3 g1(ceil_div(k, kGBN), nb1), g2(ceil_div(k, kGBN), nb2);
   CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));
@@ -197,14 +197,14 @@ size_t core_ws_bytes(int64_t m, int64_t n, int k, bool /*elem_f64*/) {
 
 cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
                         const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
-                        int* d_rank, int* d_sweeps, int* d_status, double* d_sig, double* d_Uw, double* d_Vw,
-                        void* ws, size_t ws_bytes, cudaStream_t stream) {
+                        int* d_rank, int* d_sweeps, int* d_refine, int* d_status, double* d_sig, double* d_Uw,
+                        double* d_Vw, void* ws, size_t ws_bytes, cudaStream_t stream) {
   if (elem_f64)
     return core_typed<double>(m, n, k, core, trunc_rtol, (const double*)C, (const double*)Rt, W, embed,
-                              (double*)out1, S, (double*)out2, d_rank, d_sweeps, d_status, d_sig, d_Uw, d_Vw, ws,
+                              (double*)out1, S, (double*)out2, d_rank, d_sweeps, d_refine, d_status, d_sig, d_Uw, d_Vw, ws,
                               ws_bytes, stream);
   return core_typed<float>(m, n, k, core, trunc_rtol, (const float*)C, (const float*)Rt, W, embed, (float*)out1, S,
-                           (float*)out2, d_rank, d_sweeps, d_status, d_sig, d_Uw, d_Vw, ws, ws_bytes, stream);
+                           (float*)out2, d_rank, d_sweeps, d_refine, d_status, d_sig, d_Uw, d_Vw, ws, ws_bytes, stream);
 }
 
 }  // namespace cabs

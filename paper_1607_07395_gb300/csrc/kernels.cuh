@@ -19,8 +19,8 @@ cabs_status launch_gather(const cabs_source& src, int64_t m, int64_t n, const in
 size_t core_ws_bytes(int64_t m, int64_t n, int k, bool elem_f64);
 cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
                         const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
-                        int* d_rank, int* d_sweeps, int* d_status, double* d_sig, double* d_Uw, double* d_Vw,
-                        void* ws, size_t ws_bytes, cudaStream_t stream);
+                        int* d_rank, int* d_sweeps, int* d_refine, int* d_status, double* d_sig, double* d_Uw,
+                        double* d_Vw, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 // a5: weighted k-means.
 size_t kmeans_ws_bytes(int64_t M, int d, int k2, int iters, int prec);
@@ -35,6 +35,11 @@ cabs_status launch_encoding_error(const void* X, int64_t M, int d, const int* re
 size_t snap_ws_bytes(int64_t M, int d, int k2, int prec);
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
                         void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream);
+
+// Section 5 follow-up variant (f): the k2 largest-norm rows of X, sorted.
+size_t threshold_ws_bytes(int64_t M);
+cabs_status launch_threshold(const void* X, int64_t M, int d, int k2, int prec, int* sorted, void* ws,
+                             size_t ws_bytes, cudaStream_t stream);
 
 // a9: relative Frobenius error.
 size_t error_ws_bytes(const cabs_source& src, int64_t m, int64_t n, int k, int64_t samples, int prec);

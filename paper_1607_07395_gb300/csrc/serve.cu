@@ -176,6 +176,7 @@ static void schedule_once(ServeState* st) {
     r.res = result_at(st->arena + roff, r.p);
     r.slot = slot;
     r.state = ReqState::Running;
+    SharersScope sharing((int)st->streams.size());
     const cabs_status s = sketch_enqueue(r.src, r.p, st->arena + woff, r.ws_bytes, st->streams[slot], r.res);
     if (s != CABS_OK || cudaEventRecord(st->events[slot], st->streams[slot]) != cudaSuccess) {
       cudaGetLastError();

@@ -348,7 +348,7 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* or
   CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
-  const int G = std::max(1, std::min({(int)ceil_div(M, 2048), sm_count() * std::max(per_sm, 1), 1024}));
+  const int G = std::max(1, std::min({(int)ceil_div(M, 2048), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
   CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb));
   const T* Xc = X;
   const T* Zc = Z;

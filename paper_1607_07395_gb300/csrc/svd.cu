@@ -42,8 +42,8 @@ namespace {
 constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
 constexpr float kTolA = 1e-5f;          // Phase A rotation threshold |g| > tol sqrt(a b)
 constexpr int kMaxSweepsA = 40;
-constexpr double kTolB = 1e-12;         // Phase B: converged when max |F_ij|, |G_ij| (i != j) < tol
 constexpr int kItersB = 6;
+constexpr double kConvB = 1e-8;         // Phase B: last iteration when max |F_ij|, |G_ij| (i != j) < this
 constexpr int kNotDone = 0x7fffffff;
 
 __device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& q) {
@@ -99,11 +99,20 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
   float xr[R], yr[R];
   const float4* x4 = (const float4*)(x + lane * R);
   const float4* y4 = (const float4*)(y + lane * R);
+  // the V columns are read up front, so their latency hides behind the reductions
+  float4 pv[R / 4], qv[R / 4];
+  const float4* vx4 = (const float4*)(vx + lane * R);
+  const float4* vy4 = (const float4*)(vy + lane * R);
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
     const float4 a = x4[i], b = y4[i];
     xr[4 * i] = a.x; xr[4 * i + 1] = a.y; xr[4 * i + 2] = a.z; xr[4 * i + 3] = a.w;
     yr[4 * i] = b.x; yr[4 * i + 1] = b.y; yr[4 * i + 2] = b.z; yr[4 * i + 3] = b.w;
+  }
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) {
+    pv[i] = vx4[i];
+    qv[i] = vy4[i];
   }
   float a = 0.f, b = 0.f, g = 0.f;
 #pragma unroll
@@ -139,7 +148,7 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
   float4* vyo = (float4*)(vy + lane * R);
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
-    const float4 p = vxo[i], q = vyo[i];
+    const float4 p = pv[i], q = qv[i];
     float4 p2, q2;
     p2.x = c * p.x - s * q.x; q2.x = s * p.x + c * q.x;
     p2.y = c * p.y - s * q.y; q2.y = s * p.y + c * q.y;
@@ -229,16 +238,16 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   float* buf0 = cs;
   float* buf1 = cs + 4 * blk;
   __shared__ int rot_flag[2];
-  __shared__ int top_id[32], bot_id[32];
-  if (tid < NC) {
-    top_id[tid] = tid;
-    bot_id[tid] = 2 * NC - 1 - tid;
-  }
+  // CTA c starts with blocks c (top) and 2 NC - 1 - c (bottom). Block 0 stays;
+  // the other 2 NC - 1 move one place around the circle per round, so after
+  // the 2 NC - 1 rounds of a sweep every block is back where it started and
+  // every pair of blocks has met once.
+  const int ids[2] = {c, 2 * NC - 1 - c};
   if (tid < 2) rot_flag[tid] = 0;
   __syncthreads();
   // load my two blocks into buf0
   for (int slot = 0; slot < 2; ++slot) {
-    const int B = slot == 0 ? top_id[c] : bot_id[c];
+    const int B = ids[slot];
     float* w = buf0 + slot * blk;
     float* v = buf0 + (2 + slot) * blk;
     for (int e = tid; e < (int)blk; e += blockDim.x) {
@@ -309,26 +318,6 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
           dWb[e] = srcWb[e];
           dVb[e] = srcVb[e];
         }
-        if (tid == 0) {
-          // every CTA updates its replica of the block placement identically
-          int nt[32], nb[32];
-          for (int i = 0; i < NC; ++i) {
-            nt[i] = top_id[i];
-            nb[i] = bot_id[i];
-          }
-          for (int i = 0; i < NC; ++i) {
-            const int dt = (i == 0) ? 0 : (i == NC - 1 ? NC - 1 : i + 1);
-            const int dts = (i == 0) ? 0 : (i == NC - 1 ? 1 : 0);
-            const int db = (i == 0) ? 1 : i - 1;
-            const int dbs = (i == 0) ? 0 : 1;
-            if (dts == 0) nt[dt] = top_id[i]; else nb[dt] = top_id[i];
-            if (dbs == 0) nt[db] = bot_id[i]; else nb[db] = bot_id[i];
-          }
-          for (int i = 0; i < NC; ++i) {
-            top_id[i] = nt[i];
-            bot_id[i] = nb[i];
-          }
-        }
       }
       cluster.sync();
       // every CTA has read last sweep's flags before arriving here, so the
@@ -346,8 +335,7 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
     conv = any == 0;
     ++sweep;
   }
-  // write out my two blocks
-  const int ids[2] = {top_id[c], bot_id[c]};
+  // write out my two blocks (back at their starting places after whole sweeps)
   for (int slot = 0; slot < 2; ++slot) {
     for (int j = warp; j < b; j += nwarps) {
       const int gc = ids[slot] * b + j;
@@ -487,9 +475,13 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
       if (which == 0) gemm_tile(k, y % nt, y / nt, U, 0, a.F, U, Un, As, Bs);
       else gemm_tile(k, y % nt, y / nt, V, 0, a.G, V, Vn, As, Bs);
     }
-    // quadratic convergence, or a plateau at the rounding floor
+    // Quadratic convergence: the update just applied used corrections of size
+    // m, so it leaves an error of order m^2 (times the inverse relative gap of
+    // the pairs that still rotate); at m < kConvB that is below the FP64
+    // rounding floor and no verifying iteration is needed. Or a plateau at the
+    // rounding floor (clustered values whose corrections stop shrinking).
     const double m = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + t));
-    const bool conv = m < 1e-10 || (t >= 1 && m < 1e-7 && m > 0.25 * prev);
+    const bool conv = m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev);
     prev = m;
     if (!grid_sync(a.bar, nb)) return;
     if (conv) {
@@ -507,10 +499,11 @@ __global__ void __launch_bounds__(256) refine_final_kernel(int k, double trunc_r
                                                            const double* __restrict__ Vbuf1, const double* __restrict__ d,
                                                            const int* __restrict__ done_iter, int iters,
                                                            double* __restrict__ sig_out, double* __restrict__ Uw_out,
-                                                           double* __restrict__ Vw_out, int* rank_out, int* status,
-                                                           const GridBarrier* __restrict__ bar) {
+                                                           double* __restrict__ Vw_out, int* rank_out, int* refine_out,
+                                                           int* status, const GridBarrier* __restrict__ bar) {
   const int done = *done_iter;
   if (threadIdx.x == 0 && status && bar->err) atomicOr(status, 4);
+  if (threadIdx.x == 0 && refine_out) *refine_out = done == kNotDone ? -1 : done + 1;
   if (done == kNotDone) {
     if (threadIdx.x == 0 && status) atomicOr(status, 2);
     return;  // the FP64 Jacobi fallback writes the outputs
@@ -790,7 +783,7 @@ static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0
 }
 
 cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
-                       int* sweeps, int* status, const SvdWs& w, cudaStream_t stream) {
+                       int* sweeps, int* refine, int* status, const SvdWs& w, cudaStream_t stream) {
   // ---- Phase A: FP32 Jacobi -> U[0], V[0]
   if (k <= kCtaMaxK) {
     const size_t smem = (size_t)2 * k * k * sizeof(float);
@@ -810,7 +803,7 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
     const int tiles = ceil_div(k, kGT) * ceil_div(k, kGT);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_persistent_kernel, 256, 0);
-    const int grid = std::max(1, std::min(tiles, sm_count() * std::max(per_sm, 1)));
+    const int grid = std::max(1, std::min(tiles, coop_grid_cap(sm_count() * std::max(per_sm, 1))));
     RefineArgs ra{k, W, w.U[0], w.U[1], w.V[0], w.V[1], w.P, w.T, w.UtU, w.VtV, w.F, w.G, w.d, w.maxoff,
                   w.done_iter, w.bar, status};
     void* args[] = {&ra};
@@ -820,7 +813,8 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
   }
   CABS_LAUNCH(stream, "refine_final_kernel",
               refine_final_kernel<<<1, 256, 0, stream>>>(k, trunc_rtol, w.U[0], w.U[1], w.V[0], w.V[1], w.d,
-                                                         w.done_iter, kItersB, sig, Uw, Vw, rank, status, w.bar));
+                                                         w.done_iter, kItersB, sig, Uw, Vw, rank, refine, status,
+                                                         w.bar));
   // ---- fallback: FP64 Jacobi (exits at once when Phase B converged)
   return launch_svd_jacobi_f64(W, k, trunc_rtol, w.done_iter, w.Wc, w.Vc, sig, Uw, Vw, rank, sweeps, status, stream);
 }

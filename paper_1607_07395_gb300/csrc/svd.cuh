@@ -19,9 +19,11 @@ struct SvdWs {
 SvdWs carve_svd(Carve& cv, int k);
 
 // W (k x k row-major, FP64) -> sig (k, descending), Uw, Vw (k x k row-major,
-// column r = r-th singular vector, zero beyond the kept rank), *rank, *sweeps.
+// column r = r-th singular vector, zero beyond the kept rank), *rank, *sweeps
+// (FP32 Jacobi sweeps), *refine (FP64 refinement iterations, -1 when the FP64
+// Jacobi fallback ran; may be NULL).
 cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
-                       int* sweeps, int* status, const SvdWs& w, cudaStream_t stream);
+                       int* sweeps, int* refine, int* status, const SvdWs& w, cudaStream_t stream);
 
 // One-CTA FP64 one-sided Jacobi; does nothing if *done_iter != INT_MAX
 // (done_iter may be NULL: always run).

@@ -10,7 +10,9 @@
 // |z|^2 - 2 x . z, keeping the best and second-best centre; warps holding
 // the two column halves of a row merge through shared memory. When the two
 // best are closer than the rounding bound of the operands
-// (1.25 * 4u |x| (|z_a| + |z_b|), u = 2^-9 for BF16, 2^-12 for TF32), the
+// (1.25 * 4u |x| (|z_a| + |z_b|); u = 2^-8 for BF16, which keeps 8 significant
+// bits and rounds to nearest, and 2^-10 for TF32, whose 11 significant bits
+// the tensor core may take by truncation), the
 // row is flagged and a separate coalesced pass recomputes both distances in
 // FP32 by direct differences; the smaller wins (ties to the lower index). The weighted encoding error is computed afterwards by
 // a separate pass with direct differences (k-means kernel file).
@@ -91,9 +93,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     const int e = warp - tc::kEpiWarp0;
     const int sub = warp & 3, half = e >> 2;
     const int row = sub * 32 + lane;
-    // |error of |z|^2 - 2 x.z| <= 4 u |x| |z| for operand rounding u (2^-9 BF16,
-    // 2^-12 TF32); a 1.25x margin covers the FP32 accumulation
-    const float rel = kTF32 ? 0.0012207f : 0.0097656f;
+    // the difference of two rounded contractions 2 x.z_a - 2 x.z_b is off by at
+    // most 4 u |x| (|z_a| + |z_b|) for operand rounding u (2^-8 BF16, 2^-10
+    // TF32); a 1.25x margin covers the FP32 accumulation
+    const float rel = kTF32 ? 0.0048828125f : 0.01953125f;
     int ab = 0;
     uint32_t accph[2] = {0, 0};
     for (int u = u0; u < u1; ++u) {

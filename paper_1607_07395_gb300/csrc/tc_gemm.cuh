@@ -40,9 +40,11 @@ struct alignas(8) Barriers {
   int abort;
 };
 
-// Dynamic shared memory layout: [B resident: nch x BN x 128 B][A ring: kStages x 128 x 128 B]
+// Dynamic shared memory layout: [B resident: nch x BN x 128 B][A ring: kSt x 128 x 128 B]
+// (kSt <= kStages ring stages; a kernel may append its own buffers after it).
+template <int kSt = kStages>
 __host__ __device__ constexpr size_t smem_bytes(int nch, int BN) {
-  return (size_t)nch * BN * 128 + (size_t)kStages * kBM * 128 + 1024 /* alignment slack */;
+  return (size_t)nch * BN * 128 + (size_t)kSt * kBM * 128 + 1024 /* alignment slack */;
 }
 
 __device__ __forceinline__ void unit_of(int u, int MT, int& cb, int& rt) {
@@ -50,7 +52,7 @@ __device__ __forceinline__ void unit_of(int u, int MT, int& cb, int& rt) {
   rt = u - cb * MT;
 }
 
-template <int BN>
+template <int BN, int kSt = kStages>
 __device__ __forceinline__ void producer_loop(const CUtensorMap* tmA, const CUtensorMap* tmB, uint8_t* Bres,
                                               uint8_t* Aring, Barriers* bars, int u0, int u1, int MT, int nch,
                                               int kc_elems) {
@@ -75,7 +77,7 @@ __device__ __forceinline__ void producer_loop(const CUtensorMap* tmA, const CUte
       if (!mbar_wait(&bars->empty[s], ph ^ 1, abort)) return;
       mbar_expect_tx(&bars->full[s], (uint32_t)(kBM * 128));
       tma_load_2d(Aring + (size_t)s * kBM * 128, tmA, &bars->full[s], c * kc_elems, rt * kBM);
-      if (++s == kStages) {
+      if (++s == kSt) {
         s = 0;
         ph ^= 1;
       }
@@ -83,7 +85,7 @@ __device__ __forceinline__ void producer_loop(const CUtensorMap* tmA, const CUte
   }
 }
 
-template <bool kTF32, int BN>
+template <bool kTF32, int BN, int kSt = kStages>
 __device__ __forceinline__ void mma_loop(uint8_t* Bres, uint8_t* Aring, Barriers* bars, int u0, int u1, int MT,
                                          int nch) {
   volatile int* abort = &bars->abort;
@@ -117,7 +119,7 @@ __device__ __forceinline__ void mma_loop(uint8_t* Bres, uint8_t* Aring, Barriers
       for (int kk = 0; kk < 4; ++kk)
         mma<kTF32>(dt, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (c > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&bars->empty[s]);
-      if (++s == kStages) {
+      if (++s == kSt) {
         s = 0;
         ph ^= 1;
       }

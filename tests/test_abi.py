@@ -52,7 +52,7 @@ int main(void) {
   F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma)
   F(cabs_params, seed) F(cabs_params, upsilon_pow) F(cabs_params, trunc_rtol) F(cabs_params, flags)
   F(cabs_params, err_samples) F(cabs_params, err_seed)
-  F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_result, diag) F(cabs_result, err)
+  F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_diag, refine_final) F(cabs_diag, reserved) F(cabs_result, diag) F(cabs_result, err)
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -112,7 +112,7 @@ def test_error_request_on_host(L):
     assert n1.value >= n0.value + e.value - 256
     ps = cabs.make_params(2000, 1500, 20, prec="fp32", err_samples=10 ** 6)
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(ps), C.byref(n2)) == cabs.CABS_OK
-    bad = cabs.make_params(2000, 1500, 20, flags=4)
+    bad = cabs.make_params(2000, 1500, 20, flags=8)  # no such flag
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(bad), C.byref(n0)) == cabs.CABS_EINVAL
     neg = cabs.make_params(2000, 1500, 20, err_samples=0)
     neg.err_samples = -1

@@ -337,3 +337,42 @@ def test_core_svd_fp64(ctx, C, k, kind):
     assert np.abs(Vw[:, :r].T @ Vw[:, :r] - np.eye(r)).max() <= 1e-12
     rec = (Uw[:, :r] * sig[:r]) @ Vw[:, :r].T
     assert np.linalg.norm(rec - W) <= 1e-12 * np.linalg.norm(W)
+
+
+# ------------------------------------- hard-threshold follow-up (Section 5 (f))
+
+@pytest.mark.parametrize("M,d,k2", [(1, 1, 1), (5000, 20, 20), (70000, 256, 256), (3001, 7, 3001), (1025, 33, 17)])
+def test_threshold_fp64_bit_exact(ctx, C, M, d, k2):
+    g = np.random.default_rng(M + d)
+    X = g.standard_normal((M, d)) * g.uniform(0.5, 2.0, size=(M, 1))
+    if M > 20:
+        X[10] = X[3]   # equal norms: the lower row wins wherever the cut falls
+        X[17] = -X[3]
+    got = to_np(C.cabs_threshold(ctx, dev(X), k2, prec="fp64"))
+    assert got.tolist() == o.hard_threshold(X, k2).tolist()
+
+
+def test_threshold_fp32_and_all_equal(ctx, C):
+    g = np.random.default_rng(4)
+    X = (g.standard_normal((3000, 24)) * g.uniform(0.5, 2.0, size=(3000, 1))).astype(np.float32)
+    got = to_np(C.cabs_threshold(ctx, dev(X), 50, prec="fp32"))
+    assert got.tolist() == o.hard_threshold(X.astype(np.float64), 50).tolist()
+    ones = np.ones((777, 5))
+    assert to_np(C.cabs_threshold(ctx, dev(ones), 9, prec="fp64")).tolist() == list(range(9))
+
+
+@pytest.mark.parametrize("mode", ["pinv", "stabilized"])
+def test_plain_fp64_threshold_sketch_matches_oracle(ctx, C, mode):
+    A = synth.plain_lowrank()
+    m, n = A.shape
+    Ad = dev(A)
+    p = C.make_params(m, n, 20, iters=5, seed=1607, prec="fp64", core=mode, flags=C.FLAG_HARD_THRESHOLD)
+    sk = C.cabs_sketch(ctx, C.dense_source(Ad), p)
+    ref = o.cabs(o.DenseSource(A), 20, iters=5, seed=1607, mode=mode, follow="threshold")
+    assert to_np(sk.rows).tolist() == ref.rows.tolist()
+    assert to_np(sk.cols).tolist() == ref.cols.tolist()
+    U, S, V = to_np(sk.U), to_np(sk.S), to_np(sk.V)
+    want = (ref.final.U * ref.final.S) @ ref.final.V.T
+    assert np.linalg.norm((U * S) @ V.T - want) <= 1e-10 * np.linalg.norm(want)
+    d = sk.diag()
+    assert d.rank_final == ref.final.rank and d.status == 0 and list(d.e_rows)[:5] == [0.0] * 5
