@@ -147,7 +147,7 @@ def make_source(cabs, wl, inp):
 
 # ------------------------------------------------------- algorithmic units
 
-def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps):
+def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps, svd_refine=None):
     """(bound, algorithmic amount per step, unit, launches per step) of a kernel.
 
     Per-unit figures: gathers read one 32-byte DRAM sector per scattered
@@ -177,6 +177,12 @@ def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps):
         return "alu", iters * 2.0 * (m + n) * k * d, "TFLOP/s", 2 * iters
     if name == "tc_assign_kernel":
         return "tensor", iters * 2.0 * (m + n) * k * kp, "TFLOP/s", 2 * iters
+    if name == "tc_snap_kernel":
+        return "tensor", 2.0 * (m + n) * k * kp, "TFLOP/s", 2
+    if name == "refine_persistent_kernel":
+        # iterations x (W V, U^T P, U^T U, V^T V, U F, V G): 6 k^3 multiply-adds, FP64
+        its = sum(max(r, 0) for r in (svd_refine or (3, 3)))
+        return "alu", its * 6 * 2.0 * k ** 3, "TFLOP/s", 2
     if name == "snap_cand_kernel":
         return "alu", 3.0 * (m + n) * k * d, "TFLOP/s", 2
     if name.startswith("extrap_gemm_kernel"):
@@ -190,16 +196,33 @@ def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps):
     return None
 
 
-def roofline(prof, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec):
-    """Roofline of the kernel with the largest device time in the timed region."""
-    if not prof:
-        return None, None
-    name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    info = algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps)
-    table = {nm: dict(launches=l, total_ms=round(t, 4), share=round(t / sum(x[1] for x in prof.values()), 4))
-             for nm, (l, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+def kernel_traffic(name, workload):
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/ncu_traffic.json), or None when there is none for this workload
+    or the kernel's source file has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = table.get(workload, {}).get(name)
+    if not e:
+        return None
+    try:
+        with open(os.path.join(ROOT, e["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != e["source_sha256"]:
+                return None
+    except OSError:
+        return None
+    return dict(bytes=int(e["dram_bytes_per_launch"]), captured_on=e["captured_on"], scaled=e.get("scaled"))
+
+
+def roofline_of(name, launches, ms, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec, workload,
+                svd_refine=None):
+    info = algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps, svd_refine)
     if info is None:
-        return dict(kernel=name, bound=None, achieved=None, peak=None, unit=None, frac=None, traffic=None), table
+        return dict(kernel=name, bound=None, achieved=None, peak=None, unit=None, frac=None, traffic=None)
     bound, amount, unit, _ = info
     secs = ms / 1e3
     achieved = amount * steps / secs / (1e12 if unit == "TFLOP/s" else 1e9)
@@ -212,9 +235,25 @@ def roofline(prof, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec):
         fp64 = name in ("svd_jacobi_kernel", "refine_persistent_kernel") or (prec == "fp64" and not name.startswith("svd32"))
         peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
         src = "derived from unit counts x 2.07 GHz"
+    tr = kernel_traffic(name, workload)
     return dict(kernel=name, bound=bound, achieved=round(achieved, 4), peak=round(peak, 3), unit=unit,
-                frac=round(achieved / peak, 5), traffic=None, peak_source=src,
-                avg_launch_ms=round(ms / max(launches, 1), 5)), table
+                frac=round(achieved / peak, 5), traffic=tr["bytes"] if tr else None, peak_source=src,
+                avg_launch_ms=round(ms / max(launches, 1), 5),
+                traffic_source=(f"ncu capture ({tr['captured_on']})" + (f", {tr['scaled']}" if tr.get("scaled") else ""))
+                if tr else None)
+
+
+def roofline(prof, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec, workload, svd_refine=None):
+    """Roofline of the kernel with the largest device time in the timed region
+    (and of the next ones, for context), plus the per-kernel time table."""
+    if not prof:
+        return None, None, None
+    total = sum(x[1] for x in prof.values())
+    order = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    table = {nm: dict(launches=l, total_ms=round(t, 4), share=round(t / total, 4)) for nm, (l, t) in order}
+    rl = [roofline_of(nm, l, t, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec, workload, svd_refine)
+          for nm, (l, t) in order[:6]]
+    return rl[0], table, rl[1:]
 
 
 # ------------------------------------------------------------------ clocks
@@ -534,7 +573,9 @@ def run_cabs(args):
         return None
     peaks = load_peaks()
     eb = 8 if prec == "fp64" else 4
-    roof, table = roofline(prof, wl, k, iters, eb, sweeps, args.steps * B, peaks, prec)
+    roof, table, roof_next = roofline(prof, wl, k, iters, eb, sweeps, args.steps * B, peaks, prec,
+                                      args.workload if not (args.m or args.n) else None,
+                                      [diag.refine_pilot, diag.refine_final])
     gather = None
     if wl["kind"] in ("dense", "plain") and "gather_cols_kernel" in prof:
         gl, gms = prof["gather_cols_kernel"]
@@ -566,13 +607,13 @@ def run_cabs(args):
                diag=dict(svd_sweeps=sweeps, svd_refine=[diag.refine_pilot, diag.refine_final],
                          svd_status=int(diag.status), rank=[diag.rank_pilot, diag.rank_final],
                          snap_fallbacks=int(diag.snap_fallbacks), rechecked=int(diag.rechecked)),
-               roofline=roof, kernels=table,
+               roofline=roof, roofline_next=roof_next, kernels=table,
                kernel_timing=("serial profiled pass of the same batch after the timed region" if B > 1
                               else "timed region"),
                gather=gather, plain_fp32=plain, e2e=e2e, clocks=clocks)
     if wl["kind"] == "dense" and "L" in inp:
         res["rel_fro_error_noiseless"] = noiseless_error(inp["L"], outs[0])
-    if wl["kind"] != "plain" and not (args.m or args.n):
+    if wl["kind"] != "plain" and not (args.m or args.n) and not args.no_precision:
         res["precision"] = precision_excess(cabs, ctx, wl, device)
     if not args.no_cpu:
         res["cpu_baseline"] = run_cpu_baseline(args.workload, args.cpu_steps)
@@ -616,6 +657,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the workload's columns (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-mode error report on the slice")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -293,8 +293,8 @@ cabs_status cabs_kmeans(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, cons
  * of X (M x d, elem) not yet picked, ties to the lowest row index; distances
  * by direct differences in elem. In the BF16 and TF32 modes (k2 <= 256) the
  * candidates are first ranked by |x|^2 - 2 x.z on tensor cores, and each
- * centre's 32 best are re-ranked by direct distance (computed in FP64 from
- * the FP32 inputs) before the walk.
+ * centre's 32 best are re-ranked by the same direct FP32 distance as in FP32
+ * mode before the walk.
  * d_order (k2, pick order) and d_sorted (k2, ascending) are device int32.
  * ws: cabs_snap_workspace_size() bytes. */
 cabs_status cabs_snap_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t prec, size_t* bytes);

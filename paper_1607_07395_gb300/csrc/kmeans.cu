@@ -266,8 +266,9 @@ constexpr int kUMaxPerLane = CABS_MAX_K / 32;
 
 template <typename T>
 __device__ __forceinline__ void accumulate_members(unsigned mask, long long base, const T* __restrict__ X, int d,
-                                                   const T* __restrict__ w, int lane, T (&acc)[kUMaxPerLane], T& wsum,
-                                                   int& cnt) {
+                                                   const T* __restrict__ w, int lane, const T* __restrict__ zc,
+                                                   bool want_e, T (&acc)[kUMaxPerLane], T& wsum, int& cnt,
+                                                   T& esum) {
   while (mask) {
     long long ls[4];
 #pragma unroll
@@ -296,6 +297,15 @@ __device__ __forceinline__ void accumulate_members(unsigned mask, long long base
       if (ls[u] >= 0) {
 #pragma unroll
         for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = fma(wv[u], xv[u][s], acc[s]);
+        if (want_e) {
+          T e = T(0);
+#pragma unroll
+          for (int s = 0; s < kUMaxPerLane; ++s) {
+            const T t = xv[u][s] - zc[lane + 32 * s];  // zero beyond d on both sides
+            e = fma(t, t, e);
+          }
+          esum = fma(wv[u], e, esum);
+        }
         wsum += wv[u];
         ++cnt;
       }
@@ -303,13 +313,23 @@ __device__ __forceinline__ void accumulate_members(unsigned mask, long long base
   }
 }
 
+constexpr int kULab = 4;  // label loads in flight per lane
+
+// One CTA per centre j: the weighted mean of its members (Eq. wkmeans); an
+// empty cluster keeps its centre. Warp i scans rows [M i / W, M (i + 1) / W)
+// in index order and the warps' sums are added in warp order, so the result
+// does not depend on timing. With energy != NULL the same pass also adds
+// w_l |x_l - z_j|^2 over the members with the centres the assignment used
+// (the iteration's weighted encoding error, per centre).
 template <typename T>
-__global__ void __launch_bounds__(kUWarps * 32) update_kernel(const T* __restrict__ X, long long M, int d,
+__global__ void __launch_bounds__(kUWarps * 32, sizeof(T) == 4 ? 2 : 1) update_kernel(const T* __restrict__ X, long long M, int d,
                                                               const int* __restrict__ labels, const T* __restrict__ w,
                                                               const T* __restrict__ Zcur, T* __restrict__ Znext,
-                                                              int* __restrict__ counts) {
+                                                              int* __restrict__ counts, double* __restrict__ energy) {
   __shared__ T accs[kUWarps][CABS_MAX_K];
+  __shared__ T zc[CABS_MAX_K];  // the centre the assignment used
   __shared__ T wsums[kUWarps];
+  __shared__ double esums[kUWarps];
   __shared__ int cnts[kUWarps];
   const int j = blockIdx.x;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -317,27 +337,31 @@ __global__ void __launch_bounds__(kUWarps * 32) update_kernel(const T* __restric
   T acc[kUMaxPerLane];
 #pragma unroll
   for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = T(0);
-  T wsum = T(0);
+  for (int q = threadIdx.x; q < CABS_MAX_K; q += blockDim.x) zc[q] = q < d ? Zcur[(size_t)j * d + q] : T(0);
+  __syncthreads();
+  T wsum = T(0), esum = T(0);
   int cnt = 0;
-  // four label loads in flight per lane; members are summed in index order
-  for (long long base = lo; base < hi; base += 128) {
-    int lab[4];
+  // kULab label loads in flight per lane; members are summed in index order
+  for (long long base = lo; base < hi; base += 32 * kULab) {
+    int lab[kULab];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kULab; ++u) {
       const long long l = base + 32 * u + lane;
       lab[u] = l < hi ? __ldg(labels + l) : -1;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kULab; ++u) {
       const unsigned mask = __ballot_sync(0xffffffffu, lab[u] == j);
-      accumulate_members<T>(mask, base + 32 * u, X, d, w, lane, acc, wsum, cnt);
+      accumulate_members<T>(mask, base + 32 * u, X, d, w, lane, zc, energy != nullptr, acc, wsum, cnt, esum);
     }
   }
 #pragma unroll
   for (int s = 0; s < kUMaxPerLane; ++s) accs[wi][lane + 32 * s] = acc[s];
+  const T ew = warp_sum(esum);
   if (lane == 0) {
     wsums[wi] = wsum;
     cnts[wi] = cnt;
+    esums[wi] = (double)ew;
   }
   __syncthreads();
   T W = T(0);
@@ -347,11 +371,18 @@ __global__ void __launch_bounds__(kUWarps * 32) update_kernel(const T* __restric
     C += cnts[i];
   }
   for (int q = threadIdx.x; q < d; q += blockDim.x) {
-    T s = T(0);
-    for (int i = 0; i < kUWarps; ++i) s += accs[i][q];
-    Znext[(size_t)j * d + q] = W > T(0) ? s / W : Zcur[(size_t)j * d + q];
+    T sq = T(0);
+    for (int i = 0; i < kUWarps; ++i) sq += accs[i][q];
+    Znext[(size_t)j * d + q] = W > T(0) ? sq / W : Zcur[(size_t)j * d + q];
   }
-  if (threadIdx.x == 0 && counts) counts[j] = C;
+  if (threadIdx.x == 0) {
+    if (counts) counts[j] = C;
+    if (energy) {
+      double e = 0.0;
+      for (int i = 0; i < kUWarps; ++i) e += esums[i];
+      energy[j] = e;
+    }
+  }
 }
 
 __global__ void max_count_kernel(const int* __restrict__ counts, int k2, int* __restrict__ out) {
@@ -389,12 +420,15 @@ struct KmWs {
   double *part_e, *energy;
 };
 
-// CTAs whose partial energies are summed: the FP64 assignment kernel's own
-// grid, else the exact-energy kernel's.
-int assign_blocks(int64_t M, int prec) {
+// Partial energies per iteration: the FP64 assignment kernel writes one per
+// CTA of its grid; in the other modes the update writes one per centre.
+int energy_parts(int64_t M, int k2, int prec) {
   if (prec == CABS_PREC_FP64) return ceil_div(M, kDM);
-  return std::max(1, std::min(ceil_div(M, 64), sm_count() * 4));
+  return k2;
 }
+
+// Grid of the exact-energy kernel (the encoding error of given representatives).
+int energy_blocks(int64_t M) { return std::max(1, std::min(ceil_div(M, 64), sm_count() * 4)); }
 
 KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
   const size_t eb = elem_bytes(prec);
@@ -407,7 +441,7 @@ KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
   w.labels = cv.take<int>(M);
   w.counts = cv.take<int>(k2);
   w.T = cv.take<int>(1);
-  w.part_e = cv.take<double>((size_t)std::max(iters, 1) * assign_blocks(M, prec));
+  w.part_e = cv.take<double>((size_t)std::max(iters, 1) * std::max(energy_parts(M, k2, prec), energy_blocks(M)));
   w.energy = cv.take<double>(std::max(iters, 1));
   w.tc = nullptr;
   if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
@@ -445,8 +479,7 @@ cabs_status assign_once<float>(const float* X, int64_t M, int d, const float* Z,
     CABS_TRY(tc_assign_launch(X, M, d, Z, zn, k2, xn, w, labels, d_recheck, prec == CABS_PREC_BF16, first, tcws,
                               stream));
   }
-  CABS_LAUNCH(stream, "energy_exact_kernel",
-              energy_exact_kernel<float><<<assign_blocks(M, prec), 256, 0, stream>>>(X, M, d, Z, k2, labels, w, part_e));
+  (void)part_e;  // the update pass adds up this iteration's energy
   return CABS_OK;
 }
 
@@ -468,12 +501,14 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
   T* Zc = (T*)w.Za;
   T* Zn = (T*)w.Zb;
   CABS_LAUNCH(stream, "init_centres_kernel", init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, init_rows, k2, Zc));
-  const int nb = assign_blocks(M, prec);
+  const int nb = energy_parts(M, k2, prec);
   for (int t = 0; t < iters; ++t) {
     int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
-    CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, w.part_e + (size_t)t * nb, d_recheck,
-                            t == 0, tcws, stream));
-    CABS_LAUNCH(stream, "update_kernel", update_kernel<T><<<k2, kUWarps * 32, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts));
+    double* pe = w.part_e + (size_t)t * nb;
+    CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, pe, d_recheck, t == 0, tcws, stream));
+    CABS_LAUNCH(stream, "update_kernel",
+                update_kernel<T><<<k2, kUWarps * 32, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts,
+                                                                  prec == CABS_PREC_FP64 ? nullptr : pe));
     T* tmp = Zc;
     Zc = Zn;
     Zn = tmp;
@@ -504,9 +539,14 @@ cabs_status enc_err_typed(const T* X, int64_t M, int d, const int* reps, int k2,
   CABS_LAUNCH(stream, "point_prep_kernel", point_prep_kernel<T><<<std::max(1, std::min(ceil_div(M, 8), sms * 16)), 256, 0, stream>>>(X, M, d, p, (T*)w.xn,
                                                                                            (T*)w.w));
   CABS_LAUNCH(stream, "init_centres_kernel", init_centres_kernel<T><<<k2, 128, 0, stream>>>(X, M, d, reps, k2, (T*)w.Za));
-  const int nb = assign_blocks(M, prec);
   CABS_TRY(assign_once<T>(X, M, d, (T*)w.Za, k2, prec, (T*)w.xn, (T*)w.w, (T*)w.zn, w.labels, w.part_e, nullptr,
                           true, tcws, stream));
+  int nb = energy_parts(M, k2, prec);
+  if (prec != CABS_PREC_FP64) {
+    nb = energy_blocks(M);
+    CABS_LAUNCH(stream, "energy_exact_kernel",
+                energy_exact_kernel<T><<<nb, 256, 0, stream>>>(X, M, d, (T*)w.Za, k2, w.labels, (T*)w.w, w.part_e));
+  }
   CABS_LAUNCH(stream, "energy_reduce_kernel", energy_reduce_kernel<<<1, 64, 0, stream>>>(w.part_e, nb, 1, out));
   return CABS_OK;
 }

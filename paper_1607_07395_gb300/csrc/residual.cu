@@ -201,9 +201,12 @@ cabs_status error_typed(const cabs_source& src, int64_t m, int64_t n, int k, con
 
 }  // namespace
 
+// The tensor-core residual streams A by TMA: rows must start on 16-byte
+// boundaries (lda a multiple of 4 floats, A 16-byte aligned).
 static bool use_tc_residual(const cabs_source& src, int64_t samples, int prec) {
   return samples == 0 && src.kind == CABS_SRC_DENSE && !src.a_is_f64 &&
-         (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16);
+         (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) && (src.lda & 3) == 0 &&
+         ((uintptr_t)src.A & 15) == 0;
 }
 
 size_t error_ws_bytes(const cabs_source& src, int64_t m, int64_t n, int k, int64_t samples, int prec) {

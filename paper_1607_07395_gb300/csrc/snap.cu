@@ -12,6 +12,9 @@
 //     8 x 8 per thread) and keeps, per centre, its 8 nearest rows of the tile.
 //  2. snap_merge_kernel: one CTA per centre merges the tile lists into the
 //     centre's global 8 nearest rows, ordered by (distance, row).
+//     In the BF16 and TF32 modes steps 1-2 run on tensor cores instead
+//     (tc_snap.cu): the 32 best rows per centre by |x|^2 - 2 x.z, then the
+//     same direct FP32 distances as step 1 decide the 8 candidates.
 //  3. snap_greedy_kernel (cooperative): CTA 0's warp 0 walks the centres in
 //     order and picks the first candidate not taken (a bitmap of taken rows);
 //     only if all 8 are taken do all CTAs scan every row for that centre.
@@ -20,6 +23,7 @@
 #include "grid_sync.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"
+#include "tc_snap.cuh"
 
 namespace cabs {
 namespace {
@@ -312,9 +316,12 @@ struct SnapWs {
   int *picks, *next_fb, *cta_row;
   void* cta_best;
   GridBarrier* bar;
+  void* tc;  // tensor-core candidate search (BF16 / TF32 modes)
+  size_t tc_bytes;
 };
 
-SnapWs carve_snap(Carve& cv, int64_t M, int k2, size_t eb) {
+SnapWs carve_snap(Carve& cv, int64_t M, int d, int k2, int prec) {
+  const size_t eb = elem_bytes(prec);
   SnapWs w;
   const int nblk = ceil_div(M, kSM);
   w.cand_d = cv.take<char>((size_t)nblk * k2 * kTop * eb);
@@ -327,25 +334,38 @@ SnapWs carve_snap(Carve& cv, int64_t M, int k2, size_t eb) {
   w.cta_row = cv.take<int>(1024);
   w.cta_best = cv.take<char>(1024 * eb);
   w.bar = cv.take<GridBarrier>(1);
+  w.tc = nullptr;
+  w.tc_bytes = 0;
+  if (prec == CABS_PREC_BF16 || prec == CABS_PREC_TF32) {
+    w.tc_bytes = tc_snap_ws_bytes(M, d, k2);
+    w.tc = cv.take<char>(w.tc_bytes);
+  }
   return w;
 }
 
 template <typename T>
-cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* order, int* sorted, void* ws,
+cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int prec, int* order, int* sorted, void* ws,
                        size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
-  SnapWs w = carve_snap(cv, M, k2, sizeof(T));
+  SnapWs w = carve_snap(cv, M, d, k2, prec);
   if (!cv.fits()) {
     set_error("snap workspace too small: need %zu bytes, got %zu", cv.used, ws_bytes);
     return CABS_ENOMEM;
   }
-  const int nblk = ceil_div(M, kSM);
-  const size_t stage = (size_t)(kSK * (kSM + 1) + kSK * (kSN + 1)) * sizeof(T);
-  const size_t dtile = (size_t)kSM * (kSN + 1) * sizeof(T);
-  const size_t smem = std::max(stage, dtile);
-  cudaFuncSetAttribute(snap_cand_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
-  CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
+  const bool tf32 = prec == CABS_PREC_TF32;
+  if (w.tc && sizeof(T) == 4 && tc_snap_supported(M, d, k2, tf32)) {
+    // reduced precision: candidates ranked on tensor cores, then by direct distance
+    CABS_TRY(tc_snap_candidates((const float*)X, M, d, (const float*)Z, k2, tf32, (float*)w.top_d, w.top_r, w.tc,
+                                w.tc_bytes, stream));
+  } else {
+    const int nblk = ceil_div(M, kSM);
+    const size_t stage = (size_t)(kSK * (kSM + 1) + kSK * (kSN + 1)) * sizeof(T);
+    const size_t dtile = (size_t)kSM * (kSN + 1) * sizeof(T);
+    const size_t smem = std::max(stage, dtile);
+    cudaFuncSetAttribute(snap_cand_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
+    CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
   const int G = std::max(1, std::min({(int)ceil_div(M, 2048), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
@@ -371,16 +391,16 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int* or
 
 size_t snap_ws_bytes(int64_t M, int d, int k2, int prec) {
   Carve cv;
-  carve_snap(cv, M, k2, elem_bytes(prec));
+  carve_snap(cv, M, d, k2, prec);
   return cv.used;
 }
 
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
                         void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
   if (prec == CABS_PREC_FP64)
-    return snap_typed<double>((const double*)X, M, d, (const double*)Z, k2, order, sorted, ws, ws_bytes, fallbacks,
-                              stream);
-  return snap_typed<float>((const float*)X, M, d, (const float*)Z, k2, order, sorted, ws, ws_bytes, fallbacks,
+    return snap_typed<double>((const double*)X, M, d, (const double*)Z, k2, prec, order, sorted, ws, ws_bytes,
+                              fallbacks, stream);
+  return snap_typed<float>((const float*)X, M, d, (const float*)Z, k2, prec, order, sorted, ws, ws_bytes, fallbacks,
                            stream);
 }
 

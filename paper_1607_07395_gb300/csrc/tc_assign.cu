@@ -253,6 +253,18 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
 
 }  // namespace
 
+int tc_kp_of(int d, bool tf32) { return kp_of(d, tf32); }
+
+cabs_status tc_to_operand(const float* X, int64_t rows, int d, int Kp, bool tf32, void* out, const char* name,
+                          cudaStream_t stream) {
+  const int blocks = std::max(1, std::min(ceil_div(rows * Kp, 256), sm_count() * 8));
+  if (tf32)
+    CABS_LAUNCH(stream, name, to_operand_kernel<true><<<blocks, 256, 0, stream>>>(X, rows, d, Kp, out));
+  else
+    CABS_LAUNCH(stream, name, to_operand_kernel<false><<<blocks, 256, 0, stream>>>(X, rows, d, Kp, out));
+  return CABS_OK;
+}
+
 int tc_assign_blocks(int64_t M) { return std::max(1, std::min(ceil_div(M, tc::kBM), sm_count())); }
 
 void tc_assign_carve(Carve& cv, int64_t M, int d, int k2) {

@@ -6,6 +6,13 @@
 
 namespace cabs {
 
+// Operand width (d rounded up to the 128-byte K chunk) and the conversion of
+// an FP32 row-major matrix (rows x d) to K-major BF16 or TF32 operand rows of
+// Kp elements, zero-padded; shared by the tensor-core assignment and snap.
+int tc_kp_of(int d, bool tf32);
+cabs_status tc_to_operand(const float* X, int64_t rows, int d, int Kp, bool tf32, void* out, const char* name,
+                          cudaStream_t stream);
+
 // CTAs of the assignment grid for M points.
 int tc_assign_blocks(int64_t M);
 // Extra workspace (operand copies, re-check flags) carved after the FP32 k-means slices.

@@ -4,13 +4,17 @@
 // A_hat = (U diag(S)) V^T is a contraction with K = k, so it runs on tcgen05:
 // the operands (U diag(S) and V, rounded to BF16 or kept as TF32, K padded
 // with zeros to a multiple of the 128-byte swizzle width) are staged by TMA,
-// a 128 x 256 (BF16) or 128 x 128 (TF32) tile of A_hat accumulates in TMEM,
-// and the epilogue warps read it back with tcgen05.ld while they stream the
-// same tile of A from HBM once, summing (a - a_hat)^2 and a^2 (FP32 within a
-// tile, FP64 across tiles: FP64 runs at 1/64 of the FP32 rate here). A_hat
-// is never written. A CTA keeps one column block of V resident and walks the
-// row tiles of that block, so V is read from L2 once per CTA and U diag(S)
-// once per column block. Per-CTA sums are added in a fixed order.
+// a 128 x 256 (BF16) or 128 x 128 (TF32) tile of A_hat accumulates in TMEM
+// (two accumulators, so one tile's epilogue overlaps the next tile's MMAs).
+// A itself is streamed from HBM once, by TMA as well: a fourth role (warp 3)
+// loads each tile of A as 128-row x 32-column chunks (128-byte swizzle) into
+// a ring, so the epilogue warps read their row of a chunk from shared memory
+// without bank conflicts, while the copies keep HBM busy. The epilogue sums
+// (a - a_hat)^2 and a^2 in FP32 within a tile and in FP64 across tiles (FP64
+// runs at 1/64 of the FP32 rate here). A_hat is never written. A CTA keeps
+// one column block of V resident and walks the row tiles of that block, so V
+// is read from L2 once per CTA and U diag(S) once per column block. Per-CTA
+// sums are added in a fixed order.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -48,18 +52,46 @@ __global__ void residual_prep_kernel(const float* __restrict__ U, const double* 
   }
 }
 
+constexpr int kUSt = 2;                          // ring stages of U diag(S) row tiles
+// Ring stages of A chunks. The producer alternates the two column halves and
+// each unit has an even number of chunks, so with an even stage count every
+// slot always serves the same half: a group of epilogue warps then waits on a
+// slot's next phase only after it consumed the previous one. (With an odd
+// count the halves would alternate on a slot, and a group could wait for
+// phase n + 1 while the slot is still in phase n, which a parity wait cannot
+// tell apart from phase n - 1 completing.)
+constexpr int kMSt = 4;
+static_assert(kMSt % 2 == 0, "each A slot must serve one column half");
+constexpr uint32_t kMChunkBytes = tc::kBM * 128; // one A chunk: 128 rows x 32 FP32 columns
+
+// Waits for a phase regardless of the abort flag (bounded): used to let the
+// copies a role has issued land before the CTA exits.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < tc::kWaitLimit; ++i)
+    if (tc::mbar_try_wait(bar, parity)) return;
+}
+
 template <bool kTF32>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_residual_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                       const float* __restrict__ Amat, long long lda, int m, int n, int nch, int units,
+                       const __grid_constant__ CUtensorMap tmM, int m, int nch, int units,
                        double* __restrict__ part, int* err) {
   using Cfg = ResCfg<kTF32>;
   constexpr int BN = Cfg::BN;
+  constexpr int NC = BN / 32;  // A chunks per unit
   extern __shared__ uint8_t smem_raw[];
   __shared__ tc::Barriers bars;
+  __shared__ uint64_t mfull[kMSt], mempty[kMSt];
   __shared__ double red[2][tc::kEpiWarps];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kMSt; ++i) {
+      tc::mbar_init(&mfull[i], 1);
+      tc::mbar_init(&mempty[i], 4);  // the 4 warps of one column half read a slot
+    }
+  }
   uint8_t *Bres, *Aring;
   tc::setup<BN>(smem_raw, nch, Bres, Aring, &bars);
+  uint8_t* Mring = Aring + (size_t)kUSt * tc::kBM * 128;
   const int MT = (m + tc::kBM - 1) / tc::kBM;
   const int u0 = (int)((long long)units * blockIdx.x / gridDim.x);
   const int u1 = (int)((long long)units * (blockIdx.x + 1) / gridDim.x);
@@ -68,68 +100,89 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     if (lane == 0) {
       tc::prefetch_tmap(&tmA);
       tc::prefetch_tmap(&tmB);
-      tc::producer_loop<BN>(&tmA, &tmB, Bres, Aring, &bars, u0, u1, MT, nch, Cfg::KC);
+      tc::producer_loop<BN, kUSt>(&tmA, &tmB, Bres, Aring, &bars, u0, u1, MT, nch, Cfg::KC);
     }
   } else if (warp == 1) {
-    if (lane == 0) tc::mma_loop<kTF32, BN>(Bres, Aring, &bars, u0, u1, MT, nch);
+    if (lane == 0) tc::mma_loop<kTF32, BN, kUSt>(Bres, Aring, &bars, u0, u1, MT, nch);
+  } else if (warp == 3) {
+    // A producer: the unit's A tile as NC chunks of 32 columns, interleaving
+    // the two column halves so both groups of epilogue warps progress
+    if (lane == 0) {
+      tc::prefetch_tmap(&tmM);
+      long long issued = 0;
+      bool ok = true;
+      for (int u = u0; u < u1 && ok; ++u) {
+        int cb, rt;
+        tc::unit_of(u, MT, cb, rt);
+        for (int t = 0; t < NC; ++t) {
+          const int c = (t & 1) * (NC / 2) + (t >> 1);
+          const int s = (int)(issued % kMSt);
+          const uint32_t ph = (uint32_t)((issued / kMSt) & 1);
+          if (!tc::mbar_wait(&mempty[s], ph ^ 1, &bars.abort)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&mfull[s], kMChunkBytes);
+          tc::tma_load_2d(Mring + (size_t)s * kMChunkBytes, &tmM, &mfull[s], cb * BN + c * 32, rt * tc::kBM);
+          ++issued;
+        }
+      }
+      if (!ok)  // let the copies in flight land before the CTA exits
+        for (long long j = issued > kMSt ? issued - kMSt : 0; j < issued; ++j)
+          mbar_drain(&mfull[j % kMSt], (uint32_t)((j / kMSt) & 1));
+    }
   } else if (warp >= tc::kEpiWarp0) {
     const int e = warp - tc::kEpiWarp0;
     const int sub = warp & 3;             // TMEM lane quarter
     const int half = e >> 2;              // column half
     const int row = sub * 32 + lane;      // tile row
-    const bool vec = ((lda & 3) == 0) && (((uintptr_t)Amat & 15) == 0);
     double num = 0.0, den = 0.0;
     int ab = 0;
     uint32_t accph[2] = {0, 0};
-    for (int u = u0; u < u1; ++u) {
-      int cb, rt;
-      tc::unit_of(u, MT, cb, rt);
+    long long ubase = 0;  // A chunks of the units before this one
+    bool ok = true;
+    for (int u = u0; u < u1 && ok; ++u) {
       if (!tc::mbar_wait(&bars.accfull[ab], accph[ab], &bars.abort)) break;
       accph[ab] ^= 1;
       tc::fence_after_sync();
-      const long long gi = (long long)rt * tc::kBM + row;
-      const bool row_ok = gi < m;
-      const float* arow = Amat + (row_ok ? gi : 0) * lda;
+      // Out-of-range rows and columns are zero in A (TMA fill) and in the
+      // contraction (zero operand rows), so they add nothing.
       float tn = 0.f, td = 0.f;  // FP32 within a tile (<= 128 terms), FP64 across tiles
-      constexpr int NJ = BN / 2 / 32;
-      float a[2][32];
-      auto load_chunk = [&](int j, float (&dst)[32]) {
-        const long long gc0 = (long long)cb * BN + half * (BN / 2) + j * 32;
-        if (row_ok && vec && gc0 + 32 <= n) {
-          const float4* p4 = (const float4*)(arow + gc0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 t = __ldg(p4 + q);
-            dst[4 * q] = t.x;
-            dst[4 * q + 1] = t.y;
-            dst[4 * q + 2] = t.z;
-            dst[4 * q + 3] = t.w;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 32; ++q) dst[q] = (row_ok && gc0 + q < n) ? __ldg(arow + gc0 + q) : 0.f;
+#pragma unroll 1
+      for (int j = 0; j < NC / 2; ++j) {
+        const int c = half * (NC / 2) + j;
+        const long long i = ubase + 2 * j + half;
+        const int s = (int)(i % kMSt);
+        if (!tc::mbar_wait(&mfull[s], (uint32_t)((i / kMSt) & 1), &bars.abort)) {
+          ok = false;
+          break;
         }
-      };
-      load_chunk(0, a[0]);
+        // 128-byte swizzle: 16-byte group q of row r sits at q ^ (r % 8)
+        const uint8_t* rp = Mring + (size_t)s * kMChunkBytes + (size_t)row * 128;
+        float a[32];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        if (j + 1 < NJ) load_chunk(j + 1, a[(j + 1) & 1]);  // next chunk's loads in flight
-        const int c0 = half * (BN / 2) + j * 32;
-        const long long gc0 = (long long)cb * BN + c0;
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = *(const float4*)(rp + ((q ^ (row & 7)) << 4));
+          a[4 * q] = t.x;
+          a[4 * q + 1] = t.y;
+          a[4 * q + 2] = t.z;
+          a[4 * q + 3] = t.w;
+        }
         float v[32];
-        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * BN + c0) + ((uint32_t)(sub * 32) << 16), v);
-        if (row_ok) {
+        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * BN + c * 32) + ((uint32_t)(sub * 32) << 16), v);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            if (gc0 + q < n) {
-              const float x = a[j & 1][q];
-              const float dl = x - v[q];
-              tn = fmaf(dl, dl, tn);
-              td = fmaf(x, x, td);
-            }
-          }
+        for (int q = 0; q < 32; ++q) {
+          const float dl = a[q] - v[q];
+          tn = fmaf(dl, dl, tn);
+          td = fmaf(a[q], a[q], td);
         }
+        // release the slot only once every lane has consumed its values, so no
+        // shared-memory read of this chunk can still be pending when the
+        // producer's next copy lands in it
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&mempty[s]);
       }
+      ubase += NC;
       num += (double)tn;
       den += (double)td;
       tc::fence_before_sync();
@@ -208,11 +261,13 @@ cabs_status tc_residual_typed(const cabs_source& src, int64_t m, int64_t n, int 
               residual_prep_kernel<kTF32><<<std::max(1, std::min(ceil_div((m + n) * Kp, 256), sm_count() * 8)), 256,
                                             0, stream>>>(U, S, V, m, n, k, Kp, USp, Vp));
   if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) return check_cuda("tc residual err clear");
-  const size_t smem = tc::smem_bytes(nch, Cfg::BN);
+  CUtensorMap tmM;
+  CABS_TRY(make_tmap_2d(&tmM, src.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, m, n, (uint64_t)src.lda * 4, 32, tc::kBM));
+  const size_t smem = tc::smem_bytes<kUSt>(nch, Cfg::BN) + (size_t)kMSt * kMChunkBytes;
   cudaFuncSetAttribute(tc_residual_kernel<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   CABS_LAUNCH(stream, "tc_residual_kernel",
-              tc_residual_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(
-                  tmA, tmB, (const float*)src.A, src.lda, (int)m, (int)n, nch, units, part, err));
+              tc_residual_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(tmA, tmB, tmM, (int)m, nch, units,
+                                                                            part, err));
   CABS_LAUNCH(stream, "tc_pair_reduce_kernel", tc_pair_reduce_kernel<<<1, 256, 0, stream>>>(part, grid, err, out2));
   return CABS_OK;
 }
