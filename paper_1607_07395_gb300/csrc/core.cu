@@ -29,59 +29,77 @@ namespace {
 
 // out[M x N] = X[M x K] * B[K x N] with X in T and B in FP64 (converted to T);
 // N = K = k. Also the FP64 sum of squares of each output column over this
-// CTA's rows: part[blockIdx.y * N + col].
-constexpr int kGBM = 64, kGBN = 64, kGBK = 16;
+// CTA's rows: part[blockIdx.y * N + col]. 256 threads; each thread owns a
+// TM x TN register tile (8 x 8 in FP32, 4 x 4 in FP64), so one CTA covers
+// (16 TM) x (16 TN) outputs and reads 2 (TM + TN) / 4 shared-memory vectors
+// per TM TN multiply-adds. Every output sums over K in ascending order, as a
+// plain loop would, whatever the tile shape.
+constexpr int kGBK = 16;
+template <typename T>
+struct ExtrapTile {
+  static constexpr int TM = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int TN = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int BM = 16 * TM, BN = 16 * TN;
+};
 
 template <typename T>
 __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ X, long long M, int K,
                                                          const double* __restrict__ B, int N, T* __restrict__ out,
                                                          double* __restrict__ part) {
-  __shared__ __align__(16) T As[kGBK][kGBM + 4];
-  __shared__ __align__(16) T Bs[kGBK][kGBN + 4];
-  __shared__ double colsq[16][kGBN];
+  constexpr int TM = ExtrapTile<T>::TM, TN = ExtrapTile<T>::TN;
+  constexpr int BM = ExtrapTile<T>::BM, BN = ExtrapTile<T>::BN;
+  __shared__ __align__(16) T As[kGBK][BM + 4];
+  __shared__ __align__(16) T Bs[kGBK][BN + 4];
+  __shared__ double colsq[16][BN];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const long long m0 = (long long)blockIdx.y * kGBM;
-  const int n0 = blockIdx.x * kGBN;
-  T acc[4][4];
+  const long long m0 = (long long)blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
   for (int k0 = 0; k0 < K; k0 += kGBK) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = tid + 256 * e;       // 0..1023
-      const int r = idx >> 4, c = idx & 15;  // X tile: 64 rows x 16 k
+    for (int e = 0; e < BM * kGBK / 256; ++e) {
+      const int idx = tid + 256 * e;
+      const int r = idx >> 4, c = idx & 15;  // X tile: BM rows x 16 k, read along k
       const long long gm = m0 + r;
       const int gk = k0 + c;
       As[c][r] = (gm < M && gk < K) ? X[gm * K + gk] : T(0);
-      const int br = idx >> 6, bc = idx & 63;  // B tile: 16 k x 64 cols
+    }
+#pragma unroll
+    for (int e = 0; e < BN * kGBK / 256; ++e) {
+      const int idx = tid + 256 * e;
+      const int br = idx / BN, bc = idx - br * BN;  // B tile: 16 k x BN cols
       const int bk = k0 + br, bn = n0 + bc;
       Bs[br][bc] = (bk < K && bn < N) ? (T)B[(size_t)bk * N + bn] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kGBK; ++kk) {
-      T a[4], b[4];
+      T a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
-  T sq[4] = {T(0), T(0), T(0), T(0)};
+  T sq[TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const long long gm = m0 + ty * 4 + i;
+  for (int j = 0; j < TN; ++j) sq[j] = T(0);
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const long long gm = m0 + ty * TM + i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx * TN + j;
       if (gn < N) {
         out[gm * N + gn] = acc[i][j];
         sq[j] = fma(acc[i][j], acc[i][j], sq[j]);
@@ -89,13 +107,13 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) colsq[ty][tx * 4 + j] = (double)sq[j];
+  for (int j = 0; j < TN; ++j) colsq[ty][tx * TN + j] = (double)sq[j];
   __syncthreads();
-  if (tid < kGBN) {
-    double s = 0.0;
-    for (int r = 0; r < 16; ++r) s += colsq[r][tid];
+  if (tid < BN) {
+    double s2 = 0.0;
+    for (int r = 0; r < 16; ++r) s2 += colsq[r][tid];
     const int gn = n0 + tid;
-    if (gn < N) part[(size_t)blockIdx.y * N + gn] = s;
+    if (gn < N) part[(size_t)blockIdx.y * N + gn] = s2;
   }
 }
 
@@ -148,8 +166,9 @@ CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
   w.sig = cv.take<double>(k);
   w.Uw = cv.take<double>((size_t)k * k);
   w.Vw = cv.take<double>((size_t)k * k);
-  w.part1 = cv.take<double>((size_t)ceil_div(m, kGBM) * k);
-  w.part2 = cv.take<double>((size_t)ceil_div(n, kGBM) * k);
+  // column-norm partials: one row per CTA row block (the FP64 tile is the shorter)
+  w.part1 = cv.take<double>((size_t)ceil_div(m, ExtrapTile<double>::BM) * k);
+  w.part2 = cv.take<double>((size_t)ceil_div(n, ExtrapTile<double>::BM) * k);
   w.f1 = cv.take<double>(k);
   w.f2 = cv.take<double>(k);
   w.rank = cv.take<int>(1);
@@ -174,8 +193,8 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   int* rank = d_rank ? d_rank : w.rank;
   int* sweeps = d_sweeps ? d_sweeps : w.sweeps;
   CABS_TRY(launch_svd(W, k, trunc_rtol, sig, Uw, Vw, rank, sweeps, d_refine, d_status, w.svd, stream));
-  const int nb1 = ceil_div(m, kGBM), nb2 = ceil_div(n, kGBM);
-  dim3 g1(ceil_div(k, kGBN), nb1), g2(ceil_div(k, kGBN), nb2);
+  const int nb1 = ceil_div(m, ExtrapTile<T>::BM), nb2 = ceil_div(n, ExtrapTile<T>::BM);
+  dim3 g1(ceil_div(k, ExtrapTile<T>::BN), nb1), g2(ceil_div(k, ExtrapTile<T>::BN), nb2);
   CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));
   CABS_LAUNCH(stream, "extrap_gemm_kernel(Rt U_w)", extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2));
   const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);

@@ -388,6 +388,67 @@ __device__ __forceinline__ void gemm_tile(int k, int ti, int tj, const double* _
   }
 }
 
+// One 16 x 16 tile of the symmetric C = A^T A (A column-major k x k), tile
+// (ti, tj) with ti <= tj, written to both triangles; same FP64 arithmetic as
+// gemm_tile.
+__device__ __forceinline__ void gram_tile(int k, int ti, int tj, const double* __restrict__ A,
+                                          double* __restrict__ Cout, double (*As)[kGT + 1], double (*Bs)[kGT + 1]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = ti * kGT, j0 = tj * kGT;
+  double acc = 0.0;
+  for (int p0 = 0; p0 < k; p0 += kGK) {
+    const int gi = i0 + tx, gp = p0 + ty, gj = j0 + tx;
+    As[ty][tx] = (gi < k && gp < k) ? A[(size_t)gi * k + gp] : 0.0;
+    Bs[ty][tx] = (gp < k && gj < k) ? A[(size_t)gj * k + gp] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kGK; ++p) acc = fma(As[p][ty], Bs[p][tx], acc);
+    __syncthreads();
+  }
+  const int gi = i0 + ty, gj = j0 + tx;
+  if (gi < k && gj < k) {
+    Cout[(size_t)gj * k + gi] = acc;
+    if (ti != tj) Cout[(size_t)gi * k + gj] = acc;
+  }
+}
+
+// One 16 x 16 tile of Cout = Cadd + A B (A, B, Cadd column-major k x k, FP64
+// storage) with the product in FP32. Used for the corrections U F and V G:
+// F and G are already small, so the FP32 product's rounding (about 2^-24 of
+// |U| |F|) is far below the error the iteration removes and is corrected by
+// the next one.
+__device__ __forceinline__ void corr_tile_f32(int k, int ti, int tj, const double* __restrict__ A,
+                                              const double* __restrict__ B, const double* __restrict__ Cadd,
+                                              double* __restrict__ Cout, float (*As)[kGT + 1], float (*Bs)[kGT + 1]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = ti * kGT, j0 = tj * kGT;
+  float acc = 0.f;
+  for (int p0 = 0; p0 < k; p0 += kGK) {
+    const int gi = i0 + tx, gp = p0 + ty, gj = j0 + tx;
+    As[ty][tx] = (gi < k && gp < k) ? (float)A[(size_t)gp * k + gi] : 0.f;
+    Bs[ty][tx] = (gp < k && gj < k) ? (float)B[(size_t)gj * k + gp] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kGK; ++p) acc = fmaf(As[p][ty], Bs[p][tx], acc);
+    __syncthreads();
+  }
+  const int gi = i0 + ty, gj = j0 + tx;
+  if (gi < k && gj < k) {
+    const size_t o = (size_t)gj * k + gi;
+    Cout[o] = Cadd[o] + (double)acc;
+  }
+}
+
+__device__ __forceinline__ void tri_of(int x, int nt, int& ti, int& tj) {
+  // x-th tile (ti <= tj) of the upper triangle, row by row
+  ti = 0;
+  while (x >= nt - ti) {
+    x -= nt - ti;
+    ++ti;
+  }
+  tj = ti + x;
+}
+
 struct RefineArgs {
   int k;
   const double* W;  // row-major k x k (= W^T column-major)
@@ -404,12 +465,15 @@ struct RefineArgs {
 __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
   __shared__ double As[kGK][kGT + 1];
   __shared__ double Bs[kGK][kGT + 1];
+  __shared__ float As32[kGK][kGT + 1];
+  __shared__ float Bs32[kGK][kGT + 1];
   __shared__ double dsh[CABS_MAX_K];
   __shared__ double dmax2;
   const int k = a.k;
   const unsigned nb = gridDim.x;
   const int nt = (k + kGT - 1) / kGT;
   const int tiles = nt * nt;
+  const int tri = nt * (nt + 1) / 2;
   double prev = 0.0;
   for (int t = 0; t < kItersB; ++t) {
     const double* U = (t & 1) ? a.U1 : a.U0;
@@ -418,11 +482,16 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     double* Vn = (t & 1) ? a.V0 : a.V1;
     for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
     if (!grid_sync(a.bar, nb)) return;
-    for (int x = blockIdx.x; x < 3 * tiles; x += nb) {
-      const int which = x / tiles, y = x - which * tiles;
-      if (which == 0) gemm_tile(k, y % nt, y / nt, U, 1, a.P, nullptr, a.T, As, Bs);
-      else if (which == 1) gemm_tile(k, y % nt, y / nt, U, 1, U, nullptr, a.UtU, As, Bs);
-      else gemm_tile(k, y % nt, y / nt, V, 1, V, nullptr, a.VtV, As, Bs);
+    // T = U^T P in full; the Gram matrices U^T U, V^T V by their upper triangles
+    for (int x = blockIdx.x; x < tiles + 2 * tri; x += nb) {
+      if (x < tiles) {
+        gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
+      } else {
+        const int y = x - tiles, which = y / tri;
+        int ti, tj;
+        tri_of(y - which * tri, nt, ti, tj);
+        gram_tile(k, ti, tj, which == 0 ? U : V, which == 0 ? a.UtU : a.VtV, As, Bs);
+      }
     }
     if (!grid_sync(a.bar, nb)) return;
     // coefficients F, G and singular value estimates d
@@ -472,8 +541,8 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     if (!grid_sync(a.bar, nb)) return;
     for (int x = blockIdx.x; x < 2 * tiles; x += nb) {
       const int which = x / tiles, y = x - which * tiles;
-      if (which == 0) gemm_tile(k, y % nt, y / nt, U, 0, a.F, U, Un, As, Bs);
-      else gemm_tile(k, y % nt, y / nt, V, 0, a.G, V, Vn, As, Bs);
+      if (which == 0) corr_tile_f32(k, y % nt, y / nt, U, a.F, U, Un, As32, Bs32);
+      else corr_tile_f32(k, y % nt, y / nt, V, a.G, V, Vn, As32, Bs32);
     }
     // Quadratic convergence: the update just applied used corrections of size
     // m, so it leaves an error of order m^2 (times the inverse relative gap of
