@@ -48,9 +48,14 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
                                                          double* __restrict__ part) {
   constexpr int TM = ExtrapTile<T>::TM, TN = ExtrapTile<T>::TN;
   constexpr int BM = ExtrapTile<T>::BM, BN = ExtrapTile<T>::BN;
-  __shared__ __align__(16) T As[kGBK][BM + 4];
-  __shared__ __align__(16) T Bs[kGBK][BN + 4];
-  __shared__ double colsq[16][BN];
+  constexpr int LA = BM * kGBK / 256, LB = BN * kGBK / 256;  // elements each thread stages per chunk
+  // A and B double buffers; the column sums reuse the space after the loop
+  constexpr size_t kAB = sizeof(T) * 2 * kGBK * ((BM + 4) + (BN + 4));
+  constexpr size_t kCS = sizeof(double) * 16 * BN;
+  __shared__ __align__(16) unsigned char ext_smem[kAB > kCS ? kAB : kCS];
+  auto As = reinterpret_cast<T(*)[kGBK][BM + 4]>(ext_smem);
+  auto Bs = reinterpret_cast<T(*)[kGBK][BN + 4]>(ext_smem + sizeof(T) * 2 * kGBK * (BM + 4));
+  auto colsq = reinterpret_cast<double(*)[BN]>(ext_smem);
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const long long m0 = (long long)blockIdx.y * BM;
   const int n0 = blockIdx.x * BN;
@@ -59,36 +64,61 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-  for (int k0 = 0; k0 < K; k0 += kGBK) {
+  // the next chunk is read from global memory into registers while the
+  // current one is multiplied out of shared memory (two shared buffers)
+  T ra[LA], rb[LB];
+  auto load = [&](int k0) {
 #pragma unroll
-    for (int e = 0; e < BM * kGBK / 256; ++e) {
+    for (int e = 0; e < LA; ++e) {
       const int idx = tid + 256 * e;
       const int r = idx >> 4, c = idx & 15;  // X tile: BM rows x 16 k, read along k
       const long long gm = m0 + r;
       const int gk = k0 + c;
-      As[c][r] = (gm < M && gk < K) ? X[gm * K + gk] : T(0);
+      ra[e] = (gm < M && gk < K) ? X[gm * K + gk] : T(0);
     }
 #pragma unroll
-    for (int e = 0; e < BN * kGBK / 256; ++e) {
+    for (int e = 0; e < LB; ++e) {
       const int idx = tid + 256 * e;
       const int br = idx / BN, bc = idx - br * BN;  // B tile: 16 k x BN cols
       const int bk = k0 + br, bn = n0 + bc;
-      Bs[br][bc] = (bk < K && bn < N) ? (T)B[(size_t)bk * N + bn] : T(0);
+      rb[e] = (bk < K && bn < N) ? (T)B[(size_t)bk * N + bn] : T(0);
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int e = 0; e < LA; ++e) {
+      const int idx = tid + 256 * e;
+      As[buf][idx & 15][idx >> 4] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < LB; ++e) {
+      const int idx = tid + 256 * e;
+      const int br = idx / BN;
+      Bs[buf][br][idx - br * BN] = rb[e];
+    }
+  };
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += kGBK) {
+    const bool more = k0 + kGBK < K;
+    if (more) load(k0 + kGBK);
 #pragma unroll
     for (int kk = 0; kk < kGBK; ++kk) {
       T a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx * TN + j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
+    if (more) store(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
   T sq[TN];
 #pragma unroll
