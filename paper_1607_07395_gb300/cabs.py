@@ -498,6 +498,15 @@ class _DevView:
                                              version=3, strides=None)
 
 
+def result_err(res: cabs_result, device="cuda") -> float:
+    """The relative error a request computed with CABS_FLAG_ERROR (reads one
+    FP64 device scalar of the serving arena)."""
+    import torch
+    if not res.err:
+        raise ValueError("the result carries no error (CABS_FLAG_ERROR was not set)")
+    return float(torch.as_tensor(_DevView(res.err, (1,), "<f8"), device=device).cpu()[0])
+
+
 def result_tensors(res: cabs_result, p: cabs_params, device="cuda"):
     """Copies a serving result (device pointers into the arena) into new torch tensors."""
     import torch

@@ -480,12 +480,11 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     const double* V = (t & 1) ? a.V1 : a.V0;
     double* Un = (t & 1) ? a.U0 : a.U1;
     double* Vn = (t & 1) ? a.V0 : a.V1;
-    for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
-    if (!grid_sync(a.bar, nb)) return;
-    // T = U^T P in full; the Gram matrices U^T U, V^T V by their upper triangles
+    // P = W V, and (independent of it) the Gram matrices U^T U, V^T V by
+    // their upper triangles; then T = U^T P
     for (int x = blockIdx.x; x < tiles + 2 * tri; x += nb) {
       if (x < tiles) {
-        gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
+        gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
       } else {
         const int y = x - tiles, which = y / tri;
         int ti, tj;
@@ -493,6 +492,8 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
         gram_tile(k, ti, tj, which == 0 ? U : V, which == 0 ? a.UtU : a.VtV, As, Bs);
       }
     }
+    if (!grid_sync(a.bar, nb)) return;
+    for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
     if (!grid_sync(a.bar, nb)) return;
     // coefficients F, G and singular value estimates d
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -869,7 +870,8 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
   CABS_LAUNCH(stream, "svd_flags_init",
               svd_flags_init_kernel<<<1, 32, 0, stream>>>(w.maxoff, kItersB, w.done_iter, w.bar));
   {
-    const int tiles = ceil_div(k, kGT) * ceil_div(k, kGT);
+    const int nt = ceil_div(k, kGT);
+    const int tiles = nt * nt + nt * (nt + 1);  // work units of the widest phase
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_persistent_kernel, 256, 0);
     const int grid = std::max(1, std::min(tiles, coop_grid_cap(sm_count() * std::max(per_sm, 1))));

@@ -95,7 +95,7 @@ def decaying_lowrank_host(m: int, n: int, rank: int = 256, decay: float = 30.0,
 
 def decaying_lowrank_device(m: int, n: int, rank: int = 256, decay: float = 30.0,
                             noise_std: float = 1e-4, seed: int = 1607, device="cuda",
-                            out=None, row_block: int = 8192):
+                            out=None, row_block: int = 8192, noise_fp32: bool = False):
     """Device version of A = U diag(s) V^T + noise in FP32 (e.g. 65536 x 32768, 8 GiB).
 
     U and V are Gaussian matrices (drawn on the device) orthonormalised by a
@@ -103,7 +103,9 @@ def decaying_lowrank_device(m: int, n: int, rank: int = 256, decay: float = 30.0
     so the generator also runs under a profiler); the product is formed in
     FP64 one row block at a time and rounded to FP32. ``out`` may be a
     preallocated (m x lda) FP32 device tensor whose first n columns are
-    filled. Returns (A, U, s, V) with the FP64 factors on the device."""
+    filled. noise_fp32 draws the noise in FP32 (faster, for the many matrices
+    of the batched and serving workloads). Returns (A, U, s, V) with the FP64
+    factors on the device."""
     import torch
 
     def orthonormal(rows):
@@ -122,7 +124,8 @@ def decaying_lowrank_device(m: int, n: int, rank: int = 256, decay: float = 30.0
     for r0 in range(0, m, row_block):
         r1 = min(m, r0 + row_block)
         blk = Us[r0:r1] @ V.T
-        blk += noise_std * torch.randn(r1 - r0, n, generator=gen, device=device, dtype=torch.float64)
+        ndt = torch.float32 if noise_fp32 else torch.float64
+        blk += noise_std * torch.randn(r1 - r0, n, generator=gen, device=device, dtype=ndt)
         A[r0:r1, :n].copy_(blk)
         del blk
     return A, U, s, V
