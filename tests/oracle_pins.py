@@ -317,6 +317,37 @@ def pin_threshold_known_scales(thr_fn):
     assert thr_fn(np.ones((5, 2)), 2).tolist() == [0, 1]   # all equal: the first rows
 
 
+# --------------------------------------------------------- orthogonalisation
+
+def pin_orthogonalize(orth_fn, m=60, n=45, r=6, seed=13):
+    """The SVD form of U diag(S) V^T: the same matrix, orthonormal factors,
+    and the singular values of the explicit product (numpy's SVD of the dense
+    m x n matrix, an independent route); dropped directions of an exactly
+    rank-deficient sketch; a closed form with orthogonal inputs."""
+    g = np.random.default_rng(seed)
+    U = g.standard_normal((m, r))
+    V = g.standard_normal((n, r))
+    S = np.abs(g.standard_normal(r)) + 0.5
+    X, s, Y = orth_fn(U, S, V)
+    A = (U * S) @ V.T
+    assert np.allclose((X * s) @ Y.T, A, atol=1e-12 * np.abs(A).max())
+    assert np.allclose(X.T @ X, np.eye(len(s)), atol=1e-12)
+    assert np.allclose(Y.T @ Y, np.eye(len(s)), atol=1e-12)
+    assert np.allclose(s, np.linalg.svd(A, compute_uv=False)[:r], rtol=1e-12)
+    assert np.all(np.diff(s) <= 0)
+    # two equal columns of U: the rank drops to r - 1
+    U2 = U.copy()
+    U2[:, 1] = U2[:, 0]
+    X2, s2, Y2 = orth_fn(U2, S, V)
+    assert len(s2) == r - 1
+    assert np.allclose((X2 * s2) @ Y2.T, (U2 * S) @ V.T, atol=1e-12 * np.abs(A).max())
+    # orthonormal U and V already: s is S sorted, up to signs of the columns
+    Qu, _ = np.linalg.qr(U)
+    Qv, _ = np.linalg.qr(V)
+    X3, s3, Y3 = orth_fn(Qu, S, Qv)
+    assert np.allclose(s3, np.sort(S)[::-1], rtol=1e-13)
+
+
 # ---------------------------------------------------------------------- error
 
 def pin_error_closed_form(err_fn):

@@ -123,3 +123,17 @@ THRESHOLD_MUTANTS = [
 def test_threshold_mutants_rejected(old, new):
     bad = mutate(o.hard_threshold, old, new)
     assert rejects(lambda: (pins.pin_threshold_bruteforce(bad), pins.pin_threshold_known_scales(bad)))
+
+
+ORTH_MUTANTS = [
+    ("M = (Ru * S[None, :]) @ Rv.T", "M = (Ru * S[None, :]) @ Rv"),               # transposed factor
+    ("M = (Ru * S[None, :]) @ Rv.T", "M = Ru @ Rv.T"),                            # dropped S
+    ("return Qu @ P[:, keep], s[keep], Qv @ Zt.T[:, keep]", "return Qu @ P[:, keep], s[keep], Qv @ Zt[:, keep]"),
+    ("return Qu @ P[:, keep], s[keep], Qv @ Zt.T[:, keep]", "return U @ P[:, keep], s[keep], V @ Zt.T[:, keep]"),
+]
+
+
+@pytest.mark.parametrize("old,new", ORTH_MUTANTS)
+def test_orthogonalize_mutants_rejected(old, new):
+    bad = mutate(o.orthogonalize, old, new)
+    assert rejects(lambda: pins.pin_orthogonalize(bad))

@@ -144,3 +144,7 @@ def test_plain_fp64_regression_fixture():
         assert r.pilot_rows.tolist() == g["pilot_rows"] and r.pilot_cols.tolist() == g["pilot_cols"]
         assert r.rows.tolist() == g["rows"] and r.cols.tolist() == g["cols"]
         assert abs(o.rel_fro_error_dense(A, r.final.U, r.final.S, r.final.V) - g["final_err"]) <= 1e-9 * g["final_err"]
+
+
+def test_orthogonalize():
+    pins.pin_orthogonalize(o.orthogonalize)
