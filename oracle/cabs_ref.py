@@ -502,21 +502,21 @@ def cabs(source, k1: int, k2: int = None, iters: int = 5, seed: int = 1607,
 
 def orthogonalize(U: np.ndarray, S: np.ndarray, V: np.ndarray, trunc_rtol: float = 0.0):
     """The sketch U diag(S) V^T (U m x r, V n x r, S r) rewritten in SVD form
-    X diag(s) Y^T with orthonormal columns in X and Y, in O((m + n) r^2)
-    (supplementary Section 3): thin QR factorisations U = Q_u R_u and
-    V = Q_v R_v, then the SVD of the r x r core M = R_u diag(S) R_v^T =
-    P diag(s) Z^T, and X = Q_u P, Y = Q_v Z. Components with
-    s_i <= max(trunc_rtol, r 2^-52) s_1 are dropped. Returns (X, s, Y)."""
+    with orthonormal factors, in O((m + n) r^2) (supplementary Section 3):
+    the thin SVD U = U_0 Sigma_0 V_0^T, then the SVD of the r x n matrix
+    Sigma_0 V_0^T diag(S) V^T = U_1 Sigma_1 V_1^T, giving
+    A ~ (U_0 U_1) Sigma_1 V_1^T. Components with
+    Sigma_1,i <= max(trunc_rtol, r 2^-52) Sigma_1,1 are dropped.
+    Returns (U_0 U_1, diag(Sigma_1), V_1)."""
     U = np.asarray(U, dtype=np.float64)
     V = np.asarray(V, dtype=np.float64)
     S = np.asarray(S, dtype=np.float64)
-    Qu, Ru = np.linalg.qr(U)
-    Qv, Rv = np.linalg.qr(V)
-    M = (Ru * S[None, :]) @ Rv.T
-    P, s, Zt = np.linalg.svd(M)
-    r = len(s)
-    keep = s > max(trunc_rtol, r * 2.0 ** -52) * (s[0] if r else 0.0)
-    return Qu @ P[:, keep], s[keep], Qv @ Zt.T[:, keep]
+    U0, s0, V0t = np.linalg.svd(U, full_matrices=False)
+    B = (s0[:, None] * V0t) @ (S[:, None] * V.T)
+    U1, s1, V1t = np.linalg.svd(B, full_matrices=False)
+    r = len(s1)
+    keep = s1 > max(trunc_rtol, r * 2.0 ** -52) * (s1[0] if r else 0.0)
+    return U0 @ U1[:, keep], s1[keep], V1t.T[:, keep]
 
 
 # --------------------------------------------------------------------------

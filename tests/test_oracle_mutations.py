@@ -126,10 +126,11 @@ def test_threshold_mutants_rejected(old, new):
 
 
 ORTH_MUTANTS = [
-    ("M = (Ru * S[None, :]) @ Rv.T", "M = (Ru * S[None, :]) @ Rv"),               # transposed factor
-    ("M = (Ru * S[None, :]) @ Rv.T", "M = Ru @ Rv.T"),                            # dropped S
-    ("return Qu @ P[:, keep], s[keep], Qv @ Zt.T[:, keep]", "return Qu @ P[:, keep], s[keep], Qv @ Zt[:, keep]"),
-    ("return Qu @ P[:, keep], s[keep], Qv @ Zt.T[:, keep]", "return U @ P[:, keep], s[keep], V @ Zt.T[:, keep]"),
+    ("B = (s0[:, None] * V0t) @ (S[:, None] * V.T)", "B = (s0[:, None] * V0t) @ (S[:, None] * V).T"),  # wrong shape use
+    ("B = (s0[:, None] * V0t) @ (S[:, None] * V.T)", "B = V0t @ (S[:, None] * V.T)"),                   # dropped Sigma_0
+    ("B = (s0[:, None] * V0t) @ (S[:, None] * V.T)", "B = (s0[:, None] * V0t.T) @ (S[:, None] * V.T)"),  # transposed V_0
+    ("return U0 @ U1[:, keep], s1[keep], V1t.T[:, keep]", "return U0[:, keep], s1[keep], V1t.T[:, keep]"),  # dropped U_1
+    ("return U0 @ U1[:, keep], s1[keep], V1t.T[:, keep]", "return U0 @ U1[:, keep], s1[keep], V1t[:, keep]"),
 ]
 
 
