@@ -27,7 +27,16 @@ Steps and the passages they follow (section / equation / algorithm of the paper)
                        (Section 3.2, Eq. wkmeans) from the pilot rows
 ``snap``               every centre replaced by its closest in-sample point
                        (Section 3.2, last paragraph)
+``hard_threshold``     follow-up by the k2 largest-norm rows (Section 5,
+                       follow-up variant (f))
 ``cabs``               Algorithm 2 end to end
+``orthogonalize``      the sketch in SVD form (supplementary Section 3)
+``pinv_trunc``         pseudo-inverse by the SVD with the truncation below
+``br_cur``             Bilateral Resampling CUR with given base and target
+                       samplings (Section 2.2, Algorithm 1)
+``sketch_cur``         Sketch-CUR: BR-CUR with independent random base and
+                       target samplings, target three times the base
+                       (Section 2.2 item 3; Section 5, comparison (a))
 ``rel_fro_error_*``    |A - U S V^T|_F / |A|_F (Section 5), exact or on
                        uniformly sampled entries
 =====================  ===================================================
@@ -35,7 +44,7 @@ Steps and the passages they follow (section / equation / algorithm of the paper)
 Readings where the paper is silent (the GPU library takes the same ones):
 
 * Index draw: Philox4x64-10 with key (seed, tag), tag 0 = rows, 1 = columns,
-  2 = error-estimate samples; counter (i, 0, 0, 0) for the i-th draw; output
+  2 = error-estimate samples, 4 / 5 = Sketch-CUR target rows / columns; counter (i, 0, 0, 0) for the i-th draw; output
   word 0 mapped to [0, N - i) by the high half of the 128-bit product
   (multiply-shift, bias <= N / 2^64). The drawn indices are returned in draw
   order and sorted ascending; W, C and R use the sorted order.
@@ -67,6 +76,8 @@ import numpy as np
 TAG_ROWS = 0
 TAG_COLS = 1
 TAG_EVAL = 2
+TAG_TARGET_ROWS = 4
+TAG_TARGET_COLS = 5
 
 MASK64 = (1 << 64) - 1
 _M0 = 0xD2E7470EE14C6C93
@@ -517,6 +528,64 @@ def orthogonalize(U: np.ndarray, S: np.ndarray, V: np.ndarray, trunc_rtol: float
     r = len(s1)
     keep = s1 > max(trunc_rtol, r * 2.0 ** -52) * (s1[0] if r else 0.0)
     return U0 @ U1[:, keep], s1[keep], V1t.T[:, keep]
+
+
+# --------------------------------------------------------------------------
+# Section 2.2, Algorithm 1: BR-CUR and Sketch-CUR
+# --------------------------------------------------------------------------
+
+def pinv_trunc(B: np.ndarray, trunc_rtol: float = 0.0) -> np.ndarray:
+    """Pseudo-inverse V diag(1/s) U^T of B = U diag(s) V^T over the singular
+    values s_i > max(trunc_rtol, kmax 2^-52) s_1, kmax = max(B.shape) (the
+    truncation rule of the sketching routine, MATLAB pinv's default)."""
+    B = np.asarray(B, dtype=np.float64)
+    Ub, sb, Vbt = np.linalg.svd(B, full_matrices=False)
+    if len(sb) == 0 or sb[0] == 0.0:
+        return np.zeros(B.T.shape)
+    keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]
+    return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T
+
+
+@dataclass
+class CurResult:
+    rows_b: np.ndarray   # base rows I^b_r, sorted
+    cols_b: np.ndarray   # base columns I^b_c, sorted
+    rows_t: np.ndarray   # target rows I^t_r, sorted
+    cols_t: np.ndarray   # target columns I^t_c, sorted
+    C: np.ndarray        # m x k_b
+    U: np.ndarray        # k_b x k_b, U*
+    Rt: np.ndarray       # n x k_b, R^T
+
+
+def br_cur(source, rows_b, cols_b, rows_t, cols_t, trunc_rtol: float = 0.0) -> CurResult:
+    """Algorithm 1 with the given samplings: bases C = A[:, I^b_c] and
+    R = A[I^b_r, :] (step 1), their samples C_bar = C[I^t_r, :] and
+    R_bar = R[:, I^t_c] (step 2), the target block M = A[I^t_r, I^t_c]
+    (step 3), U* = C_bar^+ M R_bar^+, the minimiser of |M - C_bar U R_bar|_F
+    (step 4); A ~ C U* R (step 5)."""
+    rows_b, cols_b = np.asarray(rows_b), np.asarray(cols_b)
+    rows_t, cols_t = np.asarray(rows_t), np.asarray(cols_t)
+    C, Rt, _ = source.gather(rows_b, cols_b)
+    Cbar = C[rows_t, :]
+    Rbar = Rt[cols_t, :].T
+    _, _, M = source.gather(rows_t, cols_t)
+    Ustar = pinv_trunc(Cbar, trunc_rtol) @ M @ pinv_trunc(Rbar, trunc_rtol)
+    return CurResult(rows_b=rows_b, cols_b=cols_b, rows_t=rows_t, cols_t=cols_t, C=C, U=Ustar, Rt=Rt)
+
+
+def sketch_cur(source, kb: int, kt: int = None, seed: int = 1607, trunc_rtol: float = 0.0) -> CurResult:
+    """Sketch-CUR: BR-CUR with independent uniform base (k_b rows and
+    columns, tags 0 and 1, as the pilot draw of Algorithm 2) and target
+    (k_t = 3 k_b by default, tags 4 and 5) samplings."""
+    kt = 3 * kb if kt is None else kt
+    m, n = source.m, source.n
+    if not (1 <= kb <= min(m, n) and 1 <= kt <= min(m, n)):
+        raise ValueError("need 1 <= kb, kt <= min(m, n)")
+    _, rows_b = draw_indices(seed, TAG_ROWS, m, kb)
+    _, cols_b = draw_indices(seed, TAG_COLS, n, kb)
+    _, rows_t = draw_indices(seed, TAG_TARGET_ROWS, m, kt)
+    _, cols_t = draw_indices(seed, TAG_TARGET_COLS, n, kt)
+    return br_cur(source, rows_b, cols_b, rows_t, cols_t, trunc_rtol)
 
 
 # --------------------------------------------------------------------------

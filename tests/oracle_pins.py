@@ -348,6 +348,70 @@ def pin_orthogonalize(orth_fn, m=60, n=45, r=6, seed=13):
     assert np.allclose(s3, np.sort(S)[::-1], rtol=1e-13)
 
 
+# ------------------------------------------------------------ BR-CUR, Sketch-CUR
+
+def pin_pinv_trunc(pinv_fn):
+    """Closed form on a matrix with known singular values: 5 x 3,
+    s = (1, 1e-3, 1e-15); the floor 5 x 2^-52 = 1.1e-15 drops the third."""
+    g = np.random.default_rng(3)
+    Q1, _ = np.linalg.qr(g.standard_normal((5, 3)))
+    Q2, _ = np.linalg.qr(g.standard_normal((3, 3)))
+    s = np.array([1.0, 1e-3, 1e-15])
+    B = (Q1 * s) @ Q2.T
+    want = (Q2[:, :2] / s[:2]) @ Q1[:, :2].T
+    assert np.allclose(pinv_fn(B), want, rtol=0, atol=1e-9)
+    want_t = (Q2[:, :1] / s[:1]) @ Q1[:, :1].T
+    assert np.allclose(pinv_fn(B, 1e-2), want_t, rtol=0, atol=1e-12)
+    # full rank square: the inverse (LU, an independent routine)
+    W = g.standard_normal((6, 6)) + 3 * np.eye(6)
+    assert np.allclose(pinv_fn(W), np.linalg.solve(W, np.eye(6)), atol=1e-12)
+    assert np.all(pinv_fn(np.zeros((4, 3))) == 0) and pinv_fn(np.zeros((4, 3))).shape == (3, 4)
+
+
+def pin_br_cur(br_cur_fn, source_cls):
+    """Algorithm 1 on facts the mathematics fixes: (1) an exactly rank-4
+    matrix is recovered exactly from 6 base and 10 target rows and columns;
+    (2) with the target equal to the base, U* = W^-1 (the pseudo-skeleton
+    C W^+ R of Eq. W; Nystrom for a symmetric PSD A with equal rows and
+    columns), checked against an LU solve; (3) U* satisfies the normal
+    equations C_bar^T (M - C_bar U* R_bar) R_bar^T = 0 of step 4."""
+    from workloads import synth
+    g = np.random.default_rng(5)
+    A = synth.exact_lowrank_int(60, 50, 4, seed=9)
+    rb = np.sort(g.choice(60, 6, replace=False))
+    cb = np.sort(g.choice(50, 6, replace=False))
+    rt = np.sort(g.choice(60, 10, replace=False))
+    ct = np.sort(g.choice(50, 10, replace=False))
+    r = br_cur_fn(source_cls(A), rb, cb, rt, ct)
+    assert r.C.shape == (60, 6) and r.U.shape == (6, 6) and r.Rt.shape == (50, 6)
+    assert np.allclose(r.C @ r.U @ r.Rt.T, A, atol=1e-9 * np.abs(A).max())
+    # (2) target = base, full-rank W
+    B = g.standard_normal((40, 30))
+    rows = np.sort(g.choice(40, 7, replace=False))
+    cols = np.sort(g.choice(30, 7, replace=False))
+    r2 = br_cur_fn(source_cls(B), rows, cols, rows, cols)
+    W = B[np.ix_(rows, cols)]
+    assert np.allclose(r2.U, np.linalg.solve(W, np.eye(7)), atol=1e-10)
+    assert np.allclose(r2.C, B[:, cols]) and np.allclose(r2.Rt, B[rows, :].T)
+    # symmetric PSD, same rows and columns: Nystrom C W^-1 C^T
+    G = g.standard_normal((30, 30))
+    K = G @ G.T
+    idx = np.sort(g.choice(30, 8, replace=False))
+    r3 = br_cur_fn(source_cls(K), idx, idx, idx, idx)
+    Cn = K[:, idx]
+    assert np.allclose(r3.C @ r3.U @ r3.Rt.T, Cn @ np.linalg.solve(K[np.ix_(idx, idx)], Cn.T),
+                       atol=1e-8 * np.abs(K).max())
+    # (3) normal equations, independent target
+    rt4 = np.sort(g.choice(40, 15, replace=False))
+    ct4 = np.sort(g.choice(30, 12, replace=False))
+    r4 = br_cur_fn(source_cls(B), rows, cols, rt4, ct4)
+    Cbar = B[np.ix_(rt4, cols)]
+    Rbar = B[np.ix_(rows, ct4)]
+    M = B[np.ix_(rt4, ct4)]
+    grad = Cbar.T @ (M - Cbar @ r4.U @ Rbar) @ Rbar.T
+    assert np.abs(grad).max() < 1e-9 * np.abs(M).max() * np.abs(Cbar).max() * np.abs(Rbar).max()
+
+
 # ---------------------------------------------------------------------- error
 
 def pin_error_closed_form(err_fn):

@@ -112,7 +112,7 @@ def test_error_request_on_host(L):
     assert n1.value >= n0.value + e.value - 256
     ps = cabs.make_params(2000, 1500, 20, prec="fp32", err_samples=10 ** 6)
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(ps), C.byref(n2)) == cabs.CABS_OK
-    bad = cabs.make_params(2000, 1500, 20, flags=8)  # no such flag
+    bad = cabs.make_params(2000, 1500, 20, flags=16)  # no such flag
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(bad), C.byref(n0)) == cabs.CABS_EINVAL
     neg = cabs.make_params(2000, 1500, 20, err_samples=0)
     neg.err_samples = -1

@@ -1,0 +1,164 @@
+"""GPU parity of the orthogonalisation (supplementary Section 3) through the
+C ABI against the FP64 oracle on the same seeded factors.
+
+Bars, from the arithmetic: FP64 factors give s within 1e-10 relative, the
+product X diag(s) Y^T within 1e-10 s_1 of U diag(S) V^T, |X^T X - I| and
+|Y^T Y - I| below 1e-10, and each singular vector within 10 x 1e-10 s_1 / gap
+of the oracle's (up to sign; the gap is the distance to the neighbouring
+values). FP32 factors round every staged value to 2^-24 and accumulate the
+Gram matrices in FP32 over chunks of a few hundred rows, so the same checks
+hold with 2e-5 in place of 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import cabs_ref as o
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1607_07395_gb300 import cabs
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return cabs.Context(0)
+
+
+def run(ctx, U, S, V, prec, trunc_rtol=0.0):
+    from paper_1607_07395_gb300 import cabs
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Ud = torch.from_numpy(np.ascontiguousarray(U)).to("cuda", dt)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to("cuda", dt)
+    Sd = torch.from_numpy(np.ascontiguousarray(S)).to("cuda", torch.float64)
+    X, s, Y, rank = cabs.cabs_orthogonalize(ctx, Ud, Sd, Vd, prec=prec, trunc_rtol=trunc_rtol)
+    torch.cuda.synchronize()
+    Uin = Ud.double().cpu().numpy()
+    Vin = Vd.double().cpu().numpy()
+    return (X.double().cpu().numpy(), s.cpu().numpy(), Y.double().cpu().numpy(), int(rank.item()), Uin, Vin)
+
+
+TOL = {"fp64": 1e-10, "fp32": 2e-5}
+
+
+def check(U, S, V, X, s, Y, r, prec, trunc_rtol=0.0):
+    tol = TOL[prec]
+    Xo, so, Yo = o.orthogonalize(U, S, V, trunc_rtol)
+    assert r == len(so)
+    assert np.all(s[r:] == 0.0) and np.all(X[:, r:] == 0.0) and np.all(Y[:, r:] == 0.0)
+    Xr, sr, Yr = X[:, :r], s[:r], Y[:, :r]
+    assert np.allclose(sr, so, rtol=tol, atol=tol * so[0])
+    assert np.abs(Xr.T @ Xr - np.eye(r)).max() < tol
+    assert np.abs(Yr.T @ Yr - np.eye(r)).max() < tol
+    A = (U * S) @ V.T
+    assert np.abs((Xr * sr) @ Yr.T - A).max() < tol * so[0]
+    # singular vectors: angle to the oracle's at most |error of the product| / gap
+    # (Wedin), with the product's bound tol s_1 and the absolute gap to the
+    # neighbouring values
+    gap = np.minimum(np.r_[np.inf, so[:-1] - so[1:]], np.r_[so[:-1] - so[1:], np.inf])
+    for i in range(r):
+        bound = 10 * tol * so[0] / gap[i]
+        if bound > 0.1:
+            continue
+        for F, Fo in ((Xr, Xo), (Yr, Yo)):
+            d = min(np.linalg.norm(F[:, i] - Fo[:, i]), np.linalg.norm(F[:, i] + Fo[:, i]))
+            assert d < bound, (i, d, bound)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("m,n,k,rank", [(3000, 2000, 40, 40), (1500, 2300, 150, 150), (777, 513, 70, 53),
+                                        (300, 200, 1, 1), (200, 160, 64, 64), (5000, 700, 256, 256)])
+def test_orthogonalize_parity(ctx, prec, m, n, k, rank):
+    U, S, V = synth.sketch_factors(m, n, k, rank, seed=m + k)
+    X, s, Y, r, Ui, Vi = run(ctx, U, S, V, prec)
+    check(Ui, S, Vi, X, s, Y, r, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_orthogonalize_duplicate_column(ctx, prec):
+    U, S, V = synth.sketch_factors(900, 600, 30, 30, seed=3, dup=True)
+    X, s, Y, r, Ui, Vi = run(ctx, U, S, V, prec)
+    assert r == 29
+    check(Ui, S, Vi, X, s, Y, r, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_orthogonalize_truncation(ctx, prec):
+    U, S, V = synth.sketch_factors(1200, 1000, 48, 48, seed=5, s_range=1e-6)
+    X, s, Y, r, Ui, Vi = run(ctx, U, S, V, prec, trunc_rtol=1e-4)
+    assert 0 < r < 48
+    check(Ui, S, Vi, X, s, Y, r, prec, trunc_rtol=1e-4)
+
+
+def test_orthogonalize_full_size_properties(ctx):
+    """Dense-workload shape, FP32: orthogonality on the device and the product
+    on sampled rows, against the factors it was given."""
+    from paper_1607_07395_gb300 import cabs
+    m, n, k = 65536, 32768, 256
+    g = torch.Generator(device="cuda").manual_seed(17)
+    U = torch.randn(m, k, device="cuda", generator=g)
+    V = torch.randn(n, k, device="cuda", generator=g)
+    U /= U.norm(dim=0)
+    V /= V.norm(dim=0)
+    S = torch.logspace(0, -3, k, device="cuda", dtype=torch.float64)
+    X, s, Y, rank = cabs.cabs_orthogonalize(ctx, U, S, V, prec="fp32")
+    torch.cuda.synchronize()
+    assert int(rank.item()) == k
+    sh = s.cpu().numpy()
+    assert np.all(np.diff(sh) <= 0)
+    for F in (X, Y):
+        G = (F.double().T @ F.double()).cpu().numpy()
+        assert np.abs(G - np.eye(k)).max() < 2e-5
+    rows = torch.randint(0, m, (64,), device="cuda", generator=g)
+    got = ((X[rows].double() * s) @ Y.double().T).cpu().numpy()
+    want = ((U[rows].double() * S) @ V.double().T).cpu().numpy()
+    assert np.abs(got - want).max() < 2e-5 * sh[0] * np.sqrt(k)
+
+
+@pytest.mark.parametrize("mode", ["pinv", "stabilized"])
+def test_sketch_svd_form_matches_oracle(ctx, mode):
+    """CABS_FLAG_SVD_FORM: the plain FP64 sketch (Algorithm 2) returned in SVD
+    form equals the oracle's sketch orthogonalised by the oracle."""
+    from paper_1607_07395_gb300 import cabs
+    A = synth.plain_lowrank()
+    m, n = A.shape
+    Ad = torch.from_numpy(A).cuda()
+    p = cabs.make_params(m, n, 20, iters=5, seed=1607, prec="fp64", core=mode, flags=cabs.FLAG_SVD_FORM)
+    sk = cabs.cabs_sketch(ctx, cabs.dense_source(Ad), p)
+    torch.cuda.synchronize()
+    ref = o.cabs(o.DenseSource(A), 20, iters=5, seed=1607, mode=mode)
+    Xo, so, Yo = o.orthogonalize(ref.final.U, ref.final.S, ref.final.V)
+    r = sk.diag().rank_final
+    assert r == len(so)
+    X, s, Y = sk.U.cpu().numpy(), sk.S.cpu().numpy(), sk.V.cpu().numpy()
+    assert np.allclose(s[:r], so, rtol=1e-10, atol=1e-10 * so[0]) and np.all(s[r:] == 0)
+    assert np.abs(X[:, :r].T @ X[:, :r] - np.eye(r)).max() < 1e-10
+    assert np.abs(Y[:, :r].T @ Y[:, :r] - np.eye(r)).max() < 1e-10
+    want = (Xo * so) @ Yo.T
+    assert np.linalg.norm((X * s) @ Y.T - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_sketch_svd_form_fp32_properties(ctx):
+    """FP32 dense sketch in SVD form: same product as the plain form, orthonormal factors."""
+    from paper_1607_07395_gb300 import cabs
+    A, _, _, _ = synth.decaying_lowrank_host(4096, 2048, rank=256, decay=30, noise_std=1e-4, seed=1607)
+    Ad = torch.from_numpy(A).cuda()
+    src = cabs.dense_source(Ad)
+    p0 = cabs.make_params(4096, 2048, 256, iters=5, seed=1607, prec="fp32", core="stabilized")
+    p1 = cabs.make_params(4096, 2048, 256, iters=5, seed=1607, prec="fp32", core="stabilized",
+                          flags=cabs.FLAG_SVD_FORM)
+    a = cabs.cabs_sketch(ctx, src, p0)
+    b = cabs.cabs_sketch(ctx, src, p1)
+    torch.cuda.synchronize()
+    assert a.rows.tolist() == b.rows.tolist() and a.cols.tolist() == b.cols.tolist()
+    r = b.diag().rank_final
+    X, s, Y = b.U.double(), b.S, b.V.double()
+    for F in (X[:, :r], Y[:, :r]):
+        assert (F.T @ F - torch.eye(r, dtype=torch.float64, device="cuda")).abs().max().item() < 2e-5
+    rows = torch.arange(0, 4096, 64, device="cuda")
+    got = (X[rows] * s) @ Y.T
+    want = (a.U[rows].double() * a.S) @ a.V.double().T
+    assert (got - want).abs().max().item() < 2e-5 * s[0].item() * 16
+    assert torch.all(s[1:] <= s[:-1])

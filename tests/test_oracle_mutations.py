@@ -138,3 +138,31 @@ ORTH_MUTANTS = [
 def test_orthogonalize_mutants_rejected(old, new):
     bad = mutate(o.orthogonalize, old, new)
     assert rejects(lambda: pins.pin_orthogonalize(bad))
+
+
+CUR_MUTANTS = [
+    ("Cbar = C[rows_t, :]", "Cbar = C[rows_t[::-1], :]"),                      # rows out of order
+    ("Rbar = Rt[cols_t, :].T", "Rbar = Rt[cols_t, :].T[:, ::-1]"),
+    ("Ustar = pinv_trunc(Cbar, trunc_rtol) @ M @ pinv_trunc(Rbar, trunc_rtol)",
+     "Ustar = pinv_trunc(Cbar, trunc_rtol) @ M.T @ pinv_trunc(Rbar, trunc_rtol)"),  # transposed target
+    ("Ustar = pinv_trunc(Cbar, trunc_rtol) @ M @ pinv_trunc(Rbar, trunc_rtol)",
+     "Ustar = Cbar.T @ M @ pinv_trunc(Rbar, trunc_rtol)"),                      # transpose for pinv
+]
+
+PINV_MUTANTS = [
+    ("keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]", "keep = sb > max(trunc_rtol, min(B.shape) * EPS64) * sb[0]"),
+    ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep].T * sb[keep]) @ Ub[:, keep].T"),
+    ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep] / sb[keep][:, None]).T @ Ub[:, keep].T[::-1]"),
+]
+
+
+@pytest.mark.parametrize("old,new", CUR_MUTANTS)
+def test_br_cur_mutants_rejected(old, new):
+    bad = mutate(o.br_cur, old, new)
+    assert rejects(lambda: pins.pin_br_cur(bad, o.DenseSource))
+
+
+@pytest.mark.parametrize("old,new", PINV_MUTANTS)
+def test_pinv_mutants_rejected(old, new):
+    bad = mutate(o.pinv_trunc, old, new)
+    assert rejects(lambda: pins.pin_pinv_trunc(bad))

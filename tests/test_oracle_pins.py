@@ -148,3 +148,24 @@ def test_plain_fp64_regression_fixture():
 
 def test_orthogonalize():
     pins.pin_orthogonalize(o.orthogonalize)
+
+
+def test_pinv_trunc():
+    pins.pin_pinv_trunc(o.pinv_trunc)
+
+
+def test_br_cur():
+    pins.pin_br_cur(o.br_cur, o.DenseSource)
+
+
+def test_sketch_cur_draws():
+    """Sketch-CUR draws k_b base and 3 k_b target indices per side, distinct,
+    sorted, inside the matrix; an exactly rank-3 matrix is recovered."""
+    from workloads import synth
+    A = synth.exact_lowrank_int(300, 200, 3, seed=4)
+    r = o.sketch_cur(o.DenseSource(A), 5, seed=11)
+    for idx, k, N in ((r.rows_b, 5, 300), (r.cols_b, 5, 200), (r.rows_t, 15, 300), (r.cols_t, 15, 200)):
+        assert len(idx) == k and len(set(idx.tolist())) == k and np.all(np.diff(idx) > 0)
+        assert idx.min() >= 0 and idx.max() < N
+    assert not np.array_equal(r.rows_b, r.rows_t[:5])
+    assert np.allclose(r.C @ r.U @ r.Rt.T, A, atol=1e-9 * np.abs(A).max())

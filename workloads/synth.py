@@ -131,6 +131,26 @@ def decaying_lowrank_device(m: int, n: int, rank: int = 256, decay: float = 30.0
     return A, U, s, V
 
 
+def sketch_factors(m: int, n: int, k: int, rank: int | None = None, seed: int = 11, s_range: float = 1e-3,
+                   dup: bool = False):
+    """Factors shaped like a sketching output: U (m x k) and V (n x k) with
+    Gaussian unit-norm columns, S geometric from 1 down to s_range, columns
+    and S entries beyond `rank` zero; with dup, column 1 of U repeats column 0."""
+    g = host_rng(seed, 5)
+    r = k if rank is None else rank
+    U = g.standard_normal((m, k))
+    V = g.standard_normal((n, k))
+    U /= np.linalg.norm(U, axis=0)
+    V /= np.linalg.norm(V, axis=0)
+    S = np.geomspace(1.0, s_range, k) if k > 1 else np.ones(1)
+    U[:, r:] = 0.0
+    V[:, r:] = 0.0
+    S[r:] = 0.0
+    if dup and r > 1:
+        U[:, 1] = U[:, 0]
+    return U, S, V
+
+
 def batched_specs(count: int = 512, seed: int = 1607, lo: int = 1000, hi: int = 20000,
                   rank_lo: int = 10, rank_hi: int = 100, k_lo: int = 16, k_hi: int = 128):
     """Per-member (m, n, rank, k) for the batched workload: m, n ~ U[lo, hi],
