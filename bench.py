@@ -199,9 +199,20 @@ def algorithmic(name, wl, k, iters, elem_bytes, svd_sweeps, svd_refine=None):
         return "alu", its * 6 * 2.0 * k ** 3, "TFLOP/s", 2
     if name == "snap_cand_kernel":
         return "alu", 3.0 * (m + n) * k * d, "TFLOP/s", 2
+    if name in ("extrap_gemm_kernel(X = U T_u)", "extrap_gemm_kernel(Y = V T_v)"):
+        # the orthogonalisation's tall products (supplementary Section 3), once per sketch
+        side = m if "X = U" in name else n
+        return "alu", 2.0 * side * k * k, "TFLOP/s", 1
     if name.startswith("extrap_gemm_kernel"):
         side = m if "C V_w" in name else n
         return "alu", 2 * 2.0 * side * k * k, "TFLOP/s", 2
+    if name == "gram_kernel":
+        # U^T U and V^T V by upper-triangle tiles of 128 x 128 (FP32): two launches per sketch
+        nt = (k + 127) // 128
+        return "alu", 2.0 * (m + n) * (nt * (nt + 1) // 2) * 128 * 128, "TFLOP/s", 2
+    if name == "lev_keys_kernel":
+        # reads the orthonormal pilot factors once, writes one 8-byte key per row
+        return "hbm", (m + n) * (k * elem_bytes + 8.0), "GB/s", 2
     if name in ("rbf_block_kernel(C)", "rbf_block_kernel(Rt)"):
         side = m if name.endswith("(C)") else n
         return "alu", 2 * side * k * (3.0 * wl.get("d", 16) + 20), "TFLOP/s", 2
@@ -473,8 +484,9 @@ def run_cabs(args):
     # launched as one captured graph over `lanes` streams, plus each error
     prec = "fp64" if args.workload == "plain" else args.prec
     B = 1 if args.form == "plain" else args.batch
+    flags = follow_flags(cabs, args)
     params = [cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank * 1000 + b, prec=prec,
-                               trunc_rtol=trunc_rtol(wl, k),
+                               trunc_rtol=trunc_rtol(wl, k), flags=flags,
                                core=wl["core"], err_samples=samples, err_seed=3) for b in range(B)]
     srcs = [src] * B
     outs = [cabs.alloc_result(p, device) for p in params]
@@ -565,7 +577,7 @@ def run_cabs(args):
     plain = None
     if args.form != "plain" and not args.no_plain and args.workload != "plain":
         pp = cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank * 1000, prec="fp32", core=wl["core"],
-                              trunc_rtol=trunc_rtol(wl, k),
+                              trunc_rtol=trunc_rtol(wl, k), flags=flags,
                               err_samples=samples, err_seed=3)
         wsp = torch.empty(cabs.cabs_workspace_size(src, pp) + 512, dtype=torch.uint8, device=device)
         outp = cabs.alloc_result(pp, device)
@@ -612,6 +624,7 @@ def run_cabs(args):
                data="synthetic",
                config=dict(workload=args.workload, desc=wl["desc"], m=wl["m"], n=wl["n"], k=k, iters=iters,
                            prec=prec, core=wl["core"], trunc_rtol=trunc_rtol(wl, k), form=args.form,
+                           follow=args.follow, svd_form=bool(args.svd_form),
                            sketches_per_step=B,
                            lanes=args.lanes if B > 1 else 1, graph=B > 1,
                            parallelism=f"replicas x{world}",
@@ -639,6 +652,116 @@ def run_cabs(args):
     if world > 1:
         dist.destroy_process_group()
     return res
+
+
+def follow_flags(cabs, args):
+    """cabs_params flags of the follow-up variant (Section 5: (d) weighted
+    k-means, (e) leverage scores, (f) hard threshold) and the SVD-form output
+    (supplementary Section 3)."""
+    f = {"kmeans": 0, "threshold": cabs.FLAG_HARD_THRESHOLD, "leverage": cabs.FLAG_LEVERAGE}[args.follow]
+    return f | (cabs.FLAG_SVD_FORM if args.svd_form else 0)
+
+
+def run_sketch_cur(args):
+    """Sketch-CUR (Section 2.2, Algorithm 1; Section 5 comparison (a)) on the
+    workload's matrix: kb base and kt = 3 kb target samples per side; B
+    sketches per step on B streams (one workspace each)."""
+    import torch
+
+    from paper_1607_07395_gb300 import cabs
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    wl = dict(WORKLOADS[args.workload])
+    kb = args.kb or max(1, min(wl["k"], cabs.MAX_K) // 3)
+    kt = min(3 * kb, cabs.MAX_K, wl["m"], wl["n"])
+    prec = "fp64" if args.workload == "plain" else "fp32"
+    ctx = cabs.Context(local)
+    inp = make_inputs(wl, device, seed=1607 + rank)
+    src = make_source(cabs, wl, inp)
+    B = 1 if args.form == "plain" else args.batch
+    streams = [torch.cuda.Stream(device=device) for _ in range(B)]
+    ps = [cabs.make_cur_params(wl["m"], wl["n"], kb, kt, seed=1607 + rank * 1000 + b, prec=prec) for b in range(B)]
+    outs = [cabs.cabs_sketch_cur(ctx, src, p, stream=st) for p, st in zip(ps, streams)]
+    main = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for p, st, o in zip(ps, streams, outs):
+            st.wait_event(ev)
+            cabs.cabs_sketch_cur(ctx, src, p, stream=st, ws=o.ws)
+        for st in streams:
+            main.wait_stream(st)
+        return []
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    if args.steps <= 0:
+        t0 = time.time()
+        step()
+        torch.cuda.synchronize()
+        est = max((time.time() - t0) * 1e3, 1e-3)
+        args.steps = int(rank_max(min(2000, max(5, math.ceil(2000.0 / est))), device))
+    sampler = ClockSampler(local)
+    launches0 = cabs.cabs_launch_count()
+    sampler.start()
+    per_step, total_ms, _ = timed_steps(ctx, cabs, step, args.steps, main, world, barrier)
+    clocks = sampler.stop()
+    launches = cabs.cabs_launch_count() - launches0
+    cabs.cabs_profile_read(ctx, reset=True)
+    cabs.cabs_profile_enable(ctx, True)
+    for p, o in zip(ps, outs):
+        cabs.cabs_sketch_cur(ctx, src, p, stream=main, ws=o.ws)
+    torch.cuda.synchronize()
+    cabs.cabs_profile_enable(ctx, False)
+    prof = cabs.cabs_profile_read(ctx, reset=True)
+    samples = wl.get("samples", 0)
+    sp = cabs.make_params(wl["m"], wl["n"], kb, prec=prec)
+    errs = [cabs.cabs_error(ctx, src, sp, o, samples=samples, seed=3) for o in outs]
+    if rank != 0:
+        return None
+    total = sum(x[1] for x in prof.values())
+    table = {nm: dict(launches=l, total_ms=round(t, 4), share=round(t / total, 4))
+             for nm, (l, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    top = next(iter(table))
+    K = max(kb, kt)
+    roof = None
+    if top.startswith("svd32"):
+        # FP32 Jacobi on the K x K padded C_bar and R_bar: 18 K flops per column pair per sweep
+        rk = [int(x) for x in outs[0].ranks.tolist()]
+        l, t = prof[top]
+        fl = sum(sw * (K * (K - 1) / 2) * 18.0 * K for sw in rk[2:4])
+        ach = fl / (t / max(l, 1) * 2 / 1e3) / 1e12  # two SVD launches per sketch
+        roof = dict(kernel=top, bound="alu", achieved=round(ach, 4), peak=round(FP32_PEAK_TFLOPS, 3),
+                    unit="TFLOP/s", frac=round(ach / FP32_PEAK_TFLOPS, 5), traffic=None,
+                    avg_launch_ms=round(t / max(l, 1), 5), peak_source="derived from unit counts x 2.07 GHz",
+                    note=f"FP32 Jacobi of a {K} x {K} matrix on one 16-CTA cluster: latency-bound")
+    return dict(metric=METRIC, value=round(job_value(world, B, args.steps, total_ms), 4), unit="sketches/s",
+                n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4),
+                higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype={"fp64": "f64", "fp32": "f32"}[prec] + "+f64core", data="synthetic",
+                config=dict(workload=args.workload, algo="sketch_cur", desc=wl["desc"], m=wl["m"], n=wl["n"],
+                            kb=kb, kt=kt, prec=prec, sketches_per_step=B, streams=B,
+                            parallelism=f"replicas x{world}"),
+                latency_ms=dict(step_p50=round(statistics.median(per_step), 4)),
+                rel_fro_error=dict(median=statistics.median(errs), max=max(errs),
+                                   samples=samples or "exact"),
+                ranks=[int(x) for x in outs[0].ranks.tolist()[:2]],
+                svd_sweeps=[int(x) for x in outs[0].ranks.tolist()[2:4]], gpu_launches=int(launches),
+                roofline=roof, kernels=table, clocks=clocks, e2e=None,
+                e2e_note="Sketch-CUR is a comparison row: device-resident inputs only")
 
 
 def run_reference(args):
@@ -723,6 +846,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--batch-count", type=int, default=512, help="members of the batched workload")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="measured seconds of the serving workload")
+    ap.add_argument("--follow", default="kmeans", choices=["kmeans", "threshold", "leverage"],
+                    help="follow-up sampling: weighted k-means (Algorithm 2), or the leverage-score or "
+                         "hard-threshold variants of Section 5")
+    ap.add_argument("--svd-form", action="store_true", help="return every sketch in SVD form (orthogonalised)")
+    ap.add_argument("--algo", default="cabs", choices=["cabs", "sketch_cur"],
+                    help="cabs (Algorithm 2) or the Sketch-CUR comparison (Algorithm 1, target = 3 x base)")
+    ap.add_argument("--kb", type=int, default=0, help="Sketch-CUR base samples (default k / 3)")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -732,6 +862,8 @@ def main():
         res = run_systems(args)
     elif args.impl == "reference":
         res = run_reference(args)
+    elif args.algo == "sketch_cur":
+        res = run_sketch_cur(args)
     else:
         res = run_cabs(args)
     if res is not None:

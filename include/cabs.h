@@ -123,6 +123,22 @@ typedef struct {
  * and the snap. iters and upsilon_pow are then unused, and the k-means
  * diagnostics (e_rows, e_cols, T_rows, T_cols) stay zero. */
 #define CABS_FLAG_HARD_THRESHOLD 4
+/* Return the sketch in SVD form (supplementary Section 3, as
+ * cabs_orthogonalize): U and V with orthonormal columns and S the singular
+ * values of U diag(S) V^T in descending order; diag.rank_final is then the
+ * rank that form keeps. */
+#define CABS_FLAG_SVD_FORM 8
+/* Follow-up rows and columns by leverage scores (Section 5, follow-up
+ * variant (e)): the pilot sketch P Q^T is put in SVD form X diag(s) Y^T
+ * (supplementary Section 3, as cabs_orthogonalize with S = 1), and k2 distinct
+ * rows (columns) are drawn without replacement with probabilities
+ * proportional to the leverage scores |X_i|^2 (|Y_j|^2): the k2 largest A-Res
+ * keys u_i^(1/l_i) (Efraimidis and Spirakis, 2006), ranked as l_i / (-ln u_i)
+ * in FP64, u_i = ((r_i >> 11) + 1/2) 2^-53, r_i = word 0 of
+ * Philox((i, 0, 0, 0), (seed, 6)) for rows and (seed, 7) for columns, ties to
+ * the lower index. Excludes CABS_FLAG_HARD_THRESHOLD; the k-means
+ * diagnostics stay zero. */
+#define CABS_FLAG_LEVERAGE 16
 
 /* Device-side diagnostics, written by the kernels of one sketch. */
 typedef struct {
@@ -310,6 +326,59 @@ cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const 
 cabs_status cabs_threshold_workspace_size(int64_t M, size_t* bytes);
 cabs_status cabs_threshold(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, int32_t k2, int32_t prec,
                            int32_t* d_sorted, void* ws, size_t ws_bytes, cabs_stream stream);
+
+/* Supplementary Section 3 (orthogonalisation of the sketching output):
+ * rewrites U diag(S) V^T as X diag(s) Y^T with orthonormal columns in X and
+ * Y, in O((m + n) k^2): U = U_0 Sigma_0 V_0^T (thin SVD, here from the Gram
+ * matrix U^T U), then the SVD of Sigma_0 V_0^T diag(S) V^T = U_1 Sigma_1 V_1^T
+ * (reduced to k x k through V^T V), X = U_0 U_1, s = diag(Sigma_1), Y = V_1.
+ * U (m x k), V (n x k): elem (FP64 for CABS_PREC_FP64, else FP32), ld k,
+ * device; S (k, FP64, device). Outputs X (m x k), Y (n x k) elem, ld k, and
+ * s (k, FP64, descending) on the device; components with
+ * s_i <= max(trunc_rtol, k 2^-52) s_1, and directions in which U or V is
+ * numerically singular (a Gram eigenvalue at or below k 2^-52, or 2^-30 for
+ * FP32, of the largest), are dropped: zero columns and zero s entries beyond
+ * the kept rank, which goes to d_rank (device int32, may be NULL).
+ * Orthogonality of X, Y: near 1e-13 (FP64) and 1e-6 (FP32) times
+ * cond(U)^2, cond(V)^2. X, Y must not overlap U, V. 1 <= k <= CABS_MAX_K,
+ * m, n >= 1. ws: cabs_orthogonalize_workspace_size() bytes (256-aligned). */
+cabs_status cabs_orthogonalize_workspace_size(int64_t m, int64_t n, int32_t k, int32_t prec, size_t* bytes);
+cabs_status cabs_orthogonalize(cabs_ctx* ctx, int64_t m, int64_t n, int32_t k, int32_t prec, double trunc_rtol,
+                               const void* U, const double* S, const void* V, void* X, double* s, void* Y,
+                               int32_t* d_rank, void* ws, size_t ws_bytes, cabs_stream stream);
+
+/* Section 2.2, Algorithm 1 (Bilateral Resampling CUR) as Sketch-CUR:
+ * independent uniform base samplings I^b_r, I^b_c (kb each; the pilot draw,
+ * Philox tags 0 and 1) and target samplings I^t_r, I^t_c (kt each, tags 4 and
+ * 5; Section 5 compares at kt = 3 kb). C = A[:, I^b_c], R = A[I^b_r, :],
+ * C_bar = A[I^t_r, I^b_c], R_bar = A[I^b_r, I^t_c], M = A[I^t_r, I^t_c],
+ * U* = C_bar^+ M R_bar^+ (FP64; pseudo-inverses truncated at
+ * sigma_i <= max(trunc_rtol, K 2^-52) sigma_1, K = max(kb, kt)).
+ * A ~ C U* R = U diag(S) V^T with U = C U*, S = 1, V = R^T. */
+typedef struct {
+  int64_t m, n;       /* A is m x n */
+  int32_t kb, kt;     /* base and target samples per side, 1..min(m, n, CABS_MAX_K) */
+  uint64_t seed;      /* Philox key word 0 of all four draws */
+  int32_t prec;       /* cabs_prec: elem type of U, V (FP64, else FP32) */
+  double trunc_rtol;
+} cabs_cur_params;
+
+typedef struct {
+  void* U;            /* elem, m x kb (ld kb): C U* */
+  double* S;          /* kb: ones */
+  void* V;            /* elem, n x kb (ld kb): R^T */
+  double* Ustar;      /* kb x kb FP64 row-major, or NULL */
+  int32_t *rows_b, *cols_b;   /* kb each, ascending */
+  int32_t *rows_t, *cols_t;   /* kt each, ascending */
+  int32_t* ranks;     /* 8 (or NULL): kept ranks of C_bar^+ and R_bar^+; the FP32
+                         Jacobi sweeps and the FP64 refinement iterations (-1:
+                         FP64 Jacobi fallback) of their SVDs; the SVD status
+                         bits (as cabs_diag.status); one reserved */
+} cabs_cur_result;
+
+cabs_status cabs_sketch_cur_workspace_size(const cabs_source* src, const cabs_cur_params* p, size_t* bytes);
+cabs_status cabs_sketch_cur(cabs_ctx* ctx, const cabs_source* src, const cabs_cur_params* p, void* ws,
+                            size_t ws_bytes, cabs_stream stream, const cabs_cur_result* out);
 
 /* ----------------------------------------------------------- profiling */
 

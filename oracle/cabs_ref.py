@@ -29,6 +29,11 @@ Steps and the passages they follow (section / equation / algorithm of the paper)
                        (Section 3.2, last paragraph)
 ``hard_threshold``     follow-up by the k2 largest-norm rows (Section 5,
                        follow-up variant (f))
+``leverage_scores`` /  follow-up by approximate leverage scores (Section 5,
+``weighted_sample``    variant (e)): squared row norms of the orthonormal
+                       factors of the pilot sketch (supplementary Section 3
+                       names leverage scores as the use of that form), used
+                       as sampling probabilities without replacement
 ``cabs``               Algorithm 2 end to end
 ``orthogonalize``      the sketch in SVD form (supplementary Section 3)
 ``pinv_trunc``         pseudo-inverse by the SVD with the truncation below
@@ -44,7 +49,8 @@ Steps and the passages they follow (section / equation / algorithm of the paper)
 Readings where the paper is silent (the GPU library takes the same ones):
 
 * Index draw: Philox4x64-10 with key (seed, tag), tag 0 = rows, 1 = columns,
-  2 = error-estimate samples, 4 / 5 = Sketch-CUR target rows / columns; counter (i, 0, 0, 0) for the i-th draw; output
+  2 = error-estimate samples, 4 / 5 = Sketch-CUR target rows / columns,
+  6 / 7 = leverage-score follow-up rows / columns; counter (i, 0, 0, 0) for the i-th draw; output
   word 0 mapped to [0, N - i) by the high half of the 128-bit product
   (multiply-shift, bias <= N / 2^64). The drawn indices are returned in draw
   order and sorted ascending; W, C and R use the sorted order.
@@ -78,6 +84,8 @@ TAG_COLS = 1
 TAG_EVAL = 2
 TAG_TARGET_ROWS = 4
 TAG_TARGET_COLS = 5
+TAG_LEV_ROWS = 6
+TAG_LEV_COLS = 7
 
 MASK64 = (1 << 64) - 1
 _M0 = 0xD2E7470EE14C6C93
@@ -392,6 +400,38 @@ def snap(X: np.ndarray, Z: np.ndarray):
     return out, np.sort(out)
 
 
+def leverage_scores(X: np.ndarray) -> np.ndarray:
+    """Leverage scores of the rows of an orthonormal basis X: |X_i|^2."""
+    X = np.asarray(X, dtype=np.float64)
+    return (X * X).sum(axis=1)
+
+
+def philox_uniform(seed: int, tag: int, N: int) -> np.ndarray:
+    """u_i = ((r_i >> 11) + 1/2) 2^-53 in (0, 1), r_i = word 0 of
+    Philox((i, 0, 0, 0), (seed, tag)), i = 0..N-1 (exact in FP64)."""
+    c0 = np.arange(N, dtype=np.uint64)
+    z = np.zeros(N, dtype=np.uint64)
+    r0 = philox4x64_10_vec(c0, z, z, z, seed, tag)[0]
+    return ((r0 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+
+
+def weighted_sample(w: np.ndarray, k: int, seed: int, tag: int):
+    """k distinct indices drawn without replacement with probabilities
+    proportional to w (the A-Res scheme of Efraimidis and Spirakis, 2006):
+    index i gets the key u_i^(1/w_i), u_i = philox_uniform(seed, tag)_i, and
+    the k largest keys win. The keys are ranked through the increasing map
+    u^(1/w) -> w / (-ln u), evaluated in FP64; ties go to the lower index, and
+    w_i = 0 gives key 0. Returns (selected indices ascending, keys)."""
+    w = np.asarray(w, dtype=np.float64)
+    N = len(w)
+    if not (0 <= k <= N):
+        raise ValueError("need 0 <= k <= N")
+    u = philox_uniform(seed, tag, N)
+    keys = w / -np.log(u)
+    order = np.lexsort((np.arange(N), -keys))
+    return np.sort(order[:k]), keys
+
+
 def hard_threshold(X: np.ndarray, k2: int):
     """Follow-up selection by hard threshold (Section 5, follow-up variant (f)):
     instead of clustering, keep the k2 rows whose weight Upsilon(|X_l|_2) is
@@ -471,8 +511,9 @@ def cabs(source, k1: int, k2: int = None, iters: int = 5, seed: int = 1607,
 
     1. pilot sampling of k1 random rows and columns; 2. pilot sketching and
     embeddings P, Q; 3. weighted k-means on P and on Q, centres snapped to
-    rows -> follow-up indices (follow="threshold": the hard-threshold variant
-    of Section 5 instead); 4. follow-up sketching on the new gather."""
+    rows -> follow-up indices (follow="threshold" or "leverage": the
+    hard-threshold or leverage-score variant of Section 5 instead);
+    4. follow-up sketching on the new gather."""
     k2 = k1 if k2 is None else k2
     m, n = source.m, source.n
     if not (1 <= k2 <= k1 <= min(m, n)):
@@ -487,13 +528,20 @@ def cabs(source, k1: int, k2: int = None, iters: int = 5, seed: int = 1607,
         km_r = km_c = None
         rows_o = rows = hard_threshold(P, k2)
         cols_o = cols = hard_threshold(Q, k2)
+    elif follow == "leverage":
+        # Section 5 variant (e): the pilot sketch P Q^T in SVD form
+        # (supplementary Section 3), its leverage scores as probabilities
+        km_r = km_c = None
+        X, _, Y = orthogonalize(P, np.ones(k1), Q, trunc_rtol)
+        rows_o = rows = weighted_sample(leverage_scores(X), k2, seed, TAG_LEV_ROWS)[0]
+        cols_o = cols = weighted_sample(leverage_scores(Y), k2, seed, TAG_LEV_COLS)[0]
     elif follow == "kmeans":
         km_r = weighted_kmeans(P, Ir_drawn[:k2], iters, upsilon_pow)
         km_c = weighted_kmeans(Q, Ic_drawn[:k2], iters, upsilon_pow)
         rows_o, rows = snap(P, km_r.Z)
         cols_o, cols = snap(Q, km_c.Z)
     else:
-        raise ValueError("follow must be 'kmeans' or 'threshold'")
+        raise ValueError("follow must be 'kmeans', 'threshold' or 'leverage'")
     Cb, Rtb, Wb = source.gather(rows, cols)
     final = sketching(Cb, Rtb, Wb, m, n, mode, trunc_rtol)
     ep_r, _, Tp_r = encoding_error(P, Ir_drawn[:k2], upsilon_pow)
@@ -536,13 +584,15 @@ def orthogonalize(U: np.ndarray, S: np.ndarray, V: np.ndarray, trunc_rtol: float
 
 def pinv_trunc(B: np.ndarray, trunc_rtol: float = 0.0) -> np.ndarray:
     """Pseudo-inverse V diag(1/s) U^T of B = U diag(s) V^T over the singular
-    values s_i > max(trunc_rtol, kmax 2^-52) s_1, kmax = max(B.shape) (the
-    truncation rule of the sketching routine, MATLAB pinv's default)."""
+    values s_i > max(trunc_rtol, sqrt(kmax 2^-52)) s_1, kmax = max(B.shape).
+    Algorithm 1 leaves the tolerance open; the floor is the square root of
+    the sketching routine's (MATLAB pinv's) k 2^-52, the resolution of
+    B^T B, through which a linear-cost implementation reaches B^+."""
     B = np.asarray(B, dtype=np.float64)
     Ub, sb, Vbt = np.linalg.svd(B, full_matrices=False)
     if len(sb) == 0 or sb[0] == 0.0:
         return np.zeros(B.T.shape)
-    keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]
+    keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]
     return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T
 
 

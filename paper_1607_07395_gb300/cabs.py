@@ -24,6 +24,8 @@ MAX_K, MAX_D, MAX_ITERS = 256, 64, 64
 FLAG_FOLLOW_ERR = 1
 FLAG_ERROR = 2
 FLAG_HARD_THRESHOLD = 4
+FLAG_SVD_FORM = 8
+FLAG_LEVERAGE = 16
 PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16}
 CORES = {"pinv": CORE_PINV, "stabilized": CORE_STABILIZED}
 
@@ -58,6 +60,17 @@ class cabs_result(C.Structure):
     _fields_ = [("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p), ("rows", C.c_void_p),
                 ("cols", C.c_void_p), ("pilot_rows", C.c_void_p), ("pilot_cols", C.c_void_p),
                 ("diag", C.c_void_p), ("err", C.c_void_p)]
+
+
+class cabs_cur_params(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("kb", C.c_int32), ("kt", C.c_int32), ("seed", C.c_uint64),
+                ("prec", C.c_int32), ("trunc_rtol", C.c_double)]
+
+
+class cabs_cur_result(C.Structure):
+    _fields_ = [("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p), ("Ustar", C.c_void_p),
+                ("rows_b", C.c_void_p), ("cols_b", C.c_void_p), ("rows_t", C.c_void_p), ("cols_t", C.c_void_p),
+                ("ranks", C.c_void_p)]
 
 
 _lib = None
@@ -96,6 +109,10 @@ def lib():
         "cabs_snap": ([vp, vp, i64, i32, vp, i32, i32, vp, vp, vp, sz, vp], i32),
         "cabs_threshold_workspace_size": ([i64, P(sz)], i32),
         "cabs_threshold": ([vp, vp, i64, i32, i32, i32, vp, vp, sz, vp], i32),
+        "cabs_orthogonalize_workspace_size": ([i64, i64, i32, i32, P(sz)], i32),
+        "cabs_sketch_cur_workspace_size": ([P(cabs_source), P(cabs_cur_params), P(sz)], i32),
+        "cabs_sketch_cur": ([vp, P(cabs_source), P(cabs_cur_params), vp, sz, vp, P(cabs_cur_result)], i32),
+        "cabs_orthogonalize": ([vp, i64, i64, i32, i32, f64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp], i32),
         "cabs_serve_start": ([vp, vp, sz, i32], i32),
         "cabs_serve_submit": ([vp, P(cabs_source), P(cabs_params), P(u64)], i32),
         "cabs_serve_poll": ([vp, u64, P(cabs_result), P(f64), i32], i32),
@@ -119,7 +136,8 @@ def exported_names():
             "cabs_sketch_batched", "cabs_error_workspace_size", "cabs_error", "cabs_draw_indices", "cabs_gather",
             "cabs_sketching_workspace_size", "cabs_sketching", "cabs_kmeans_workspace_size", "cabs_kmeans",
             "cabs_snap_workspace_size", "cabs_snap", "cabs_threshold_workspace_size", "cabs_threshold",
-            "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
+            "cabs_orthogonalize_workspace_size", "cabs_orthogonalize", "cabs_sketch_cur_workspace_size",
+            "cabs_sketch_cur", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
             "cabs_launch_count", "cabs_error_noalloc"]
 
@@ -427,6 +445,66 @@ def cabs_threshold(ctx: Context, X, k2, prec="fp64", stream=None):
     srt = torch.empty(k2, dtype=torch.int32, device=dev)
     _check(lib().cabs_threshold(ctx.h, _ptr(X), M, d, k2, p, _ptr(srt), wp, wn, _stream(stream)), ctx.h)
     return srt
+
+
+def cabs_orthogonalize(ctx: Context, U, S, V, prec="fp64", trunc_rtol=0.0, stream=None):
+    """Supplementary Section 3: U diag(S) V^T -> X diag(s) Y^T with orthonormal X, Y.
+    Returns (X, s, Y, rank) on the device; columns and s beyond rank are zero."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    m, k = U.shape
+    n = V.shape[0]
+    p = PRECS[prec] if isinstance(prec, str) else prec
+    nb = C.c_size_t()
+    _check(lib().cabs_orthogonalize_workspace_size(m, n, k, p, C.byref(nb)))
+    ws = _ws(nb.value, dev)
+    wp, wn = _aligned(ws)
+    X = torch.empty(m, k, dtype=U.dtype, device=dev)
+    Y = torch.empty(n, k, dtype=V.dtype, device=dev)
+    s = torch.empty(k, dtype=torch.float64, device=dev)
+    rank = torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib().cabs_orthogonalize(ctx.h, m, n, k, p, trunc_rtol, _ptr(U), _ptr(S), _ptr(V), _ptr(X), _ptr(s),
+                                    _ptr(Y), _ptr(rank), wp, wn, _stream(stream)), ctx.h)
+    return X, s, Y, rank
+
+
+class CurSketch:
+    """Device outputs of one Sketch-CUR: A ~ U diag(S) V^T with U = C U*, S = 1, V = R^T."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def make_cur_params(m, n, kb, kt=None, seed=1607, prec="fp64", trunc_rtol=0.0):
+    p = PRECS[prec] if isinstance(prec, str) else prec
+    return cabs_cur_params(m=m, n=n, kb=kb, kt=3 * kb if kt is None else kt, seed=seed, prec=p,
+                           trunc_rtol=trunc_rtol)
+
+
+def cabs_sketch_cur(ctx: Context, src: Source, p: cabs_cur_params, stream=None, ws=None):
+    """Section 2.2, Algorithm 1 as Sketch-CUR (see cabs.h)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    nb = C.c_size_t()
+    _check(lib().cabs_sketch_cur_workspace_size(C.byref(src.c), C.byref(p), C.byref(nb)))
+    if ws is None or ws.numel() < nb.value + 256:
+        ws = _ws(nb.value, dev)
+    wp, wn = _aligned(ws)
+    dt = elem_dtype(p.prec)
+    i32 = dict(dtype=torch.int32, device=dev)
+    o = CurSketch(U=torch.empty(p.m, p.kb, dtype=dt, device=dev), S=torch.empty(p.kb, dtype=torch.float64, device=dev),
+                  V=torch.empty(p.n, p.kb, dtype=dt, device=dev),
+                  Ustar=torch.empty(p.kb, p.kb, dtype=torch.float64, device=dev),
+                  rows_b=torch.empty(p.kb, **i32), cols_b=torch.empty(p.kb, **i32),
+                  rows_t=torch.empty(p.kt, **i32), cols_t=torch.empty(p.kt, **i32), ranks=torch.zeros(8, **i32),
+                  ws=ws)
+    res = cabs_cur_result(U=_ptr(o.U), S=_ptr(o.S), V=_ptr(o.V), Ustar=_ptr(o.Ustar), rows_b=_ptr(o.rows_b),
+                          cols_b=_ptr(o.cols_b), rows_t=_ptr(o.rows_t), cols_t=_ptr(o.cols_t), ranks=_ptr(o.ranks))
+    _check(lib().cabs_sketch_cur(ctx.h, C.byref(src.c), C.byref(p), wp, wn, _stream(stream), C.byref(res)), ctx.h)
+    # the factor form U diag(S) V^T, as cabs_error takes it
+    o.result = cabs_result(U=_ptr(o.U), S=_ptr(o.S), V=_ptr(o.V), rows=_ptr(o.rows_b), cols=_ptr(o.cols_b),
+                           pilot_rows=_ptr(o.rows_b), pilot_cols=_ptr(o.cols_b), diag=None, err=None)
+    return o
 
 
 # -------------------------------------------------------------- profiling

@@ -100,8 +100,11 @@ cabs_status validate_params(const cabs_params* p) {
   CABS_REQUIRE(p->core == CABS_CORE_PINV || p->core == CABS_CORE_STABILIZED, "unknown core %d", p->core);
   CABS_REQUIRE(finite(p->upsilon_pow), "upsilon_pow must be finite");
   CABS_REQUIRE(finite(p->trunc_rtol) && p->trunc_rtol >= 0.0, "trunc_rtol must be finite and >= 0");
-  CABS_REQUIRE((p->flags & ~(CABS_FLAG_FOLLOW_ERR | CABS_FLAG_ERROR | CABS_FLAG_HARD_THRESHOLD)) == 0,
+  CABS_REQUIRE((p->flags & ~(CABS_FLAG_FOLLOW_ERR | CABS_FLAG_ERROR | CABS_FLAG_HARD_THRESHOLD | CABS_FLAG_SVD_FORM |
+                             CABS_FLAG_LEVERAGE)) == 0,
                "unknown flags 0x%x", p->flags);
+  CABS_REQUIRE(!((p->flags & CABS_FLAG_HARD_THRESHOLD) && (p->flags & CABS_FLAG_LEVERAGE)),
+               "CABS_FLAG_HARD_THRESHOLD and CABS_FLAG_LEVERAGE exclude each other");
   if (p->flags & CABS_FLAG_ERROR) CABS_REQUIRE(p->err_samples >= 0, "err_samples must be >= 0");
   return CABS_OK;
 }
@@ -135,7 +138,9 @@ SketchWs carve_sketch(Carve& cv, const cabs_source& src, const cabs_params& p) {
   w.Zr = cv.take<char>((size_t)k2 * k1 * eb);
   w.Zc = cv.take<char>((size_t)k2 * k1 * eb);
   w.diag = cv.take<cabs_diag>(1);
-  const size_t core_b = std::max(core_ws_bytes(m, n, k1, eb == 8), core_ws_bytes(m, n, k2, eb == 8));
+  size_t core_b = std::max(core_ws_bytes(m, n, k1, eb == 8), core_ws_bytes(m, n, k2, eb == 8));
+  if (p.flags & CABS_FLAG_SVD_FORM) core_b = std::max(core_b, orth_ws_bytes(m, n, k2, eb == 8));
+  if (p.flags & CABS_FLAG_LEVERAGE) core_b = std::max(core_b, orth_ws_bytes(m, n, k1, eb == 8));
   size_t side_r = std::max(kmeans_ws_bytes(m, k1, k2, p.iters, p.prec), snap_ws_bytes(m, k1, k2, p.prec));
   size_t side_c = std::max(kmeans_ws_bytes(n, k1, k2, p.iters, p.prec), snap_ws_bytes(n, k1, k2, p.prec));
   side_r = std::max({side_r, kmeans_ws_bytes(m, k1, k2, 1, p.prec), threshold_ws_bytes(m)});
@@ -146,6 +151,14 @@ SketchWs carve_sketch(Carve& cv, const cabs_source& src, const cabs_params& p) {
   w.core = cv.take<char>(w.core_bytes);
   w.side_r = cv.take<char>(w.side_r_bytes);
   w.side_c = cv.take<char>(w.side_c_bytes);
+  w.lev_X = w.lev_Y = nullptr;
+  w.lev_one = w.lev_s = nullptr;
+  if (p.flags & CABS_FLAG_LEVERAGE) {
+    w.lev_X = cv.take<char>((size_t)m * k1 * eb);
+    w.lev_Y = cv.take<char>((size_t)n * k1 * eb);
+    w.lev_one = cv.take<double>(k1);
+    w.lev_s = cv.take<double>(k1);
+  }
   w.err_out2 = nullptr;
   w.err_ws = nullptr;
   w.err_bytes = 0;
@@ -169,10 +182,17 @@ __global__ void err_finalize_kernel(const double* out2, double* err) {
   if (threadIdx.x == 0) err[0] = out2[1] > 0.0 ? sqrt(out2[0] / out2[1]) : 0.0;
 }
 
+__global__ void fill_kernel(double* x, int n, double v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = v;
+}
+
 __global__ void diag_clear_kernel(cabs_diag* d) {
   int* p = (int*)d;
   for (size_t i = threadIdx.x; i < sizeof(cabs_diag) / sizeof(int); i += blockDim.x) p[i] = 0;
 }
+
+constexpr int kTagLevRows = 6;  // Philox tags of the leverage-score draws
+constexpr int kTagLevCols = 7;
 
 // The launch sequence of one sketch on one stream.
 cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
@@ -199,6 +219,16 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
     // step 3, hard-threshold variant (Section 5): largest-norm rows of P and Q
     CABS_TRY(launch_threshold(w.P, m, k1, k2, p.prec, out.rows, w.side_r, w.side_r_bytes, s));
     CABS_TRY(launch_threshold(w.Q, n, k1, k2, p.prec, out.cols, w.side_c, w.side_c_bytes, s));
+  } else if (p.flags & CABS_FLAG_LEVERAGE) {
+    // step 3, leverage-score variant (Section 5): P Q^T in SVD form
+    // (supplementary Section 3), its leverage scores as sampling probabilities
+    CABS_LAUNCH(s, "fill_kernel", fill_kernel<<<1, 256, 0, s>>>(w.lev_one, k1, 1.0));
+    CABS_TRY(launch_orthogonalize(m, n, k1, f64, p.trunc_rtol, w.P, w.lev_one, w.Q, w.lev_X, w.lev_s, w.lev_Y, nullptr,
+                                  &dg->status, w.core, w.core_bytes, s));
+    CABS_TRY(launch_leverage_select(w.lev_X, m, k1, k2, f64, p.seed, kTagLevRows, out.rows, w.side_r, w.side_r_bytes,
+                                    s));
+    CABS_TRY(launch_leverage_select(w.lev_Y, n, k1, k2, f64, p.seed, kTagLevCols, out.cols, w.side_c, w.side_c_bytes,
+                                    s));
   } else {
     // step 3: weighted k-means on P and Q, snap to rows
     CABS_TRY(launch_kmeans(w.P, m, k1, w.pr_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zr, dg->e_rows,
@@ -218,9 +248,18 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   }
   // steps 3-4: follow-up gather and sketching
   CABS_TRY(launch_gather(src, m, n, out.rows, k2, out.cols, k2, f64, w.C, w.Rt, w.W, s));
-  CABS_TRY(launch_core(m, n, k2, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, out.U, out.S, out.V,
-                       &dg->rank_final, &dg->sweeps_final, &dg->refine_final, &dg->status, nullptr, nullptr, nullptr, w.core,
+  const bool svd_form = (p.flags & CABS_FLAG_SVD_FORM) != 0;
+  // with the SVD form, the factors go to the (now free) embedding buffers first
+  void* U1 = svd_form ? w.P : out.U;
+  void* V1 = svd_form ? w.Q : out.V;
+  double* S1 = svd_form ? w.S_pilot : out.S;
+  CABS_TRY(launch_core(m, n, k2, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, U1, S1, V1, &dg->rank_final,
+                       &dg->sweeps_final, &dg->refine_final, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
+  // supplementary Section 3: orthogonalisation into SVD form
+  if (svd_form)
+    CABS_TRY(launch_orthogonalize(m, n, k2, f64, p.trunc_rtol, U1, S1, V1, out.U, out.S, out.V, &dg->rank_final,
+                                  &dg->status, w.core, w.core_bytes, s));
   // Section 5: relative Frobenius error of the result
   if (p.flags & CABS_FLAG_ERROR) {
     CABS_TRY(launch_error(src, m, n, k2, f64, p.prec, out.U, out.S, out.V, p.err_samples, p.err_seed, w.err_ws,
@@ -478,6 +517,73 @@ cabs_status cabs_threshold(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, i
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
   return launch_threshold(X, M, d, k2, prec, d_sorted, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+cabs_status cabs_orthogonalize_workspace_size(int64_t m, int64_t n, int32_t k, int32_t prec, size_t* bytes) {
+  clear_error();
+  CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
+  CABS_REQUIRE(m >= 1 && n >= 1 && k >= 1 && k <= CABS_MAX_K, "bad m, n, k");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
+  *bytes = orth_ws_bytes(m, n, k, prec == CABS_PREC_FP64);
+  return CABS_OK;
+}
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+cabs_status cabs_orthogonalize(cabs_ctx* ctx, int64_t m, int64_t n, int32_t k, int32_t prec, double trunc_rtol,
+                               const void* U, const double* S, const void* V, void* X, double* s, void* Y,
+                               int32_t* d_rank, void* ws, size_t ws_bytes, cabs_stream stream) {
+  clear_error();
+  CABS_REQUIRE(ctx != nullptr, "ctx is NULL");
+  CABS_REQUIRE(m >= 1 && n >= 1 && k >= 1 && k <= CABS_MAX_K, "bad m, n, k");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
+  CABS_REQUIRE(U && S && V && X && s && Y, "NULL input or output");
+  CABS_REQUIRE(std::isfinite(trunc_rtol) && trunc_rtol >= 0.0, "bad trunc_rtol");
+  const size_t e = prec == CABS_PREC_FP64 ? 8 : 4;
+  const size_t bu = (size_t)m * k * e, bv = (size_t)n * k * e;
+  CABS_REQUIRE(!overlaps(X, bu, U, bu) && !overlaps(X, bu, V, bv) && !overlaps(Y, bv, U, bu) &&
+                   !overlaps(Y, bv, V, bv) && !overlaps(X, bu, Y, bv),
+               "X and Y must not overlap U, V or each other");
+  CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
+  DeviceGuard g(ctx->device);
+  return launch_orthogonalize(m, n, k, prec == CABS_PREC_FP64, trunc_rtol, U, S, V, X, s, Y, d_rank, nullptr, ws,
+                              ws_bytes, (cudaStream_t)stream);
+}
+
+static cabs_status validate_cur(const cabs_source* src, const cabs_cur_params* p) {
+  CABS_REQUIRE(src != nullptr && p != nullptr, "NULL source or params");
+  CABS_REQUIRE(p->m >= 1 && p->n >= 1 && p->m < (int64_t)INT32_MAX && p->n < (int64_t)INT32_MAX, "bad m, n");
+  const int64_t mn = std::min<int64_t>({p->m, p->n, (int64_t)CABS_MAX_K});
+  CABS_REQUIRE(p->kb >= 1 && p->kb <= mn && p->kt >= 1 && p->kt <= mn, "kb = %d, kt = %d outside [1, min(m, n, %d)]",
+               p->kb, p->kt, CABS_MAX_K);
+  CABS_REQUIRE(p->prec >= CABS_PREC_FP64 && p->prec <= CABS_PREC_BF16, "unknown precision %d", p->prec);
+  CABS_REQUIRE(std::isfinite(p->trunc_rtol) && p->trunc_rtol >= 0.0, "trunc_rtol must be finite and >= 0");
+  return validate_source(src, p->m, p->n);
+}
+
+cabs_status cabs_sketch_cur_workspace_size(const cabs_source* src, const cabs_cur_params* p, size_t* bytes) {
+  clear_error();
+  CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
+  CABS_TRY(validate_cur(src, p));
+  *bytes = cur_ws_bytes(p->m, p->n, p->kb, p->kt, p->prec == CABS_PREC_FP64);
+  return CABS_OK;
+}
+
+cabs_status cabs_sketch_cur(cabs_ctx* ctx, const cabs_source* src, const cabs_cur_params* p, void* ws,
+                            size_t ws_bytes, cabs_stream stream, const cabs_cur_result* out) {
+  clear_error();
+  CABS_REQUIRE(ctx != nullptr, "ctx is NULL");
+  CABS_TRY(validate_cur(src, p));
+  CABS_REQUIRE(out && out->U && out->S && out->V && out->rows_b && out->cols_b && out->rows_t && out->cols_t,
+               "NULL output");
+  CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
+  DeviceGuard g(ctx->device);
+  return launch_sketch_cur(*src, p->m, p->n, p->kb, p->kt, p->seed, p->prec == CABS_PREC_FP64, p->trunc_rtol, out->U,
+                           out->S, out->V, out->Ustar, out->rows_b, out->cols_b, out->rows_t, out->cols_t, out->ranks,
+                           ws, ws_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

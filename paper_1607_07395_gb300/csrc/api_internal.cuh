@@ -29,6 +29,8 @@ struct SketchWs {
   cabs_diag* diag;
   void *core, *side_r, *side_c;
   size_t core_bytes, side_r_bytes, side_c_bytes;
+  void *lev_X, *lev_Y;      // CABS_FLAG_LEVERAGE: orthonormal pilot factors
+  double *lev_one, *lev_s;  //   ones (the S of P Q^T) and its singular values
   double* err_out2;  // CABS_FLAG_ERROR: (num, den) of the error
   void* err_ws;
   size_t err_bytes;

@@ -238,6 +238,24 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
 
 }  // namespace
 
+int extrap_row_blocks(int64_t M, bool elem_f64) {
+  return ceil_div(M, elem_f64 ? ExtrapTile<double>::BM : ExtrapTile<float>::BM);
+}
+
+cabs_status launch_extrap_gemm(const void* X, int64_t M, int K, const double* B, int N, bool elem_f64, void* out,
+                               double* part, const char* name, cudaStream_t stream) {
+  if (elem_f64) {
+    dim3 g(ceil_div(N, ExtrapTile<double>::BN), ceil_div(M, ExtrapTile<double>::BM));
+    CABS_LAUNCH(stream, name,
+                extrap_gemm_kernel<double><<<g, 256, 0, stream>>>((const double*)X, M, K, B, N, (double*)out, part));
+  } else {
+    dim3 g(ceil_div(N, ExtrapTile<float>::BN), ceil_div(M, ExtrapTile<float>::BM));
+    CABS_LAUNCH(stream, name,
+                extrap_gemm_kernel<float><<<g, 256, 0, stream>>>((const float*)X, M, K, B, N, (float*)out, part));
+  }
+  return CABS_OK;
+}
+
 size_t core_ws_bytes(int64_t m, int64_t n, int k, bool /*elem_f64*/) {
   Carve cv;
   carve_core(cv, m, n, k);

@@ -208,4 +208,17 @@ cabs_status launch_gather(const cabs_source& src, int64_t m, int64_t n, const in
   return gather_typed<float>(src, m, n, rows, kr, cols, kc, (float*)C, (float*)Rt, W, stream);
 }
 
+cabs_status launch_rows_of(const void* C, int64_t m, int kc, const int* rows, int kr, bool elem_f64, double* W,
+                           cudaStream_t stream) {
+  const int total = kr * kc;
+  if (total <= 0) return CABS_OK;
+  if (elem_f64)
+    CABS_LAUNCH(stream, "w_from_c_kernel",
+                w_from_c_kernel<double><<<ceil_div(total, 256), 256, 0, stream>>>((const double*)C, m, kc, rows, kr, W));
+  else
+    CABS_LAUNCH(stream, "w_from_c_kernel",
+                w_from_c_kernel<float><<<ceil_div(total, 256), 256, 0, stream>>>((const float*)C, m, kc, rows, kr, W));
+  return CABS_OK;
+}
+
 }  // namespace cabs

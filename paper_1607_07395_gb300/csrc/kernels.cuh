@@ -22,6 +22,27 @@ cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, do
                         int* d_rank, int* d_sweeps, int* d_refine, int* d_status, double* d_sig, double* d_Uw,
                         double* d_Vw, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+// out (M x N, elem) = X (M x K, elem) * B (K x N, FP64), with the FP64 sum of
+// squares of each output column over each block of rows in part
+// (extrap_row_blocks(M) x N).
+int extrap_row_blocks(int64_t M, bool elem_f64);
+cabs_status launch_extrap_gemm(const void* X, int64_t M, int K, const double* B, int N, bool elem_f64, void* out,
+                               double* part, const char* name, cudaStream_t stream);
+
+// k x k FP64 product C = diag(a) op(A) diag(d) op(B) diag(b) (a, b, d may be NULL).
+cabs_status launch_kk_gemm(int k, const double* A, bool transA, const double* d, const double* B, bool transB,
+                           const double* a, const double* b, double* C, cudaStream_t stream);
+
+// FP64 C (M x N) = op(A) diag(d) op(B) for small row-major operands.
+cabs_status launch_small_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* d,
+                              const double* B, int ldb, bool transB, double* C, int ldc, cudaStream_t stream);
+
+// Supplementary Section 3: U diag(S) V^T -> X diag(s) Y^T with orthonormal X, Y.
+size_t orth_ws_bytes(int64_t m, int64_t n, int k, bool elem_f64);
+cabs_status launch_orthogonalize(int64_t m, int64_t n, int k, bool elem_f64, double trunc_rtol, const void* U,
+                                 const double* S, const void* V, void* X, double* s, void* Y, int* d_rank,
+                                 int* d_status, void* ws, size_t ws_bytes, cudaStream_t stream);
+
 // a5: weighted k-means.
 size_t kmeans_ws_bytes(int64_t M, int d, int k2, int iters, int prec);
 cabs_status launch_kmeans(const void* X, int64_t M, int d, const int* init_rows, int k2, int iters, int prec,
@@ -40,6 +61,22 @@ cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, 
 size_t threshold_ws_bytes(int64_t M);
 cabs_status launch_threshold(const void* X, int64_t M, int d, int k2, int prec, int* sorted, void* ws,
                              size_t ws_bytes, cudaStream_t stream);
+// Section 5 follow-up variant (e): k2 distinct rows drawn with probabilities
+// proportional to the leverage scores |X_i|^2 of an orthonormal X (A-Res keys,
+// Philox key (seed, tag)), sorted. Workspace: threshold_ws_bytes(M).
+cabs_status launch_leverage_select(const void* X, int64_t M, int d, int k2, bool elem_f64, uint64_t seed, int tag,
+                                   int* sorted, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+// W[p][t] = C[rows[p]][t] (kr x kc, FP64) from C (m x kc, elem).
+cabs_status launch_rows_of(const void* C, int64_t m, int kc, const int* rows, int kr, bool elem_f64, double* W,
+                           cudaStream_t stream);
+
+// Section 2.2, Algorithm 1: Sketch-CUR.
+size_t cur_ws_bytes(int64_t m, int64_t n, int kb, int kt, bool elem_f64);
+cabs_status launch_sketch_cur(const cabs_source& src, int64_t m, int64_t n, int kb, int kt, uint64_t seed,
+                              bool elem_f64, double trunc_rtol, void* U, double* S, void* V, double* Ustar,
+                              int* rows_b, int* cols_b, int* rows_t, int* cols_t, int* ranks, void* ws,
+                              size_t ws_bytes, cudaStream_t stream);
 
 // a9: relative Frobenius error.
 size_t error_ws_bytes(const cabs_source& src, int64_t m, int64_t n, int k, int64_t samples, int prec);

@@ -11,7 +11,10 @@
 //    shared memories of its CTAs: each CTA owns two blocks of columns, rotates
 //    every pair across them (and, once per sweep, the pairs inside them), then
 //    the blocks move one step along the round-robin circle through distributed
-//    shared memory; one cluster barrier per round, double-buffered.
+//    shared memory; one cluster barrier per round, double-buffered. In the
+//    cross-block steps a warp keeps its top column in registers for the whole
+//    round, and the V columns receive each step's rotations one step later on
+//    otherwise idle warps, off the dependent chain of W rotations.
 //  Phase B (FP64, refinement): from U0, V0, iterate
 //      T = U^T W V,  R = I - U^T U,  S = I - V^T V,
 //      d_i = T_ii / (1 - (R_ii + S_ii) / 2),
@@ -19,7 +22,9 @@
 //        F_ij = (a d_j + b d_i) / (d_j^2 - d_i^2),  G_ij = (a d_i + b d_j) / (d_j^2 - d_i^2),
 //      F_ii = R_ii / 2, G_ii = S_ii / 2;  U <- U + U F,  V <- V + V G,
 //    which solves the first-order conditions U'^T U' = I, V'^T V' = I and
-//    U'^T W V' diagonal, and so converges quadratically. Every product is an
+//    U'^T W V' diagonal, and so converges quadratically. Before the first
+//    iteration the kept columns of U are recomputed in FP64 as W V / |W V|.
+//    Every product is an
 //    FP64 GEMM spread over all SMs. Pairs with d_i^2 ~ d_j^2 keep only the
 //    orthogonality correction. Iteration t's kernels exit at once if an
 //    earlier iteration already converged (a device-side flag; no host sync).
@@ -160,6 +165,79 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
   return true;
 }
 
+template <int R>
+__device__ __forceinline__ void load_col(const float* x, int lane, float* xr) {
+  const float4* x4 = (const float4*)(x + lane * R);
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) {
+    const float4 a = x4[i];
+    xr[4 * i] = a.x; xr[4 * i + 1] = a.y; xr[4 * i + 2] = a.z; xr[4 * i + 3] = a.w;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void store_col(float* x, int lane, const float* xr) {
+  float4* x4 = (float4*)(x + lane * R);
+#pragma unroll
+  for (int i = 0; i < R / 4; ++i) x4[i] = make_float4(xr[4 * i], xr[4 * i + 1], xr[4 * i + 2], xr[4 * i + 3]);
+}
+
+// The rotation of rotate_pair_reg with column x held in registers (xr) and
+// column y in shared memory; V is left alone and (c, s) is recorded in *cs
+// ((1, 0) when the pair is already orthogonal to the tolerance).
+template <int R>
+__device__ __forceinline__ bool rotate_top_reg(float* xr, float* y, int lane, float2* cs) {
+  float yr[R];
+  load_col<R>(y, lane, yr);
+  float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    a = fmaf(xr[i], xr[i], a);
+    b = fmaf(yr[i], yr[i], b);
+    g = fmaf(xr[i], yr[i], g);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    g += __shfl_xor_sync(0xffffffffu, g, off);
+  }
+  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) {
+    if (lane == 0) *cs = make_float2(1.f, 0.f);
+    return false;
+  }
+  const float zeta = (b - a) / (2.f * g);
+  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  const float c = rsqrtf(fmaf(t, t, 1.f));
+  const float s = c * t;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const float u = xr[i], v = yr[i];
+    xr[i] = c * u - s * v;
+    yr[i] = s * u + c * v;
+  }
+  store_col<R>(y, lane, yr);
+  if (lane == 0) *cs = make_float2(c, s);
+  return true;
+}
+
+// V columns (vx, vy) <- the rotation recorded for their W columns.
+template <int R>
+__device__ __forceinline__ void apply_rot_v(float* vx, float* vy, int lane, float2 cs) {
+  if (cs.y == 0.f) return;
+  float pr[R], qr[R];
+  load_col<R>(vx, lane, pr);
+  load_col<R>(vy, lane, qr);
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const float p = pr[i], q = qr[i];
+    pr[i] = cs.x * p - cs.y * q;
+    qr[i] = cs.y * p + cs.x * q;
+  }
+  store_col<R>(vx, lane, pr);
+  store_col<R>(vy, lane, qr);
+}
+
 // Writes U0 (normalised columns) and V0 in FP64, column-major k x k.
 __device__ __forceinline__ void emit_column(const float* w, const float* v, int k, int gc, int lane, double* U0,
                                             double* V0) {
@@ -219,6 +297,7 @@ __global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict
 // ------------------------------------------------------- Phase A, cluster
 
 constexpr int kClusterThreads = 512;
+constexpr int kMaxBlkRot = 16;  // columns per block (b) the cluster kernel supports
 
 // Cluster of NC CTAs; CTA c holds blocks top[c], bot[c] of b columns each.
 // Round-robin over the 2 NC blocks: block slot top[0] stays, the others move
@@ -238,6 +317,7 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   float* buf0 = cs;
   float* buf1 = cs + 4 * blk;
   __shared__ int rot_flag[2];
+  __shared__ float2 rot_cs[kMaxBlkRot][kMaxBlkRot];  // (c, s) of step s, pair j
   // CTA c starts with blocks c (top) and 2 NC - 1 - c (bottom). Block 0 stays;
   // the other 2 NC - 1 move one place around the circle per round, so after
   // the 2 NC - 1 rounds of a sweep every block is back where it started and
@@ -286,13 +366,28 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
           __syncthreads();
         }
       }
-      // every column of the top block against every column of the bottom block
-      for (int s = 0; s < b; ++s) {
-        for (int j = warp; j < b; j += nwarps) {
-          const int q = (j + s) % b;
-          my_rot |= rotate_pair_reg<R>(Wt + (size_t)j * kp, Wb + (size_t)q * kp, Vt + (size_t)j * kp,
-                                       Vb + (size_t)q * kp, lane);
+      // every column of the top block against every column of the bottom block:
+      // in step s warp j rotates W columns (top j, bottom (j + s) % b), keeping
+      // top column j in registers for the whole round, and records (c, s); the
+      // same rotation reaches the V columns one step later on another warp
+      // (or the same warp when there are no spare warps), off the critical path
+      {
+        const bool spare = 2 * b <= nwarps;
+        float xr[R];
+        if (warp < b) load_col<R>(Wt + (size_t)warp * kp, lane, xr);
+        for (int s = 0; s <= b; ++s) {
+          if (warp < b && s < b) {
+            const int q = (warp + s) % b;
+            my_rot |= rotate_top_reg<R>(xr, Wb + (size_t)q * kp, lane, &rot_cs[s][warp]);
+          }
+          const int vw = spare ? warp - b : warp;
+          if (s >= 1 && vw >= 0 && vw < b) {
+            const int q = (vw + s - 1) % b;
+            apply_rot_v<R>(Vt + (size_t)vw * kp, Vb + (size_t)q * kp, lane, rot_cs[s - 1][vw]);
+          }
+          __syncthreads();
         }
+        if (warp < b) store_col<R>(Wt + (size_t)warp * kp, lane, xr);
         __syncthreads();
       }
       // move blocks one step around the circle (into the destinations' next buffers)
@@ -480,21 +575,80 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     const double* V = (t & 1) ? a.V1 : a.V0;
     double* Un = (t & 1) ? a.U0 : a.U1;
     double* Vn = (t & 1) ? a.V0 : a.V1;
-    // P = W V, and (independent of it) the Gram matrices U^T U, V^T V by
-    // their upper triangles; then T = U^T P
-    for (int x = blockIdx.x; x < tiles + 2 * tri; x += nb) {
-      if (x < tiles) {
-        gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
-      } else {
-        const int y = x - tiles, which = y / tri;
-        int ti, tj;
-        tri_of(y - which * tri, nt, ti, tj);
-        gram_tile(k, ti, tj, which == 0 ? U : V, which == 0 ? a.UtU : a.VtV, As, Bs);
+    if (t == 0) {
+      // First iteration: P = W V and V^T V; then every column of P above the
+      // FP32 phase's noise level (2^-18 of the largest) replaces the FP32
+      // column of U (U_j = P_j / |P_j|), so that the kept columns span the
+      // range of W to FP64 accuracy. U + U F only mixes existing columns, so
+      // it could not leave an FP32-accurate span where W has exactly zero
+      // columns (nothing else supplies the missing directions). Columns at
+      // the noise level keep their FP32 directions. Then U^T U and T = U^T P.
+      for (int x = blockIdx.x; x < tiles + tri; x += nb) {
+        if (x < tiles) {
+          gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
+        } else {
+          int ti, tj;
+          tri_of(x - tiles, nt, ti, tj);
+          gram_tile(k, ti, tj, V, a.VtV, As, Bs);
+        }
       }
+      if (!grid_sync(a.bar, nb)) return;
+      for (int j = blockIdx.x; j < k; j += nb) {
+        double s2 = 0.0;
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+          const double v = a.P[(size_t)j * k + i];
+          s2 = fma(v, v, s2);
+        }
+        s2 = warp_sum(s2);
+        if ((threadIdx.x & 31) == 0) dsh[threadIdx.x >> 5] = s2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double tot = 0.0;
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += dsh[w];
+          a.d[j] = sqrt(tot);
+        }
+        __syncthreads();
+      }
+      if (!grid_sync(a.bar, nb)) return;
+      {
+        double mx = 0.0;
+        for (int j = 0; j < k; ++j) mx = fmax(mx, a.d[j]);
+        double* Uw = const_cast<double*>(U);
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
+             e += (long long)nb * blockDim.x) {
+          const int j = (int)(e / k);
+          const double nj = a.d[j];
+          if (nj > 3.814697265625e-06 * mx) Uw[e] = a.P[e] / nj;
+        }
+      }
+      if (!grid_sync(a.bar, nb)) return;
+      for (int x = blockIdx.x; x < tiles + tri; x += nb) {
+        if (x < tiles) {
+          gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
+        } else {
+          int ti, tj;
+          tri_of(x - tiles, nt, ti, tj);
+          gram_tile(k, ti, tj, U, a.UtU, As, Bs);
+        }
+      }
+      if (!grid_sync(a.bar, nb)) return;
+    } else {
+      // P = W V, and (independent of it) the Gram matrices U^T U, V^T V by
+      // their upper triangles; then T = U^T P
+      for (int x = blockIdx.x; x < tiles + 2 * tri; x += nb) {
+        if (x < tiles) {
+          gemm_tile(k, x % nt, x / nt, a.W, 1, V, nullptr, a.P, As, Bs);
+        } else {
+          const int y = x - tiles, which = y / tri;
+          int ti, tj;
+          tri_of(y - which * tri, nt, ti, tj);
+          gram_tile(k, ti, tj, which == 0 ? U : V, which == 0 ? a.UtU : a.VtV, As, Bs);
+        }
+      }
+      if (!grid_sync(a.bar, nb)) return;
+      for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
+      if (!grid_sync(a.bar, nb)) return;
     }
-    if (!grid_sync(a.bar, nb)) return;
-    for (int x = blockIdx.x; x < tiles; x += nb) gemm_tile(k, x % nt, x / nt, U, 1, a.P, nullptr, a.T, As, Bs);
-    if (!grid_sync(a.bar, nb)) return;
     // coefficients F, G and singular value estimates d
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
       const size_t ii = (size_t)i * k + i;
@@ -833,6 +987,10 @@ static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0
     }
   }
   const int b = (k + 2 * nc - 1) / (2 * nc);
+  if (b > kMaxBlkRot) {
+    set_error("svd: %d columns per block exceed %d (k = %d on a %d-CTA cluster)", b, kMaxBlkRot, k, nc);
+    return CABS_EINVAL;
+  }
   const size_t smem = smem_for(nc);
   cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(svd32_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,6 +10,13 @@
 //     x 32 dimensions through shared memory so the loads are coalesced while
 //     each lane sums one row. Non-negative floats order like their bit
 //     patterns, so the bits are the selection keys.
+//  Leverage-score variant (Section 5, follow-up variant (e)): lev_keys_kernel
+//     takes the leverage score l_i = |X_i|^2 of each row of an orthonormal
+//     factor X (FP64 sum) and the A-Res key of Efraimidis and Spirakis (2006),
+//     u_i^(1/l_i), ranked through the increasing map l_i / (-ln u_i) in FP64,
+//     with u_i = ((r_i >> 11) + 1/2) 2^-53 and r_i = word 0 of
+//     Philox((i, 0, 0, 0), (seed, tag)); the k2 largest keys are a draw of k2
+//     distinct rows with probabilities proportional to l.
 //  2. select_topk_kernel (one CTA): a radix select finds the k2-th largest
 //     key T, 8 bits at a time with warp-aggregated shared-memory histograms;
 //     then one pass in index order keeps every row with key > T and the
@@ -65,6 +72,38 @@ __global__ void __launch_bounds__(kNormThreads) sq_norms_kernel(const T* __restr
       __syncwarp();
     }
     if (r0 + lane < M) key[r0 + lane] = key_bits<T>(s);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNormThreads) lev_keys_kernel(const T* __restrict__ X, long long M, int d,
+                                                                uint64_t seed, int tag,
+                                                                unsigned long long* __restrict__ key) {
+  __shared__ T tile[kNormThreads / 32][32][33];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long r0 = ((long long)blockIdx.x * (blockDim.x >> 5) + wi) * 32; r0 < M; r0 += nwarps * 32) {
+    double s = 0.0;
+    for (int q0 = 0; q0 < d; q0 += 32) {
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const long long l = r0 + r;
+        tile[wi][r][lane] = (l < M && q0 + lane < d) ? X[l * d + q0 + lane] : T(0);
+      }
+      __syncwarp();
+      const int qn = min(32, d - q0);
+      for (int q = 0; q < qn; ++q) {
+        const double x = (double)tile[wi][lane][q];
+        s = fma(x, x, s);
+      }
+      __syncwarp();
+    }
+    const long long i = r0 + lane;
+    if (i < M) {
+      const uint64_t r = philox4x64_10((uint64_t)i, 0, 0, 0, seed, (uint64_t)tag).v[0];
+      const double u = ((double)(r >> 11) + 0.5) * 1.1102230246251565e-16;  // 2^-53
+      key[i] = (unsigned long long)__double_as_longlong(s / -log(u));
+    }
   }
 }
 
@@ -177,7 +216,29 @@ cabs_status threshold_typed(const T* X, int64_t M, int d, int k2, int* sorted, v
   return CABS_OK;
 }
 
+template <typename T>
+cabs_status leverage_typed(const T* X, int64_t M, int d, int k2, uint64_t seed, int tag, int* sorted, void* ws,
+                           size_t ws_bytes, cudaStream_t stream) {
+  if (ws_bytes < (size_t)M * sizeof(unsigned long long)) {
+    set_error("leverage workspace too small: need %zu bytes, got %zu", (size_t)M * 8, ws_bytes);
+    return CABS_ENOMEM;
+  }
+  unsigned long long* key = (unsigned long long*)ws;
+  const int blocks = std::max(1, std::min(ceil_div(M, kNormThreads), sm_count() * 8));
+  CABS_LAUNCH(stream, "lev_keys_kernel",
+              lev_keys_kernel<T><<<blocks, kNormThreads, 0, stream>>>(X, M, d, seed, tag, key));
+  CABS_LAUNCH(stream, "select_topk_kernel",
+              select_topk_kernel<<<1, kSelThreads, 0, stream>>>(key, M, k2, 56, sorted));
+  return CABS_OK;
+}
+
 }  // namespace
+
+cabs_status launch_leverage_select(const void* X, int64_t M, int d, int k2, bool elem_f64, uint64_t seed, int tag,
+                                   int* sorted, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (elem_f64) return leverage_typed<double>((const double*)X, M, d, k2, seed, tag, sorted, ws, ws_bytes, stream);
+  return leverage_typed<float>((const float*)X, M, d, k2, seed, tag, sorted, ws, ws_bytes, stream);
+}
 
 size_t threshold_ws_bytes(int64_t M) { return align256((size_t)M * sizeof(unsigned long long)); }
 

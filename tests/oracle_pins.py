@@ -352,11 +352,12 @@ def pin_orthogonalize(orth_fn, m=60, n=45, r=6, seed=13):
 
 def pin_pinv_trunc(pinv_fn):
     """Closed form on a matrix with known singular values: 5 x 3,
-    s = (1, 1e-3, 1e-15); the floor 5 x 2^-52 = 1.1e-15 drops the third."""
+    s = (1, 1e-3, 3e-8); the floor sqrt(5 x 2^-52) = 3.33e-8 drops the third
+    (sqrt(3 x 2^-52) = 2.58e-8 would keep it)."""
     g = np.random.default_rng(3)
     Q1, _ = np.linalg.qr(g.standard_normal((5, 3)))
     Q2, _ = np.linalg.qr(g.standard_normal((3, 3)))
-    s = np.array([1.0, 1e-3, 1e-15])
+    s = np.array([1.0, 1e-3, 3e-8])
     B = (Q1 * s) @ Q2.T
     want = (Q2[:, :2] / s[:2]) @ Q1[:, :2].T
     assert np.allclose(pinv_fn(B), want, rtol=0, atol=1e-9)
@@ -410,6 +411,62 @@ def pin_br_cur(br_cur_fn, source_cls):
     M = B[np.ix_(rt4, ct4)]
     grad = Cbar.T @ (M - Cbar @ r4.U @ Rbar) @ Rbar.T
     assert np.abs(grad).max() < 1e-9 * np.abs(M).max() * np.abs(Cbar).max() * np.abs(Rbar).max()
+
+
+# ------------------------------------------------------ leverage-score follow-up
+
+def pin_leverage_scores(lev_fn, orth_fn):
+    """Leverage scores of the pilot form P Q^T through its SVD form equal the
+    diagonal of the hat matrix P (P^T P)^-1 P^T (an LU solve, independent of
+    any SVD) for full-rank factors, and sum to the rank."""
+    g = np.random.default_rng(21)
+    P = g.standard_normal((80, 6))
+    Q = g.standard_normal((50, 6))
+    X, _, Y = orth_fn(P, np.ones(6), Q)
+    hat = np.einsum("ij,ji->i", P, np.linalg.solve(P.T @ P, P.T))
+    assert np.allclose(lev_fn(X), hat, atol=1e-12)
+    hat_q = np.einsum("ij,ji->i", Q, np.linalg.solve(Q.T @ Q, Q.T))
+    assert np.allclose(lev_fn(Y), hat_q, atol=1e-12)
+    assert abs(lev_fn(X).sum() - 6) < 1e-12
+
+
+def pin_weighted_sample(ws_fn):
+    """A-Res sampling: (1) k = N selects everything; (2) zero weights are
+    never drawn while positive ones remain; (3) over 4000 seeds the inclusion
+    frequency of each index for k = 2 matches the closed form of successive
+    weighted draws without replacement, P(i in S) = p_i + sum_{j != i} p_j
+    p_i / (1 - p_j), within 4.5 standard errors; (4) equal weights reduce to
+    the k smallest -ln u, i.e. the k largest u."""
+    w = np.array([5.0, 1.0, 0.0, 2.0, 2.0])
+    assert ws_fn(w, 5, 1, 6)[0].tolist() == [0, 1, 2, 3, 4]
+    for seed in range(50):
+        sel = ws_fn(w, 4, seed, 6)[0].tolist()
+        assert 2 not in sel and sorted(sel) == sel and len(set(sel)) == 4
+    p = w / w.sum()
+    want = np.array([p[i] + sum(p[j] * p[i] / (1 - p[j]) for j in range(5) if j != i) for i in range(5)])
+    T = 4000
+    cnt = np.zeros(5)
+    for seed in range(T):
+        cnt[ws_fn(w, 2, seed, 7)[0]] += 1
+    freq = cnt / T
+    se = np.sqrt(np.maximum(want * (1 - want), 1e-12) / T)
+    assert np.all(np.abs(freq - want) <= 4.5 * se + 1e-12), (freq, want)
+    u = philox_uniform_for_pin(11, 6, 9)
+    assert ws_fn(np.ones(9), 3, 11, 6)[0].tolist() == sorted(np.argsort(-u, kind="stable")[:3].tolist())
+
+
+def philox_uniform_for_pin(seed, tag, N):
+    """Uniforms from numpy's own Philox4x64-10 (an independent implementation
+    of the generator; it increments its counter before each block): word 0 of
+    block (i, 0, 0, 0), mapped to ((r >> 11) + 1/2) 2^-53."""
+    out = []
+    for i in range(N):
+        c = (i - 1) % (1 << 256)
+        start = np.array([(c >> (64 * t)) & (2**64 - 1) for t in range(4)], dtype=np.uint64)
+        bg = np.random.Philox(key=np.array([seed, tag], dtype=np.uint64), counter=start)
+        r = int(bg.random_raw(4)[0])
+        out.append(((r >> 11) + 0.5) * 2.0 ** -53)
+    return np.array(out)
 
 
 # ---------------------------------------------------------------------- error

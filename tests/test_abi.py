@@ -49,6 +49,9 @@ def test_struct_layout_matches_c():
 int main(void) {
   printf("cabs_source %zu\ncabs_params %zu\ncabs_diag %zu\ncabs_result %zu\n", sizeof(cabs_source),
          sizeof(cabs_params), sizeof(cabs_diag), sizeof(cabs_result));
+  printf("cabs_cur_params %zu\ncabs_cur_result %zu\n", sizeof(cabs_cur_params), sizeof(cabs_cur_result));
+  F(cabs_cur_params, kt) F(cabs_cur_params, seed) F(cabs_cur_params, prec) F(cabs_cur_params, trunc_rtol)
+  F(cabs_cur_result, Ustar) F(cabs_cur_result, rows_t) F(cabs_cur_result, ranks)
   F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma)
   F(cabs_params, seed) F(cabs_params, upsilon_pow) F(cabs_params, trunc_rtol) F(cabs_params, flags)
   F(cabs_params, err_samples) F(cabs_params, err_seed)
@@ -63,7 +66,8 @@ int main(void) {
         lines = dict(ln.rsplit(" ", 1) for ln in subprocess.run([exe], capture_output=True, text=True,
                                                                 check=True).stdout.split("\n") if ln)
     for name, cls in [("cabs_source", cabs.cabs_source), ("cabs_params", cabs.cabs_params),
-                      ("cabs_diag", cabs.cabs_diag), ("cabs_result", cabs.cabs_result)]:
+                      ("cabs_diag", cabs.cabs_diag), ("cabs_result", cabs.cabs_result),
+                      ("cabs_cur_params", cabs.cabs_cur_params), ("cabs_cur_result", cabs.cabs_cur_result)]:
         assert int(lines[name]) == C.sizeof(cls), name
     for key, val in lines.items():
         if "." in key:
@@ -112,8 +116,14 @@ def test_error_request_on_host(L):
     assert n1.value >= n0.value + e.value - 256
     ps = cabs.make_params(2000, 1500, 20, prec="fp32", err_samples=10 ** 6)
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(ps), C.byref(n2)) == cabs.CABS_OK
-    bad = cabs.make_params(2000, 1500, 20, flags=16)  # no such flag
+    bad = cabs.make_params(2000, 1500, 20, flags=32)  # no such flag
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(bad), C.byref(n0)) == cabs.CABS_EINVAL
+    both = cabs.make_params(2000, 1500, 20, flags=cabs.FLAG_HARD_THRESHOLD | cabs.FLAG_LEVERAGE)
+    assert L.cabs_workspace_size(C.byref(_src()), C.byref(both), C.byref(n0)) == cabs.CABS_EINVAL
+    for fl in (cabs.FLAG_LEVERAGE, cabs.FLAG_SVD_FORM):
+        assert L.cabs_workspace_size(C.byref(_src()), C.byref(cabs.make_params(2000, 1500, 20, flags=fl)),
+                                     C.byref(n2)) == cabs.CABS_OK
+        assert n2.value > n0.value
     neg = cabs.make_params(2000, 1500, 20, err_samples=0)
     neg.err_samples = -1
     assert L.cabs_workspace_size(C.byref(_src()), C.byref(neg), C.byref(n0)) == cabs.CABS_EINVAL

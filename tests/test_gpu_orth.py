@@ -52,14 +52,17 @@ def check(U, S, V, X, s, Y, r, prec, trunc_rtol=0.0):
     assert np.allclose(sr, so, rtol=tol, atol=tol * so[0])
     assert np.abs(Xr.T @ Xr - np.eye(r)).max() < tol
     assert np.abs(Yr.T @ Yr - np.eye(r)).max() < tol
-    A = (U * S) @ V.T
-    assert np.abs((Xr * sr) @ Yr.T - A).max() < tol * so[0]
+    # the oracle's (possibly truncated) product; without truncation also the input product
+    got = (Xr * sr) @ Yr.T
+    assert np.abs(got - (Xo * so) @ Yo.T).max() < tol * so[0]
+    if trunc_rtol == 0.0:
+        assert np.abs(got - (U * S) @ V.T).max() < tol * so[0]
     # singular vectors: angle to the oracle's at most |error of the product| / gap
     # (Wedin), with the product's bound tol s_1 and the absolute gap to the
     # neighbouring values
     gap = np.minimum(np.r_[np.inf, so[:-1] - so[1:]], np.r_[so[:-1] - so[1:], np.inf])
     for i in range(r):
-        bound = 10 * tol * so[0] / gap[i]
+        bound = 10 * tol * so[0] / min(gap[i], so[0])
         if bound > 0.1:
             continue
         for F, Fo in ((Xr, Xo), (Yr, Yo)):

@@ -150,7 +150,10 @@ CUR_MUTANTS = [
 ]
 
 PINV_MUTANTS = [
-    ("keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]", "keep = sb > max(trunc_rtol, min(B.shape) * EPS64) * sb[0]"),
+    ("keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]",
+     "keep = sb > max(trunc_rtol, math.sqrt(min(B.shape) * EPS64)) * sb[0]"),
+    ("keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]",
+     "keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]"),
     ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep].T * sb[keep]) @ Ub[:, keep].T"),
     ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep] / sb[keep][:, None]).T @ Ub[:, keep].T[::-1]"),
 ]
@@ -166,3 +169,28 @@ def test_br_cur_mutants_rejected(old, new):
 def test_pinv_mutants_rejected(old, new):
     bad = mutate(o.pinv_trunc, old, new)
     assert rejects(lambda: pins.pin_pinv_trunc(bad))
+
+
+WS_MUTANTS = [
+    ("keys = w / -np.log(u)", "keys = w * -np.log(u)"),                  # inverted key map
+    ("keys = w / -np.log(u)", "keys = w / -np.log(1 - u)"),              # other uniform
+    ("order = np.lexsort((np.arange(N), -keys))", "order = np.lexsort((np.arange(N), keys))"),  # smallest keys
+]
+
+
+@pytest.mark.parametrize("old,new", WS_MUTANTS)
+def test_weighted_sample_mutants_rejected(old, new):
+    bad = mutate(o.weighted_sample, old, new)
+    assert rejects(lambda: pins.pin_weighted_sample(bad))
+
+
+LEV_MUTANTS = [
+    ("return (X * X).sum(axis=1)", "return np.abs(X).sum(axis=1)"),
+    ("return (X * X).sum(axis=1)", "return (X * X).sum(axis=0)"),
+]
+
+
+@pytest.mark.parametrize("old,new", LEV_MUTANTS)
+def test_leverage_mutants_rejected(old, new):
+    bad = mutate(o.leverage_scores, old, new)
+    assert rejects(lambda: pins.pin_leverage_scores(bad, o.orthogonalize))

@@ -169,3 +169,29 @@ def test_sketch_cur_draws():
         assert idx.min() >= 0 and idx.max() < N
     assert not np.array_equal(r.rows_b, r.rows_t[:5])
     assert np.allclose(r.C @ r.U @ r.Rt.T, A, atol=1e-9 * np.abs(A).max())
+
+
+def test_leverage_scores():
+    pins.pin_leverage_scores(o.leverage_scores, o.orthogonalize)
+
+
+def test_weighted_sample():
+    pins.pin_weighted_sample(o.weighted_sample)
+
+
+def test_philox_uniform_matches_numpy():
+    assert np.array_equal(o.philox_uniform(11, 6, 9), pins.philox_uniform_for_pin(11, 6, 9))
+
+
+def test_leverage_follow_up_sketch():
+    """Section 5 variant (e) end to end on an exactly rank-3 matrix whose
+    rows 0..99 are zero: those rows have leverage 0 and are never drawn, the
+    indices are distinct and sorted, and the follow-up sketch recovers A."""
+    from workloads import synth
+    A = synth.exact_lowrank_int(400, 300, 3, seed=2)
+    A[:100] = 0.0
+    r = o.cabs(o.DenseSource(A), 12, 6, seed=5, follow="leverage")
+    assert r.rows.min() >= 100 and len(set(r.rows.tolist())) == 6 and np.all(np.diff(r.rows) > 0)
+    assert len(set(r.cols.tolist())) == 6 and np.all(np.diff(r.cols) > 0)
+    F = r.final
+    assert np.allclose((F.U * F.S) @ F.V.T, A, atol=1e-8 * np.abs(A).max())
