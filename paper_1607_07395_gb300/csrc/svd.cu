@@ -45,7 +45,10 @@ namespace cabs {
 namespace {
 
 constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
-constexpr float kTolA = 1e-5f;          // Phase A rotation threshold |g| > tol sqrt(a b)
+#ifndef CABS_SVD_TOL_A
+#define CABS_SVD_TOL_A 1e-5f
+#endif
+constexpr float kTolA = CABS_SVD_TOL_A;  // Phase A rotation threshold |g| > tol sqrt(a b)
 constexpr int kMaxSweepsA = 40;
 constexpr int kItersB = 6;
 constexpr double kConvB = 1e-8;         // Phase B: last iteration when max |F_ij|, |G_ij| (i != j) < this
@@ -66,6 +69,30 @@ __device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& 
   }
 }
 
+// The Hestenes rotation that makes two columns with squared norms a, b and
+// inner product g orthogonal: zeta = (b - a) / 2g,
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
+// Returns false (no rotation) unless |g| > tol sqrt(a b), tested as
+// g^2 > tol^2 a b. Phase A needs only approximate rotations -- c and s form
+// an exact rotation for any t, and the FP64 refinement finishes the job -- so
+// the divisions and square roots are the fast hardware approximations,
+// which shortens the dependent chain of every rotation step.
+__device__ __forceinline__ bool jacobi_cs(float a, float b, float g, float& c, float& s) {
+  if (!(g * g > kTolA * kTolA * a * b)) return false;
+  const float zeta = __fdividef(b - a, 2.f * g);
+  const float az = fabsf(zeta);
+  float t;
+  if (az > 1e18f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    t = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+  }
+  c = rsqrtf(fmaf(t, t, 1.f));
+  s = c * t;
+  return true;
+}
+
 // Rotates columns x, y (length k, lane-strided) so that they become
 // orthogonal; returns true if a rotation was applied. x, y, vx, vy may live
 // in shared or distributed shared memory.
@@ -80,11 +107,8 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
   a = warp_sum(a);
   b = warp_sum(b);
   g = warp_sum(g);
-  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) return false;
-  const float zeta = (b - a) / (2.f * g);
-  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-  const float c = rsqrtf(fmaf(t, t, 1.f));
-  const float s = c * t;
+  float c, s;
+  if (!jacobi_cs(a, b, g, c, s)) return false;
   for (int i = lane; i < k; i += 32) {
     const float u = x[i], v = y[i];
     x[i] = c * u - s * v;
@@ -96,28 +120,30 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
   return true;
 }
 
-// Same rotation with each lane owning R contiguous rows of a column padded to
-// 32 R entries (R a multiple of 4): the two columns are read once with
-// 16-byte loads, rotated in registers and written back once.
+// Same rotation with each lane owning R rows of a column padded to 32 R
+// entries (R a multiple of 4), as R / 4 float4 groups interleaved across the
+// lanes (group i of lane l at float4 index l + 32 i, so a warp's 16-byte
+// accesses are consecutive and free of bank conflicts): the two columns are
+// read once, rotated in registers and written back once.
 template <int R>
 __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, float* vy, int lane) {
   float xr[R], yr[R];
-  const float4* x4 = (const float4*)(x + lane * R);
-  const float4* y4 = (const float4*)(y + lane * R);
+  const float4* x4 = (const float4*)x;
+  const float4* y4 = (const float4*)y;
   // the V columns are read up front, so their latency hides behind the reductions
   float4 pv[R / 4], qv[R / 4];
-  const float4* vx4 = (const float4*)(vx + lane * R);
-  const float4* vy4 = (const float4*)(vy + lane * R);
+  const float4* vx4 = (const float4*)vx;
+  const float4* vy4 = (const float4*)vy;
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
-    const float4 a = x4[i], b = y4[i];
+    const float4 a = x4[lane + 32 * i], b = y4[lane + 32 * i];
     xr[4 * i] = a.x; xr[4 * i + 1] = a.y; xr[4 * i + 2] = a.z; xr[4 * i + 3] = a.w;
     yr[4 * i] = b.x; yr[4 * i + 1] = b.y; yr[4 * i + 2] = b.z; yr[4 * i + 3] = b.w;
   }
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
-    pv[i] = vx4[i];
-    qv[i] = vy4[i];
+    pv[i] = vx4[lane + 32 * i];
+    qv[i] = vy4[lane + 32 * i];
   }
   float a = 0.f, b = 0.f, g = 0.f;
 #pragma unroll
@@ -132,13 +158,10 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
     b += __shfl_xor_sync(0xffffffffu, b, off);
     g += __shfl_xor_sync(0xffffffffu, g, off);
   }
-  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) return false;
-  const float zeta = (b - a) / (2.f * g);
-  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-  const float c = rsqrtf(fmaf(t, t, 1.f));
-  const float s = c * t;
-  float4* xo = (float4*)(x + lane * R);
-  float4* yo = (float4*)(y + lane * R);
+  float c, s;
+  if (!jacobi_cs(a, b, g, c, s)) return false;
+  float4* xo = (float4*)x;
+  float4* yo = (float4*)y;
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
     float4 p, q;
@@ -146,11 +169,11 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
     p.y = c * xr[4 * i + 1] - s * yr[4 * i + 1]; q.y = s * xr[4 * i + 1] + c * yr[4 * i + 1];
     p.z = c * xr[4 * i + 2] - s * yr[4 * i + 2]; q.z = s * xr[4 * i + 2] + c * yr[4 * i + 2];
     p.w = c * xr[4 * i + 3] - s * yr[4 * i + 3]; q.w = s * xr[4 * i + 3] + c * yr[4 * i + 3];
-    xo[i] = p;
-    yo[i] = q;
+    xo[lane + 32 * i] = p;
+    yo[lane + 32 * i] = q;
   }
-  float4* vxo = (float4*)(vx + lane * R);
-  float4* vyo = (float4*)(vy + lane * R);
+  float4* vxo = (float4*)vx;
+  float4* vyo = (float4*)vy;
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
     const float4 p = pv[i], q = qv[i];
@@ -159,27 +182,27 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
     p2.y = c * p.y - s * q.y; q2.y = s * p.y + c * q.y;
     p2.z = c * p.z - s * q.z; q2.z = s * p.z + c * q.z;
     p2.w = c * p.w - s * q.w; q2.w = s * p.w + c * q.w;
-    vxo[i] = p2;
-    vyo[i] = q2;
+    vxo[lane + 32 * i] = p2;
+    vyo[lane + 32 * i] = q2;
   }
   return true;
 }
 
 template <int R>
 __device__ __forceinline__ void load_col(const float* x, int lane, float* xr) {
-  const float4* x4 = (const float4*)(x + lane * R);
+  const float4* x4 = (const float4*)x;
 #pragma unroll
   for (int i = 0; i < R / 4; ++i) {
-    const float4 a = x4[i];
+    const float4 a = x4[lane + 32 * i];
     xr[4 * i] = a.x; xr[4 * i + 1] = a.y; xr[4 * i + 2] = a.z; xr[4 * i + 3] = a.w;
   }
 }
 
 template <int R>
 __device__ __forceinline__ void store_col(float* x, int lane, const float* xr) {
-  float4* x4 = (float4*)(x + lane * R);
+  float4* x4 = (float4*)x;
 #pragma unroll
-  for (int i = 0; i < R / 4; ++i) x4[i] = make_float4(xr[4 * i], xr[4 * i + 1], xr[4 * i + 2], xr[4 * i + 3]);
+  for (int i = 0; i < R / 4; ++i) x4[lane + 32 * i] = make_float4(xr[4 * i], xr[4 * i + 1], xr[4 * i + 2], xr[4 * i + 3]);
 }
 
 // The rotation of rotate_pair_reg with column x held in registers (xr) and
@@ -202,14 +225,11 @@ __device__ __forceinline__ bool rotate_top_reg(float* xr, float* y, int lane, fl
     b += __shfl_xor_sync(0xffffffffu, b, off);
     g += __shfl_xor_sync(0xffffffffu, g, off);
   }
-  if (!(fabsf(g) > kTolA * sqrtf(a) * sqrtf(b))) {
+  float c, s;
+  if (!jacobi_cs(a, b, g, c, s)) {
     if (lane == 0) *cs = make_float2(1.f, 0.f);
     return false;
   }
-  const float zeta = (b - a) / (2.f * g);
-  const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-  const float c = rsqrtf(fmaf(t, t, 1.f));
-  const float s = c * t;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const float u = xr[i], v = yr[i];
@@ -715,16 +735,14 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
   }
 }
 
-// Sort, sign-fix, truncate, and write sig (desc), Uw, Vw (row-major, column r
-// = r-th singular vector). Runs unless the FP64 Jacobi fallback is needed.
-__global__ void __launch_bounds__(256) refine_final_kernel(int k, double trunc_rtol, const double* __restrict__ Ubuf0,
-                                                           const double* __restrict__ Ubuf1,
-                                                           const double* __restrict__ Vbuf0,
-                                                           const double* __restrict__ Vbuf1, const double* __restrict__ d,
-                                                           const int* __restrict__ done_iter, int iters,
-                                                           double* __restrict__ sig_out, double* __restrict__ Uw_out,
-                                                           double* __restrict__ Vw_out, int* rank_out, int* refine_out,
-                                                           int* status, const GridBarrier* __restrict__ bar) {
+// Sort and truncate: the position of every singular value in descending
+// order (ties to the lower index), the kept rank and sig (desc). One CTA.
+// Runs unless the FP64 Jacobi fallback is needed.
+__global__ void __launch_bounds__(256) refine_sort_kernel(int k, double trunc_rtol, const double* __restrict__ d,
+                                                          const int* __restrict__ done_iter, double* __restrict__ sig_out,
+                                                          int* __restrict__ pos_out, int* __restrict__ rank_tmp,
+                                                          int* rank_out, int* refine_out, int* status,
+                                                          const GridBarrier* __restrict__ bar) {
   const int done = *done_iter;
   if (threadIdx.x == 0 && status && bar->err) atomicOr(status, 4);
   if (threadIdx.x == 0 && refine_out) *refine_out = done == kNotDone ? -1 : done + 1;
@@ -732,20 +750,15 @@ __global__ void __launch_bounds__(256) refine_final_kernel(int k, double trunc_r
     if (threadIdx.x == 0 && status) atomicOr(status, 2);
     return;  // the FP64 Jacobi fallback writes the outputs
   }
-  const int last = done;  // U, V after iteration `done` live in buffer (done + 1) % 2
-  const double* U = ((last + 1) & 1) ? Ubuf1 : Ubuf0;
-  const double* V = ((last + 1) & 1) ? Vbuf1 : Vbuf0;
   __shared__ double sg[CABS_MAX_K];
-  __shared__ int pos[CABS_MAX_K];
-  __shared__ int rank_s;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = fabs(d[i]);
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     int r = 0;
     for (int i = 0; i < k; ++i) r += (sg[i] > sg[j]) || (sg[i] == sg[j] && i < j);
-    pos[j] = r;
+    pos_out[j] = r;
+    sig_out[r] = sg[j];
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
     double smax = 0.0;
     for (int j = 0; j < k; ++j) smax = fmax(smax, sg[j]);
@@ -754,14 +767,29 @@ __global__ void __launch_bounds__(256) refine_final_kernel(int k, double trunc_r
       const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
       for (int j = 0; j < k; ++j) r += sg[j] > tol;
     }
-    rank_s = r;
+    *rank_tmp = r;
     if (rank_out) *rank_out = r;
   }
-  __syncthreads();
-  const int rank = rank_s;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) sig_out[pos[j]] = sg[j];
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int j = e / k, i = e - j * k;  // column j, row i of U / V (column-major)
+}
+
+// Sign-fix and write Uw, Vw (row-major, column r = r-th singular vector,
+// zero beyond the kept rank) from the last iterates; spread over the grid.
+__global__ void __launch_bounds__(256) refine_write_kernel(int k, const double* __restrict__ Ubuf0,
+                                                           const double* __restrict__ Ubuf1,
+                                                           const double* __restrict__ Vbuf0,
+                                                           const double* __restrict__ Vbuf1, const double* __restrict__ d,
+                                                           const int* __restrict__ done_iter,
+                                                           const int* __restrict__ pos, const int* __restrict__ rank_tmp,
+                                                           double* __restrict__ Uw_out, double* __restrict__ Vw_out) {
+  const int done = *done_iter;
+  if (done == kNotDone) return;
+  const int last = done;  // U, V after iteration `done` live in buffer (done + 1) % 2
+  const double* U = ((last + 1) & 1) ? Ubuf1 : Ubuf0;
+  const double* V = ((last + 1) & 1) ? Vbuf1 : Vbuf0;
+  const int rank = *rank_tmp;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / k), i = (int)(e - (long long)j * k);  // column j, row i of U / V (column-major)
     const int r = pos[j];
     const bool keep = r < rank;
     const double sgn = d[j] < 0.0 ? -1.0 : 1.0;
@@ -945,6 +973,8 @@ SvdWs carve_svd(Carve& cv, int k) {
   w.d = cv.take<double>(k);
   w.maxoff = cv.take<unsigned long long>(kItersB);
   w.done_iter = cv.take<int>(1);
+  w.pos = cv.take<int>(k);
+  w.rank_tmp = cv.take<int>(1);
   w.bar = cv.take<GridBarrier>(1);
   w.Wc = cv.take<double>(kk);
   w.Vc = cv.take<double>(kk);
@@ -1040,10 +1070,12 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
                 cudaLaunchCooperativeKernel((const void*)refine_persistent_kernel, dim3(grid), dim3(256), args, 0,
                                             stream));
   }
-  CABS_LAUNCH(stream, "refine_final_kernel",
-              refine_final_kernel<<<1, 256, 0, stream>>>(k, trunc_rtol, w.U[0], w.U[1], w.V[0], w.V[1], w.d,
-                                                         w.done_iter, kItersB, sig, Uw, Vw, rank, refine, status,
-                                                         w.bar));
+  CABS_LAUNCH(stream, "refine_sort_kernel",
+              refine_sort_kernel<<<1, 256, 0, stream>>>(k, trunc_rtol, w.d, w.done_iter, sig, w.pos, w.rank_tmp, rank,
+                                                        refine, status, w.bar));
+  CABS_LAUNCH(stream, "refine_write_kernel",
+              refine_write_kernel<<<std::max(1, std::min(ceil_div(k * k, 256), 2 * sm_count())), 256, 0, stream>>>(
+                  k, w.U[0], w.U[1], w.V[0], w.V[1], w.d, w.done_iter, w.pos, w.rank_tmp, Uw, Vw));
   // ---- fallback: FP64 Jacobi (exits at once when Phase B converged)
   return launch_svd_jacobi_f64(W, k, trunc_rtol, w.done_iter, w.Wc, w.Vc, sig, Uw, Vw, rank, sweeps, status, stream);
 }

@@ -12,6 +12,7 @@ struct SvdWs {
   double* d;                           // current singular value estimates
   unsigned long long* maxoff;          // per-iteration max |F|, |G| (as ordered bits)
   int* done_iter;                      // first converged iteration, or INT_MAX
+  int *pos, *rank_tmp;                 // descending position of each value; kept rank
   GridBarrier* bar;
   double *Wc, *Vc;                     // FP64 Jacobi fallback scratch
 };
