@@ -207,24 +207,24 @@ __device__ __forceinline__ void store_col(float* x, int lane, const float* xr) {
 
 // The rotation of rotate_pair_reg with column x held in registers (xr) and
 // column y in shared memory; V is left alone and (c, s) is recorded in *cs
-// ((1, 0) when the pair is already orthogonal to the tolerance).
+// ((1, 0) when the pair is already orthogonal to the tolerance). The squared
+// norms travel with the columns -- a in a register, b in shared memory at
+// *bn -- and are updated by the exact identities |c x - s y|^2 =
+// c^2 a - 2 c s g + s^2 b and |s x + c y|^2 = s^2 a + 2 c s g + c^2 b, so a
+// step reduces only the inner product g across the warp. They are
+// recomputed from the columns at the start of every round.
 template <int R>
-__device__ __forceinline__ bool rotate_top_reg(float* xr, float* y, int lane, float2* cs) {
+__device__ __forceinline__ bool rotate_top_reg(float* xr, float& a, float* y, float* bn, int lane, float2* cs) {
   float yr[R];
   load_col<R>(y, lane, yr);
-  float a = 0.f, b = 0.f, g = 0.f;
+  // every lane reads b before the shuffles below, which lane 0 must pass
+  // before it overwrites *bn
+  const float b = *bn;
+  float g = 0.f;
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    a = fmaf(xr[i], xr[i], a);
-    b = fmaf(yr[i], yr[i], b);
-    g = fmaf(xr[i], yr[i], g);
-  }
+  for (int i = 0; i < R; ++i) g = fmaf(xr[i], yr[i], g);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, off);
-    b += __shfl_xor_sync(0xffffffffu, b, off);
-    g += __shfl_xor_sync(0xffffffffu, g, off);
-  }
+  for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
   float c, s;
   if (!jacobi_cs(a, b, g, c, s)) {
     if (lane == 0) *cs = make_float2(1.f, 0.f);
@@ -237,8 +237,25 @@ __device__ __forceinline__ bool rotate_top_reg(float* xr, float* y, int lane, fl
     yr[i] = s * u + c * v;
   }
   store_col<R>(y, lane, yr);
-  if (lane == 0) *cs = make_float2(c, s);
+  const float cc = c * c, ss = s * s, cs2 = 2.f * c * s * g;
+  const float a2 = cc * a - cs2 + ss * b;
+  if (lane == 0) {
+    *bn = ss * a + cs2 + cc * b;
+    *cs = make_float2(c, s);
+  }
+  a = a2;
   return true;
+}
+
+// Squared norm of a column held as in load_col.
+template <int R>
+__device__ __forceinline__ float col_sq(const float* xr) {
+  float a = 0.f;
+#pragma unroll
+  for (int i = 0; i < R; ++i) a = fmaf(xr[i], xr[i], a);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+  return a;
 }
 
 // V columns (vx, vy) <- the rotation recorded for their W columns.
@@ -338,6 +355,7 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   float* buf1 = cs + 4 * blk;
   __shared__ int rot_flag[2];
   __shared__ float2 rot_cs[kMaxBlkRot][kMaxBlkRot];  // (c, s) of step s, pair j
+  __shared__ float bnorm[kMaxBlkRot];                 // squared norms of the bottom block's columns
   // CTA c starts with blocks c (top) and 2 NC - 1 - c (bottom). Block 0 stays;
   // the other 2 NC - 1 move one place around the circle per round, so after
   // the 2 NC - 1 rounds of a sweep every block is back where it started and
@@ -394,11 +412,20 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
       {
         const bool spare = 2 * b <= nwarps;
         float xr[R];
-        if (warp < b) load_col<R>(Wt + (size_t)warp * kp, lane, xr);
+        float an = 0.f;
+        if (warp < b) {
+          float yr[R];
+          load_col<R>(Wt + (size_t)warp * kp, lane, xr);
+          load_col<R>(Wb + (size_t)warp * kp, lane, yr);
+          an = col_sq<R>(xr);
+          const float bq = col_sq<R>(yr);
+          if (lane == 0) bnorm[warp] = bq;  // read in step 0 by this warp only
+          __syncwarp();
+        }
         for (int s = 0; s <= b; ++s) {
           if (warp < b && s < b) {
             const int q = (warp + s) % b;
-            my_rot |= rotate_top_reg<R>(xr, Wb + (size_t)q * kp, lane, &rot_cs[s][warp]);
+            my_rot |= rotate_top_reg<R>(xr, an, Wb + (size_t)q * kp, &bnorm[q], lane, &rot_cs[s][warp]);
           }
           const int vw = spare ? warp - b : warp;
           if (s >= 1 && vw >= 0 && vw < b) {
@@ -751,22 +778,38 @@ __global__ void __launch_bounds__(256) refine_sort_kernel(int k, double trunc_rt
     return;  // the FP64 Jacobi fallback writes the outputs
   }
   __shared__ double sg[CABS_MAX_K];
+  __shared__ double wmax[8];
   for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = fabs(d[i]);
   __syncthreads();
+  // position of value j: the number of values before it in descending order
+  // (four independent counters, so the loads overlap)
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    int r = 0;
-    for (int i = 0; i < k; ++i) r += (sg[i] > sg[j]) || (sg[i] == sg[j] && i < j);
-    pos_out[j] = r;
-    sig_out[r] = sg[j];
-  }
-  if (threadIdx.x == 0) {
-    double smax = 0.0;
-    for (int j = 0; j < k; ++j) smax = fmax(smax, sg[j]);
-    int r = 0;
-    if (smax > 0.0) {
-      const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
-      for (int j = 0; j < k; ++j) r += sg[j] > tol;
+    const double v = sg[j];
+    int r0 = 0, r1 = 0, r2 = 0, r3 = 0, i = 0;
+    for (; i + 4 <= k; i += 4) {
+      r0 += (sg[i] > v) || (sg[i] == v && i < j);
+      r1 += (sg[i + 1] > v) || (sg[i + 1] == v && i + 1 < j);
+      r2 += (sg[i + 2] > v) || (sg[i + 2] == v && i + 2 < j);
+      r3 += (sg[i + 3] > v) || (sg[i + 3] == v && i + 3 < j);
     }
+    for (; i < k; ++i) r0 += (sg[i] > v) || (sg[i] == v && i < j);
+    const int r = r0 + r1 + r2 + r3;
+    pos_out[j] = r;
+    sig_out[r] = v;
+  }
+  // the largest value (block maximum), then the kept count
+  double m = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) m = fmax(m, sg[j]);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double smax = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) smax = fmax(smax, wmax[w]);
+  const double tol = fmax(trunc_rtol, (double)k * 2.220446049250313e-16) * smax;
+  int keep = 0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) keep += (smax > 0.0 && sg[j] > tol) ? 1 : 0;
+  const int r = __syncthreads_count(keep);
+  if (threadIdx.x == 0) {
     *rank_tmp = r;
     if (rank_out) *rank_out = r;
   }
