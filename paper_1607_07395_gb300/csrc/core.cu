@@ -147,17 +147,32 @@ __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ 
   }
 }
 
-// One CTA of k threads: column norms, S and the per-column scale factors.
-__global__ void core_finalize_kernel(const double* __restrict__ part1, int nb1, const double* __restrict__ part2,
-                                     int nb2, int k, const double* __restrict__ sig, const int* __restrict__ rank_p,
-                                     int core, int embed, double mn_over_kk, double* __restrict__ S,
-                                     double* __restrict__ f1, double* __restrict__ f2) {
-  const int r = threadIdx.x;
-  if (r >= k) return;
+// One CTA per column r: its norms N_c, N_r from the per-row-block partials
+// (summed by a fixed tree over the CTA's threads, so deterministic), then S
+// and the column's two scale factors.
+__global__ void __launch_bounds__(256) core_finalize_kernel(const double* __restrict__ part1, int nb1,
+                                                            const double* __restrict__ part2, int nb2, int k,
+                                                            const double* __restrict__ sig,
+                                                            const int* __restrict__ rank_p, int core, int embed,
+                                                            double mn_over_kk, double* __restrict__ S,
+                                                            double* __restrict__ f1, double* __restrict__ f2) {
+  __shared__ double red[2][256];
+  const int r = blockIdx.x, tid = threadIdx.x;
   double s1 = 0.0, s2 = 0.0;
-  for (int b = 0; b < nb1; ++b) s1 += part1[(size_t)b * k + r];
-  for (int b = 0; b < nb2; ++b) s2 += part2[(size_t)b * k + r];
-  const double nc = sqrt(s1), nr = sqrt(s2);
+  for (int b = tid; b < nb1; b += blockDim.x) s1 += part1[(size_t)b * k + r];
+  for (int b = tid; b < nb2; b += blockDim.x) s2 += part2[(size_t)b * k + r];
+  red[0][tid] = s1;
+  red[1][tid] = s2;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[0][tid] += red[0][tid + w];
+      red[1][tid] += red[1][tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid != 0) return;
+  const double nc = sqrt(red[0][0]), nr = sqrt(red[1][0]);
   const int rank = *rank_p;
   double sv = 0.0, a = 0.0, c = 0.0;
   if (r < rank && nc > 0.0 && nr > 0.0) {
@@ -228,8 +243,9 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));
   CABS_LAUNCH(stream, "extrap_gemm_kernel(Rt U_w)", extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2));
   const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);
-  CABS_LAUNCH(stream, "core_finalize_kernel", core_finalize_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
-                                                     mn_over_kk, S, w.f1, w.f2));
+  CABS_LAUNCH(stream, "core_finalize_kernel",
+              core_finalize_kernel<<<k, 256, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
+                                                          mn_over_kk, S, w.f1, w.f2));
   const int sms = sm_count();
   CABS_LAUNCH(stream, "scale_cols_kernel(1)", scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(m * k, 256), sms * 8)), 256, 0, stream>>>(out1, m, k, w.f1));
   CABS_LAUNCH(stream, "scale_cols_kernel(2)", scale_cols_kernel<T><<<std::max(1, std::min(ceil_div(n * k, 256), sms * 8)), 256, 0, stream>>>(out2, n, k, w.f2));

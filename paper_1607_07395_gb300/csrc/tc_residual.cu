@@ -34,20 +34,28 @@ struct ResCfg {
 
 // US_p[i][r] = U[i][r] S[r], V_p[j][r] = V[j][r] for r < k; zero for k <= r < Kp.
 template <bool kTF32>
-__global__ void residual_prep_kernel(const float* __restrict__ U, const double* __restrict__ S,
-                                     const float* __restrict__ V, long long m, long long n, int k, int Kp,
-                                     void* __restrict__ USp, void* __restrict__ Vp) {
-  const long long total = (m + n) * Kp;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long row = e / Kp;
-    const int r = (int)(e - row * Kp);
-    float v = 0.f;
-    if (r < k) v = row < m ? (float)((double)U[row * k + r] * S[r]) : V[(row - m) * k + r];
-    if constexpr (kTF32) {
-      (row < m ? (float*)USp : (float*)Vp)[(row < m ? row : row - m) * Kp + r] = v;
-    } else {
-      (row < m ? (__nv_bfloat16*)USp : (__nv_bfloat16*)Vp)[(row < m ? row : row - m) * Kp + r] = __float2bfloat16_rn(v);
+__global__ void __launch_bounds__(256) residual_prep_kernel(const float* __restrict__ U, const double* __restrict__ S,
+                                                            const float* __restrict__ V, long long m, long long n,
+                                                            int k, int Kp, void* __restrict__ USp,
+                                                            void* __restrict__ Vp) {
+  // one warp per row, lanes along the row (coalesced); U diag(S) in FP32
+  // before the rounding to the operand type, whose unit roundoff dominates
+  __shared__ float s32[CABS_MAX_K];
+  for (int r = threadIdx.x; r < k; r += blockDim.x) s32[r] = (float)S[r];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (long long row = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); row < m + n;
+       row += (long long)gridDim.x * wpb) {
+    const bool top = row < m;
+    const long long rr = top ? row : row - m;
+    const float* src = (top ? U : V) + rr * k;
+    for (int r = lane; r < Kp; r += 32) {
+      const float v = r < k ? (top ? src[r] * s32[r] : src[r]) : 0.f;
+      if constexpr (kTF32) {
+        ((float*)(top ? USp : Vp))[rr * Kp + r] = v;
+      } else {
+        ((__nv_bfloat16*)(top ? USp : Vp))[rr * Kp + r] = __float2bfloat16_rn(v);
+      }
     }
   }
 }
@@ -258,8 +266,8 @@ cabs_status tc_residual_typed(const cabs_source& src, int64_t m, int64_t n, int 
   CABS_TRY(make_tmap_2d(&tmA, USp, dt, m, Kp, (uint64_t)Kp * Cfg::ES, Cfg::KC, tc::kBM));
   CABS_TRY(make_tmap_2d(&tmB, Vp, dt, n, Kp, (uint64_t)Kp * Cfg::ES, Cfg::KC, Cfg::BN));
   CABS_LAUNCH(stream, "tc_residual_prep",
-              residual_prep_kernel<kTF32><<<std::max(1, std::min(ceil_div((m + n) * Kp, 256), sm_count() * 8)), 256,
-                                            0, stream>>>(U, S, V, m, n, k, Kp, USp, Vp));
+              residual_prep_kernel<kTF32><<<std::max(1, std::min(ceil_div(m + n, 8), sm_count() * 8)), 256, 0,
+                                            stream>>>(U, S, V, m, n, k, Kp, USp, Vp));
   if (cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess) return check_cuda("tc residual err clear");
   CUtensorMap tmM;
   CABS_TRY(make_tmap_2d(&tmM, src.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, m, n, (uint64_t)src.lda * 4, 32, tc::kBM));
