@@ -73,7 +73,7 @@ typedef enum {
   CABS_CORE_STABILIZED = 1
 } cabs_core;
 
-typedef enum { CABS_SRC_DENSE = 0, CABS_SRC_RBF = 1 } cabs_source_kind;
+typedef enum { CABS_SRC_DENSE = 0, CABS_SRC_RBF = 1, CABS_SRC_CSR = 2 } cabs_source_kind;
 
 /* Where the entries of A come from. */
 typedef struct {
@@ -90,6 +90,17 @@ typedef struct {
   const float* Y;
   int32_t d;
   float sigma;
+  /* CABS_SRC_CSR: a sparse A (the sparse inputs of Table 1) in compressed
+   * rows, device: row_ptr (m + 1, int64, row_ptr[0] = 0, non-decreasing,
+   * row_ptr[m] = nnz), col_idx (nnz, int32, strictly increasing within each
+   * row, in [0, n)) and the values in A (nnz, FP64 when a_is_f64 != 0, else
+   * FP32); lda is unused. Entries not stored are zero. The kernels clamp
+   * row_ptr to [0, nnz] and skip column indices outside [0, n), so malformed
+   * arrays give wrong values but no out-of-bounds access; unsorted rows give
+   * wrong values. */
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  int64_t nnz;
 } cabs_source;
 
 #define CABS_MAX_K 256      /* largest k1 / k2 the sketch accepts */

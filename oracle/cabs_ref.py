@@ -34,6 +34,7 @@ Steps and the passages they follow (section / equation / algorithm of the paper)
                        factors of the pilot sketch (supplementary Section 3
                        names leverage scores as the use of that form), used
                        as sampling probabilities without replacement
+``CSRSource``          sparse A in compressed rows (Table 1's sparse inputs)
 ``cabs``               Algorithm 2 end to end
 ``orthogonalize``      the sketch in SVD form (supplementary Section 3)
 ``pinv_trunc``         pseudo-inverse by the SVD with the truncation below
@@ -480,6 +481,33 @@ class RBFSource:
 
     def entries(self, ii, jj):
         return rbf_entries(self.X, self.Y, self.sigma, ii, jj)
+
+
+class CSRSource:
+    """A sparse A (the sparse inputs of Table 1) in compressed rows: indptr
+    (m + 1), indices (sorted within each row), data; missing entries are 0.
+    Gathers go through scipy's sparse slicing, an implementation independent
+    of the dense one."""
+
+    def __init__(self, indptr, indices, data, n):
+        import scipy.sparse as sp
+        indptr = np.asarray(indptr)
+        self.m, self.n = len(indptr) - 1, int(n)
+        self.A = sp.csr_matrix((np.asarray(data), np.asarray(indices), indptr), shape=(self.m, self.n))
+
+    def gather(self, rows, cols):
+        rows = np.asarray(rows)
+        cols = np.asarray(cols)
+        C = np.asarray(self.A[:, cols].toarray(), dtype=np.float64)
+        Rt = np.asarray(self.A[rows, :].toarray().T, dtype=np.float64)
+        W = np.asarray(self.A[rows, :][:, cols].toarray(), dtype=np.float64)
+        return C, Rt, W
+
+    def entries(self, ii, jj):
+        return np.asarray(self.A[np.asarray(ii), np.asarray(jj)], dtype=np.float64).ravel()
+
+    def dense(self):
+        return np.asarray(self.A.toarray(), dtype=np.float64)
 
 
 @dataclass

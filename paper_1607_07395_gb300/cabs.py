@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "libcabs.so")
 CABS_OK, CABS_EINVAL, CABS_ENOMEM, CABS_ECUDA, CABS_ETIMEOUT, CABS_EBUSY, CABS_ERANK, CABS_ENOTFOUND = range(8)
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = range(4)
 CORE_PINV, CORE_STABILIZED = 0, 1
-SRC_DENSE, SRC_RBF = 0, 1
+SRC_DENSE, SRC_RBF, SRC_CSR = 0, 1, 2
 TAG_ROWS, TAG_COLS, TAG_EVAL = 0, 1, 2
 MAX_K, MAX_D, MAX_ITERS = 256, 64, 64
 FLAG_FOLLOW_ERR = 1
@@ -38,7 +38,8 @@ class CabsError(RuntimeError):
 
 class cabs_source(C.Structure):
     _fields_ = [("kind", C.c_int32), ("A", C.c_void_p), ("lda", C.c_int64), ("a_is_f64", C.c_int32),
-                ("X", C.c_void_p), ("Y", C.c_void_p), ("d", C.c_int32), ("sigma", C.c_float)]
+                ("X", C.c_void_p), ("Y", C.c_void_p), ("d", C.c_int32), ("sigma", C.c_float),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("nnz", C.c_int64)]
 
 
 class cabs_params(C.Structure):
@@ -226,6 +227,18 @@ def rbf_source(X, Y, sigma):
     X, Y = X.contiguous(), Y.contiguous()
     c = cabs_source(kind=SRC_RBF, X=X.data_ptr(), Y=Y.data_ptr(), d=X.shape[1], sigma=float(sigma))
     return Source(c, (X, Y))
+
+
+def csr_source(row_ptr, col_idx, vals):
+    """A sparse matrix in compressed rows on the device: row_ptr (m + 1, int64),
+    col_idx (nnz, int32, sorted within rows), vals (nnz, FP32 or FP64)."""
+    import torch
+    assert row_ptr.is_cuda and row_ptr.dtype == torch.int64
+    assert col_idx.is_cuda and col_idx.dtype == torch.int32 and vals.is_cuda
+    row_ptr, col_idx, vals = row_ptr.contiguous(), col_idx.contiguous(), vals.contiguous()
+    c = cabs_source(kind=SRC_CSR, A=vals.data_ptr(), a_is_f64=int(vals.dtype == torch.float64),
+                    row_ptr=row_ptr.data_ptr(), col_idx=col_idx.data_ptr(), nnz=vals.numel())
+    return Source(c, (row_ptr, col_idx, vals))
 
 
 def make_params(m, n, k1, k2=None, iters=5, seed=1607, prec="fp64", core="pinv", upsilon_pow=0.0, trunc_rtol=0.0,

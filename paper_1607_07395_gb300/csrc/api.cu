@@ -80,6 +80,11 @@ cabs_status validate_source(const cabs_source* src, int64_t m, int64_t n) {
     CABS_REQUIRE(src->X != nullptr && src->Y != nullptr, "rbf source: X or Y is NULL");
     CABS_REQUIRE(src->d >= 1 && src->d <= CABS_MAX_D, "rbf source: d = %d outside [1, %d]", src->d, CABS_MAX_D);
     CABS_REQUIRE(src->sigma > 0.0f && finite(src->sigma), "rbf source: sigma must be positive and finite");
+  } else if (src->kind == CABS_SRC_CSR) {
+    CABS_REQUIRE(src->row_ptr != nullptr, "csr source: row_ptr is NULL");
+    CABS_REQUIRE(src->nnz >= 0, "csr source: nnz < 0");
+    CABS_REQUIRE(src->nnz == 0 || (src->col_idx != nullptr && src->A != nullptr),
+                 "csr source: col_idx or values are NULL");
   } else {
     CABS_REQUIRE(false, "unknown source kind %d", src->kind);
   }
@@ -114,7 +119,7 @@ cabs_status validate_params(const cabs_params* p) {
 cabs_status validate_error_request(const cabs_source* src, const cabs_params* p, const cabs_result* out) {
   if (!(p->flags & CABS_FLAG_ERROR)) return CABS_OK;
   CABS_REQUIRE(out->err != nullptr, "CABS_FLAG_ERROR needs result.err");
-  CABS_REQUIRE(p->err_samples > 0 || src->kind == CABS_SRC_DENSE, "the exact error needs a dense source");
+  CABS_REQUIRE(p->err_samples > 0 || src->kind != CABS_SRC_RBF, "the exact error needs stored entries (dense or CSR)");
   return CABS_OK;
 }
 
@@ -360,7 +365,7 @@ cabs_status cabs_error_workspace_size(const cabs_source* src, const cabs_params*
   CABS_TRY(validate_params(p));
   CABS_TRY(validate_source(src, p->m, p->n));
   CABS_REQUIRE(samples >= 0, "samples must be >= 0");
-  CABS_REQUIRE(samples > 0 || src->kind == CABS_SRC_DENSE, "the exact error needs a dense source");
+  CABS_REQUIRE(samples > 0 || src->kind != CABS_SRC_RBF, "the exact error needs stored entries (dense or CSR)");
   *bytes = error_ws_bytes(*src, p->m, p->n, p->k2, samples, p->prec) + 256;
   return CABS_OK;
 }

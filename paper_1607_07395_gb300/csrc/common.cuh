@@ -103,6 +103,27 @@ __host__ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1
   return o;
 }
 
+// ------------------------------------------------------------ CSR sources
+
+// Position of column j in the sorted col_idx[lo, hi), or -1.
+__device__ __forceinline__ long long csr_find(const int* __restrict__ col_idx, long long lo, long long hi, int j) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    const int c = col_idx[mid];
+    if (c == j) return mid;
+    if (c < j) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+// The stored range [lo, hi) of row i, clamped to [0, nnz].
+__device__ __forceinline__ void csr_row_range(const long long* __restrict__ row_ptr, long long nnz, long long i,
+                                              long long& lo, long long& hi) {
+  lo = min(max(row_ptr[i], 0ll), nnz);
+  hi = min(max(row_ptr[i + 1], lo), nnz);
+}
+
 // ------------------------------------------------------------ elem types
 
 template <typename T>

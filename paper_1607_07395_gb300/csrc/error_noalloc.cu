@@ -146,6 +146,13 @@ template <typename T>
 __device__ __forceinline__ double noalloc_entry(const cabs_source& src, long long i, long long j) {
   if (src.kind == CABS_SRC_DENSE)
     return src.a_is_f64 ? ((const double*)src.A)[i * src.lda + j] : (double)((const float*)src.A)[i * src.lda + j];
+  if (src.kind == CABS_SRC_CSR) {
+    long long lo, hi;
+    csr_row_range((const long long*)src.row_ptr, src.nnz, i, lo, hi);
+    const long long e = csr_find(src.col_idx, lo, hi, (int)j);
+    if (e < 0) return 0.0;
+    return src.a_is_f64 ? ((const double*)src.A)[e] : (double)((const float*)src.A)[e];
+  }
   T acc = T(0);
   for (int q = 0; q < src.d; ++q) {
     const T diff = (T)src.X[i * src.d + q] - (T)src.Y[j * src.d + q];
@@ -250,7 +257,8 @@ extern "C" cabs_status cabs_error_noalloc(cabs_ctx* ctx, const cabs_source* src,
   CABS_TRY(validate_source(src, p->m, p->n));
   CABS_REQUIRE(res != nullptr && res->U && res->S && res->V, "result U, S, V must be set");
   CABS_REQUIRE(samples >= 0, "samples must be >= 0");
-  CABS_REQUIRE(samples > 0 || src->kind == CABS_SRC_DENSE, "the exact error needs a dense source");
+  CABS_REQUIRE(samples > 0 || src->kind == CABS_SRC_DENSE,
+               "the exact error without a workspace needs a dense source (cabs_error takes CSR too)");
   CABS_REQUIRE(samples > 0 || p->m <= (int64_t)kTile * kNoAllocMaxBlocks,
                "the no-allocation exact error supports m <= %d rows (its fixed scratch holds %d row blocks); "
                "got m = %lld", kTile * kNoAllocMaxBlocks, kNoAllocMaxBlocks, (long long)p->m);

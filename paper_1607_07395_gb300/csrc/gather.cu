@@ -10,6 +10,12 @@
 // k contiguous rows with coalesced loads and transposes them through a
 // padded shared-memory tile so the n x k output is written coalesced.
 //
+// Sparse A in compressed rows (the sparse inputs of Table 1): C is filled
+// one warp per row, each lane binary-searching the row's sorted column
+// indices for its selected columns (absent entries are zero); Rt is zeroed
+// and then each selected row scatters its stored entries into its column of
+// Rt. Both read the stored value itself, so W == C[I, :] == Rt[J, :]^T.
+//
 // Implicit RBF A[i, j] = exp(-|x_i - y_j|^2 / 2 sigma^2): the same outputs
 // are generated on the fly (the entries are never stored). C uses points X
 // against the selected Y rows and Rt uses Y against the selected X rows; the
@@ -155,6 +161,53 @@ __global__ void __launch_bounds__(kGatherThreads) rbf_block_kernel(const float* 
   }
 }
 
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kGatherThreads) csr_cols_kernel(const long long* __restrict__ row_ptr,
+                                                                  const int* __restrict__ col_idx,
+                                                                  const Tin* __restrict__ vals, long long nnz,
+                                                                  long long m, const int* __restrict__ cols, int kc,
+                                                                  Tout* __restrict__ C) {
+  __shared__ int cs[CABS_MAX_K];
+  for (int t = threadIdx.x; t < kc; t += blockDim.x) cs[t] = cols[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < m; i += nwarps) {
+    long long lo, hi;
+    csr_row_range(row_ptr, nnz, i, lo, hi);
+    for (int t = lane; t < kc; t += 32) {
+      const long long e = csr_find(col_idx, lo, hi, cs[t]);
+      C[i * kc + t] = e >= 0 ? (Tout)vals[e] : Tout(0);
+    }
+  }
+}
+
+// Rt[j, p] = A[rows[p], j]: one CTA per selected row p scatters its stored
+// entries (Rt must be zero beforehand).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kGatherThreads) csr_rows_t_kernel(const long long* __restrict__ row_ptr,
+                                                                    const int* __restrict__ col_idx,
+                                                                    const Tin* __restrict__ vals, long long nnz,
+                                                                    long long m, long long n,
+                                                                    const int* __restrict__ rows, int kr,
+                                                                    Tout* __restrict__ Rt) {
+  const int p = blockIdx.x;
+  const long long i = min(max((long long)rows[p], 0ll), m - 1);
+  long long lo, hi;
+  csr_row_range(row_ptr, nnz, i, lo, hi);
+  for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const int j = col_idx[e];
+    if (j >= 0 && j < n) Rt[(long long)j * kr + p] = (Tout)vals[e];
+  }
+}
+
+template <typename Tout>
+__global__ void zero_kernel(Tout* __restrict__ x, long long count) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] = Tout(0);
+}
+
 template <typename Tout>
 cabs_status gather_typed(const cabs_source& src, int64_t m, int64_t n, const int* rows, int kr, const int* cols,
                          int kc, Tout* C, Tout* Rt, double* W, cudaStream_t stream) {
@@ -177,6 +230,27 @@ cabs_status gather_typed(const cabs_source& src, int64_t m, int64_t n, const int
                       (const double*)src.A, src.lda, m, n, rows, kr, Rt);
                   else gather_rows_t_kernel<float, Tout><<<grid, kGatherThreads, 0, stream>>>(
                       (const float*)src.A, src.lda, m, n, rows, kr, Rt));
+    }
+  } else if (src.kind == CABS_SRC_CSR) {
+    const long long* rp = (const long long*)src.row_ptr;
+    if (C && kc > 0) {
+      const int blocks = std::max(1, std::min(ceil_div(m, kGatherThreads / 32), sms * 8));
+      CABS_LAUNCH(stream, "csr_cols_kernel",
+                  if (src.a_is_f64) csr_cols_kernel<double, Tout><<<blocks, kGatherThreads, 0, stream>>>(
+                      rp, src.col_idx, (const double*)src.A, src.nnz, m, cols, kc, C);
+                  else csr_cols_kernel<float, Tout><<<blocks, kGatherThreads, 0, stream>>>(
+                      rp, src.col_idx, (const float*)src.A, src.nnz, m, cols, kc, C));
+    }
+    if (Rt && kr > 0) {
+      const long long cnt = (long long)n * kr;
+      CABS_LAUNCH(stream, "zero_kernel",
+                  zero_kernel<Tout><<<(int)std::max<long long>(1, std::min<long long>((cnt + 255) / 256, sms * 8)), 256,
+                                      0, stream>>>(Rt, cnt));
+      CABS_LAUNCH(stream, "csr_rows_t_kernel",
+                  if (src.a_is_f64) csr_rows_t_kernel<double, Tout><<<kr, kGatherThreads, 0, stream>>>(
+                      rp, src.col_idx, (const double*)src.A, src.nnz, m, n, rows, kr, Rt);
+                  else csr_rows_t_kernel<float, Tout><<<kr, kGatherThreads, 0, stream>>>(
+                      rp, src.col_idx, (const float*)src.A, src.nnz, m, n, rows, kr, Rt));
     }
   } else {
     const double inv2s2 = 1.0 / (2.0 * (double)src.sigma * (double)src.sigma);

@@ -29,6 +29,10 @@ int extrap_row_blocks(int64_t M, bool elem_f64);
 cabs_status launch_extrap_gemm(const void* X, int64_t M, int K, const double* B, int N, bool elem_f64, void* out,
                                double* part, const char* name, cudaStream_t stream);
 
+// G = X^T X (K x K, FP64) of a tall X (M x K, elem); part: gram_ws_bytes(M, K) of scratch.
+size_t gram_ws_bytes(int64_t M, int K, bool elem_f64);
+cabs_status launch_gram(const void* X, int64_t M, int K, bool elem_f64, void* part, double* G, cudaStream_t stream);
+
 // k x k FP64 product C = diag(a) op(A) diag(d) op(B) diag(b) (a, b, d may be NULL).
 cabs_status launch_kk_gemm(int k, const double* A, bool transA, const double* d, const double* B, bool transB,
                            const double* a, const double* b, double* C, cudaStream_t stream);

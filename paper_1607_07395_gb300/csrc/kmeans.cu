@@ -264,122 +264,196 @@ __global__ void __launch_bounds__(256) energy_exact_kernel(const T* __restrict__
 constexpr int kUWarps = 16;
 constexpr int kUMaxPerLane = CABS_MAX_K / 32;
 
+// ------------------------------------------------ members by centre
+// The update reads each centre's members from a stable counting sort of the
+// labels (index order within a centre) instead of scanning all labels once
+// per centre: per-chunk histograms, an offset table, a stable scatter, then
+// one CTA per centre over its own members only.
+
+constexpr int kSortChunk = 2048;  // points per histogram / scatter chunk
+
+__global__ void __launch_bounds__(256) label_hist_kernel(const int* __restrict__ labels, long long M, int k2,
+                                                         int* __restrict__ chunk_cnt) {
+  __shared__ int h[CABS_MAX_K];
+  for (int j = threadIdx.x; j < k2; j += blockDim.x) h[j] = 0;
+  __syncthreads();
+  const long long lo = (long long)blockIdx.x * kSortChunk, hi = min(M, lo + kSortChunk);
+  for (long long l = lo + threadIdx.x; l < hi; l += blockDim.x) {
+    const int j = labels[l];
+    if (j >= 0 && j < k2) atomicAdd(&h[j], 1);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < k2; j += blockDim.x) chunk_cnt[(size_t)blockIdx.x * k2 + j] = h[j];
+}
+
+// One CTA of k2 threads: chunk_off[c][j] = start of chunk c's members of
+// centre j in the sorted order; base[j], cnt[j] = centre j's range.
+__global__ void __launch_bounds__(CABS_MAX_K) label_offsets_kernel(const int* __restrict__ chunk_cnt, int chunks,
+                                                                   int k2, int* __restrict__ chunk_off,
+                                                                   int* __restrict__ base, int* __restrict__ cnt) {
+  __shared__ int tot[CABS_MAX_K];
+  const int j = threadIdx.x;
+  int t = 0;
+  if (j < k2)
+    for (int c = 0; c < chunks; ++c) t += chunk_cnt[(size_t)c * k2 + j];
+  tot[j] = j < k2 ? t : 0;
+  __syncthreads();
+  if (j == 0) {
+    int run = 0;
+    for (int i = 0; i < k2; ++i) {
+      const int v = tot[i];
+      tot[i] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  if (j < k2) {
+    int run = tot[j];
+    base[j] = run;
+    cnt[j] = t;
+    for (int c = 0; c < chunks; ++c) {
+      chunk_off[(size_t)c * k2 + j] = run;
+      run += chunk_cnt[(size_t)c * k2 + j];
+    }
+  }
+}
+
+// One warp per chunk, 32 points at a time in index order: a point's slot is
+// its centre's running offset plus its rank among the batch's points of the
+// same centre (stable).
+__global__ void __launch_bounds__(32) label_scatter_kernel(const int* __restrict__ labels, long long M, int k2,
+                                                           const int* __restrict__ chunk_off, int* __restrict__ perm) {
+  __shared__ int run[CABS_MAX_K];
+  const int lane = threadIdx.x;
+  for (int j = lane; j < k2; j += 32) run[j] = chunk_off[(size_t)blockIdx.x * k2 + j];
+  __syncwarp();
+  const long long lo = (long long)blockIdx.x * kSortChunk, hi = min(M, lo + kSortChunk);
+  for (long long b = lo; b < hi; b += 32) {
+    const long long l = b + lane;
+    int j = l < hi ? labels[l] : -1;
+    if (j >= k2) j = -1;
+    const unsigned act = __ballot_sync(0xffffffffu, j >= 0);
+    if (j >= 0) {
+      const unsigned peers = __match_any_sync(act, j);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      perm[run[j] + rank] = (int)l;
+      __syncwarp(act);
+      if (lane == 31 - __clz(peers)) run[j] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// CTA (j, p) over part p of centre j's members perm[base_j, base_j + cnt_j)
+// (kUParts parts, so a large cluster -- sparse inputs put every empty row in
+// one -- spreads over several SMs): warp i takes the i-th contiguous piece of
+// the part, in order, and the warps' sums are added in warp order. The part
+// sums go to `part`; update_combine_kernel adds the parts in order
+// (deterministic) and forms the weighted mean (an empty cluster keeps its
+// centre), the count and, with energy, sum w_l |x_l - z_j|^2 with the centre
+// the assignment used.
+constexpr int kUParts = 4;
+
 template <typename T>
-__device__ __forceinline__ void accumulate_members(unsigned mask, long long base, const T* __restrict__ X, int d,
-                                                   const T* __restrict__ w, int lane, const T* __restrict__ zc,
-                                                   bool want_e, T (&acc)[kUMaxPerLane], T& wsum, int& cnt,
-                                                   T& esum) {
-  while (mask) {
+__global__ void __launch_bounds__(kUWarps * 32, sizeof(T) == 4 ? 2 : 1) update_sorted_kernel(
+    const T* __restrict__ X, int d, const int* __restrict__ perm, const int* __restrict__ base,
+    const int* __restrict__ cnt_in, const T* __restrict__ w, const T* __restrict__ Zcur, T* __restrict__ part,
+    double* __restrict__ part_e, bool want_e) {
+  __shared__ T accs[kUWarps][CABS_MAX_K];
+  __shared__ T zc[CABS_MAX_K];
+  __shared__ T wsums[kUWarps];
+  __shared__ double esums[kUWarps];
+  const int j = blockIdx.x, pp = blockIdx.y, k2 = gridDim.x;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const long long nm = cnt_in[j];
+  const long long p_lo = base[j] + nm * pp / kUParts, p_hi = base[j] + nm * (pp + 1) / kUParts;
+  const long long pn = p_hi - p_lo;
+  const long long lo = p_lo + pn * wi / kUWarps, hi = p_lo + pn * (wi + 1) / kUWarps;
+  for (int q = threadIdx.x; q < CABS_MAX_K; q += blockDim.x) zc[q] = q < d ? Zcur[(size_t)j * d + q] : T(0);
+  __syncthreads();
+  T acc[kUMaxPerLane];
+#pragma unroll
+  for (int s2 = 0; s2 < kUMaxPerLane; ++s2) acc[s2] = T(0);
+  T wsum = T(0), esum = T(0);
+  for (long long e0 = lo; e0 < hi; e0 += 4) {
     long long ls[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        ls[u] = base + b;
-      } else {
-        ls[u] = -1;
-      }
-    }
+    for (int u = 0; u < 4; ++u) ls[u] = e0 + u < hi ? (long long)perm[e0 + u] : -1;
     T xv[4][kUMaxPerLane];
     T wv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       wv[u] = ls[u] >= 0 ? w[ls[u]] : T(0);
 #pragma unroll
-      for (int s = 0; s < kUMaxPerLane; ++s) {
-        const int q = lane + 32 * s;
-        xv[u][s] = (ls[u] >= 0 && q < d) ? X[ls[u] * d + q] : T(0);
+      for (int s2 = 0; s2 < kUMaxPerLane; ++s2) {
+        const int q = lane + 32 * s2;
+        xv[u][s2] = (ls[u] >= 0 && q < d) ? X[ls[u] * d + q] : T(0);
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       if (ls[u] >= 0) {
 #pragma unroll
-        for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = fma(wv[u], xv[u][s], acc[s]);
+        for (int s2 = 0; s2 < kUMaxPerLane; ++s2) acc[s2] = fma(wv[u], xv[u][s2], acc[s2]);
         if (want_e) {
-          T e = T(0);
+          T ee = T(0);
 #pragma unroll
-          for (int s = 0; s < kUMaxPerLane; ++s) {
-            const T t = xv[u][s] - zc[lane + 32 * s];  // zero beyond d on both sides
-            e = fma(t, t, e);
+          for (int s2 = 0; s2 < kUMaxPerLane; ++s2) {
+            const T t = xv[u][s2] - zc[lane + 32 * s2];
+            ee = fma(t, t, ee);
           }
-          esum = fma(wv[u], e, esum);
+          esum = fma(wv[u], ee, esum);
         }
         wsum += wv[u];
-        ++cnt;
       }
     }
   }
-}
-
-constexpr int kULab = 4;  // label loads in flight per lane
-
-// One CTA per centre j: the weighted mean of its members (Eq. wkmeans); an
-// empty cluster keeps its centre. Warp i scans rows [M i / W, M (i + 1) / W)
-// in index order and the warps' sums are added in warp order, so the result
-// does not depend on timing. With energy != NULL the same pass also adds
-// w_l |x_l - z_j|^2 over the members with the centres the assignment used
-// (the iteration's weighted encoding error, per centre).
-template <typename T>
-__global__ void __launch_bounds__(kUWarps * 32, sizeof(T) == 4 ? 2 : 1) update_kernel(const T* __restrict__ X, long long M, int d,
-                                                              const int* __restrict__ labels, const T* __restrict__ w,
-                                                              const T* __restrict__ Zcur, T* __restrict__ Znext,
-                                                              int* __restrict__ counts, double* __restrict__ energy) {
-  __shared__ T accs[kUWarps][CABS_MAX_K];
-  __shared__ T zc[CABS_MAX_K];  // the centre the assignment used
-  __shared__ T wsums[kUWarps];
-  __shared__ double esums[kUWarps];
-  __shared__ int cnts[kUWarps];
-  const int j = blockIdx.x;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const long long lo = M * wi / kUWarps, hi = M * (wi + 1) / kUWarps;
-  T acc[kUMaxPerLane];
 #pragma unroll
-  for (int s = 0; s < kUMaxPerLane; ++s) acc[s] = T(0);
-  for (int q = threadIdx.x; q < CABS_MAX_K; q += blockDim.x) zc[q] = q < d ? Zcur[(size_t)j * d + q] : T(0);
-  __syncthreads();
-  T wsum = T(0), esum = T(0);
-  int cnt = 0;
-  // kULab label loads in flight per lane; members are summed in index order
-  for (long long base = lo; base < hi; base += 32 * kULab) {
-    int lab[kULab];
-#pragma unroll
-    for (int u = 0; u < kULab; ++u) {
-      const long long l = base + 32 * u + lane;
-      lab[u] = l < hi ? __ldg(labels + l) : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < kULab; ++u) {
-      const unsigned mask = __ballot_sync(0xffffffffu, lab[u] == j);
-      accumulate_members<T>(mask, base + 32 * u, X, d, w, lane, zc, energy != nullptr, acc, wsum, cnt, esum);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < kUMaxPerLane; ++s) accs[wi][lane + 32 * s] = acc[s];
+  for (int s2 = 0; s2 < kUMaxPerLane; ++s2) accs[wi][lane + 32 * s2] = acc[s2];
   const T ew = warp_sum(esum);
   if (lane == 0) {
     wsums[wi] = wsum;
-    cnts[wi] = cnt;
     esums[wi] = (double)ew;
   }
   __syncthreads();
-  T W = T(0);
-  int C = 0;
-  for (int i = 0; i < kUWarps; ++i) {
-    W += wsums[i];
-    C += cnts[i];
-  }
+  // part layout: [p][j][d + 1]: the d sums and the weight sum; energy in part_e[p][j]
+  T* out = part + ((size_t)pp * k2 + j) * (d + 1);
   for (int q = threadIdx.x; q < d; q += blockDim.x) {
     T sq = T(0);
     for (int i = 0; i < kUWarps; ++i) sq += accs[i][q];
+    out[q] = sq;
+  }
+  if (threadIdx.x == 0) {
+    T W = T(0);
+    double e = 0.0;
+    for (int i = 0; i < kUWarps; ++i) {
+      W += wsums[i];
+      e += esums[i];
+    }
+    out[d] = W;
+    part_e[(size_t)pp * k2 + j] = e;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) update_combine_kernel(const T* __restrict__ part,
+                                                             const double* __restrict__ part_e, int d,
+                                                             const int* __restrict__ cnt_in,
+                                                             const T* __restrict__ Zcur, T* __restrict__ Znext,
+                                                             int* __restrict__ counts, double* __restrict__ energy) {
+  const int j = blockIdx.x, k2 = gridDim.x;
+  T W = T(0);
+  for (int pp = 0; pp < kUParts; ++pp) W += part[((size_t)pp * k2 + j) * (d + 1) + d];
+  for (int q = threadIdx.x; q < d; q += blockDim.x) {
+    T sq = T(0);
+    for (int pp = 0; pp < kUParts; ++pp) sq += part[((size_t)pp * k2 + j) * (d + 1) + q];
     Znext[(size_t)j * d + q] = W > T(0) ? sq / W : Zcur[(size_t)j * d + q];
   }
   if (threadIdx.x == 0) {
-    if (counts) counts[j] = C;
+    if (counts) counts[j] = cnt_in[j];
     if (energy) {
       double e = 0.0;
-      for (int i = 0; i < kUWarps; ++i) e += esums[i];
+      for (int pp = 0; pp < kUParts; ++pp) e += part_e[(size_t)pp * k2 + j];
       energy[j] = e;
     }
   }
@@ -417,8 +491,13 @@ __global__ void copy_kernel(const T* __restrict__ a, T* __restrict__ b, long lon
 struct KmWs {
   void *xn, *w, *Za, *Zb, *zn, *tc;
   int *labels, *counts, *T;
+  int *chunk_cnt, *chunk_off, *perm, *lbase, *lcnt;  // members by centre
+  void* upart;                                        // per-part sums of the update
+  double* upart_e;                                    //   and their energies
   double *part_e, *energy;
 };
+
+int sort_chunks(int64_t M) { return (int)((M + kSortChunk - 1) / kSortChunk); }
 
 // Partial energies per iteration: the FP64 assignment kernel writes one per
 // CTA of its grid; in the other modes the update writes one per centre.
@@ -443,6 +522,13 @@ KmWs carve_km(Carve& cv, int64_t M, int d, int k2, int iters, int prec) {
   w.T = cv.take<int>(1);
   w.part_e = cv.take<double>((size_t)std::max(iters, 1) * std::max(energy_parts(M, k2, prec), energy_blocks(M)));
   w.energy = cv.take<double>(std::max(iters, 1));
+  w.chunk_cnt = cv.take<int>((size_t)sort_chunks(M) * k2);
+  w.chunk_off = cv.take<int>((size_t)sort_chunks(M) * k2);
+  w.perm = cv.take<int>(M);
+  w.lbase = cv.take<int>(k2);
+  w.lcnt = cv.take<int>(k2);
+  w.upart = cv.take<char>((size_t)kUParts * k2 * (d + 1) * eb);
+  w.upart_e = cv.take<double>((size_t)kUParts * k2);
   w.tc = nullptr;
   if (prec == CABS_PREC_TF32 || prec == CABS_PREC_BF16) {
     w.tc = cv.base ? cv.base + cv.used : nullptr;
@@ -506,9 +592,19 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
     int* lab = labels_out ? labels_out + (size_t)t * M : w.labels;
     double* pe = w.part_e + (size_t)t * nb;
     CABS_TRY(assign_once<T>(X, M, d, Zc, k2, prec, xn, wt, (T*)w.zn, lab, pe, d_recheck, t == 0, tcws, stream));
+    const int ch = sort_chunks(M);
+    CABS_LAUNCH(stream, "label_hist_kernel", label_hist_kernel<<<ch, 256, 0, stream>>>(lab, M, k2, w.chunk_cnt));
+    CABS_LAUNCH(stream, "label_offsets_kernel",
+                label_offsets_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.chunk_cnt, ch, k2, w.chunk_off, w.lbase, w.lcnt));
+    CABS_LAUNCH(stream, "label_scatter_kernel",
+                label_scatter_kernel<<<ch, 32, 0, stream>>>(lab, M, k2, w.chunk_off, w.perm));
     CABS_LAUNCH(stream, "update_kernel",
-                update_kernel<T><<<k2, kUWarps * 32, 0, stream>>>(X, M, d, lab, wt, Zc, Zn, w.counts,
-                                                                  prec == CABS_PREC_FP64 ? nullptr : pe));
+                update_sorted_kernel<T><<<dim3(k2, kUParts), kUWarps * 32, 0, stream>>>(
+                    X, d, w.perm, w.lbase, w.lcnt, wt, Zc, (T*)w.upart, w.upart_e, prec != CABS_PREC_FP64));
+    CABS_LAUNCH(stream, "update_combine_kernel",
+                update_combine_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.upart, w.upart_e, d, w.lcnt, Zc, Zn,
+                                                                 w.counts,
+                                                                 prec == CABS_PREC_FP64 ? nullptr : pe));
     T* tmp = Zc;
     Zc = Zn;
     Zn = tmp;

@@ -347,6 +347,16 @@ cabs_status orth_typed(int64_t m, int64_t n, int k, double trunc_rtol, const T* 
 
 }  // namespace
 
+size_t gram_ws_bytes(int64_t M, int K, bool elem_f64) {
+  const size_t e = elem_f64 ? gram_part_elems<double>(M, K) * sizeof(double) : gram_part_elems<float>(M, K) * sizeof(float);
+  return align256(e);
+}
+
+cabs_status launch_gram(const void* X, int64_t M, int K, bool elem_f64, void* part, double* G, cudaStream_t stream) {
+  if (elem_f64) return gram<double>((const double*)X, M, K, (double*)part, G, stream);
+  return gram<float>((const float*)X, M, K, (float*)part, G, stream);
+}
+
 cabs_status launch_kk_gemm(int k, const double* A, bool transA, const double* d, const double* B, bool transB,
                            const double* a, const double* b, double* C, cudaStream_t stream) {
   const dim3 g(ceil_div(k, 16), ceil_div(k, 16));

@@ -251,8 +251,8 @@ cabs_status cabs_serve_submit(cabs_ctx* ctx, const cabs_source* src, const cabs_
   CABS_REQUIRE(ticket != nullptr, "ticket is NULL");
   CABS_TRY(validate_params(p));
   CABS_TRY(validate_source(src, p->m, p->n));
-  CABS_REQUIRE(!(p->flags & CABS_FLAG_ERROR) || p->err_samples > 0 || src->kind == CABS_SRC_DENSE,
-               "the exact error needs a dense source");
+  CABS_REQUIRE(!(p->flags & CABS_FLAG_ERROR) || p->err_samples > 0 || src->kind != CABS_SRC_RBF,
+               "the exact error needs stored entries (dense or CSR)");
   ServeState* st = ctx->serve;
   Request r;
   r.src = *src;

@@ -23,11 +23,13 @@
 //      F_ii = R_ii / 2, G_ii = S_ii / 2;  U <- U + U F,  V <- V + V G,
 //    which solves the first-order conditions U'^T U' = I, V'^T V' = I and
 //    U'^T W V' diagonal, and so converges quadratically. Before the first
-//    iteration the kept columns of U are recomputed in FP64 as W V / |W V|.
-//    Every product is an
-//    FP64 GEMM spread over all SMs. Pairs with d_i^2 ~ d_j^2 keep only the
-//    orthogonality correction. Iteration t's kernels exit at once if an
-//    earlier iteration already converged (a device-side flag; no host sync).
+//    iteration the kept columns of U are recomputed in FP64 as W V / |W V|
+//    (and, where W has zero rows, the others completed to span R^k). Every
+//    product is an FP64 GEMM spread over all SMs. Pairs with d_i^2 ~ d_j^2,
+//    or whose correction would exceed 0.05 (values not yet separated by more
+//    than the estimates' error), keep only the orthogonality correction.
+//    Iteration t's kernels exit at once if an earlier iteration already
+//    converged (a device-side flag; no host sync).
 //  Fallback: if Phase B has not converged after its iterations, the one-CTA
 //    FP64 Jacobi SVD runs instead (status bit 1).
 // The result is sorted by singular value and truncated as before.
@@ -50,7 +52,8 @@ constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
 #endif
 constexpr float kTolA = CABS_SVD_TOL_A;  // Phase A rotation threshold |g| > tol sqrt(a b)
 constexpr int kMaxSweepsA = 40;
-constexpr int kItersB = 6;
+constexpr int kItersB = 8;
+constexpr double kMaxCorrB = 0.05;      // Phase B: larger first-order corrections are deferred
 constexpr double kConvB = 1e-8;         // Phase B: last iteration when max |F_ij|, |G_ij| (i != j) < this
 constexpr int kNotDone = 0x7fffffff;
 
@@ -667,6 +670,113 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           const double nj = a.d[j];
           if (nj > 3.814697265625e-06 * mx) Uw[e] = a.P[e] / nj;
         }
+        // Columns at the noise level whose W has all-zero rows: each takes a
+        // unit vector e_i of such a row, an exact left null vector of W. A
+        // zero row of W is zero in every column the FP32 phase produces, so
+        // without these the columns of U could not span R^k.
+        if (blockIdx.x == 0) {
+          __shared__ int zrow[CABS_MAX_K], ncol[CABS_MAX_K], zcol[CABS_MAX_K], counts[2];
+          {
+            // one warp per row of W and per column of U: all-zero tests by ballot
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int i = threadIdx.x >> 5; i < k; i += nw) {
+              bool nzr = false, nzc = false;
+              for (int j = lane; j < k; j += 32) {
+                nzr |= a.W[(size_t)i * k + j] != 0.0;
+                nzc |= Uw[(size_t)i * k + j] != 0.0;
+              }
+              const bool anyr = __any_sync(0xffffffffu, nzr), anyc = __any_sync(0xffffffffu, nzc);
+              if (lane == 0) {
+                zrow[i] = anyr ? 0 : 1;
+                zcol[i] = anyc ? 0 : 1;
+                ncol[i] = a.d[i] > 3.814697265625e-06 * mx ? 0 : 1;
+              }
+            }
+          }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            int nz = 0, nn = 0;
+            for (int i = 0; i < k; ++i) {
+              if (zrow[i]) zrow[nz++] = i;
+              if (ncol[i]) ncol[nn++] = i;
+            }
+            counts[0] = nz;
+            counts[1] = nn;
+          }
+          __syncthreads();
+          const int pairs = min(counts[0], counts[1]);
+          for (long long e = threadIdx.x; e < (long long)pairs * k; e += blockDim.x) {
+            const int t2 = (int)(e / k), i = (int)(e - (long long)t2 * k);
+            Uw[(size_t)ncol[t2] * k + i] = i == zrow[t2] ? 1.0 : 0.0;
+          }
+          __syncthreads();
+          // Null columns left over (the rank falls short of k by more than the
+          // zero rows, e.g. through repeated nonzero rows) lie in the span of
+          // the others or are zero, and the refinement cannot make them
+          // orthonormal. When W has zero rows or U exactly zero columns (the
+          // sparse regime) they are all replaced by Gram-Schmidt: each takes
+          // e_i for the row i least covered by the columns so far (smallest
+          // rho_i = sum_b U_ib^2, so |e_i - proj|^2 = 1 - rho_i >= 1 - r / k
+          // > 0), minus its projection. Elsewhere the noise columns keep their
+          // FP32 directions, which span the complement.
+          __shared__ double rho[CABS_MAX_K], qv[CABS_MAX_K], red[CABS_MAX_K];
+          __shared__ int slot_s[CABS_MAX_K], nslot, istar;
+          if (threadIdx.x == 0) {
+            bool sparse = counts[0] > 0;
+            for (int t2 = pairs; t2 < counts[1] && !sparse; ++t2) sparse = zcol[ncol[t2]] != 0;
+            int ns = 0;
+            if (sparse)
+              for (int t2 = pairs; t2 < counts[1]; ++t2) slot_s[ns++] = ncol[t2];
+            nslot = ns;
+          }
+          __syncthreads();
+          for (long long e = threadIdx.x; e < (long long)nslot * k; e += blockDim.x) {
+            const int t2 = (int)(e / k), i = (int)(e - (long long)t2 * k);
+            Uw[(size_t)slot_s[t2] * k + i] = 0.0;
+          }
+          __syncthreads();
+          if (nslot > 0) {
+            for (int i = threadIdx.x; i < k; i += blockDim.x) {
+              double r2 = 0.0;
+              for (int b2 = 0; b2 < k; ++b2) {
+                const double u = Uw[(size_t)b2 * k + i];  // zero columns add nothing
+                r2 = fma(u, u, r2);
+              }
+              rho[i] = r2;
+            }
+            __syncthreads();
+            for (int t2 = 0; t2 < nslot; ++t2) {
+              if (threadIdx.x == 0) {
+                int best = 0;
+                for (int i = 1; i < k; ++i)
+                  if (rho[i] < rho[best]) best = i;
+                istar = best;
+              }
+              __syncthreads();
+              const int is = istar;
+              for (int i = threadIdx.x; i < k; i += blockDim.x) {
+                double q = i == is ? 1.0 : 0.0;
+                for (int b2 = 0; b2 < k; ++b2) q = fma(-Uw[(size_t)b2 * k + is], Uw[(size_t)b2 * k + i], q);
+                qv[i] = q;
+                red[i] = q * q;
+              }
+              for (int i = k + threadIdx.x; i < CABS_MAX_K; i += blockDim.x) red[i] = 0.0;
+              __syncthreads();
+              for (int w2 = CABS_MAX_K / 2; w2 > 0; w2 >>= 1) {
+                for (int i = threadIdx.x; i < w2; i += blockDim.x) red[i] += red[i + w2];
+                __syncthreads();
+              }
+              const double inv = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 0.0;
+              const int j = slot_s[t2];
+              for (int i = threadIdx.x; i < k; i += blockDim.x) {
+                const double q = qv[i] * inv;
+                Uw[(size_t)j * k + i] = q;
+                rho[i] += q * q;
+              }
+              __syncthreads();
+            }
+          }
+        }
       }
       if (!grid_sync(a.bar, nb)) return;
       for (int x = blockIdx.x; x < tiles + tri; x += nb) {
@@ -732,6 +842,14 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           const double be = a.T[ji] + dj * Sij;
           f = (al * dj + be * di) / den;
           g = (al * di + be * dj) / den;
+          // A first-order correction this large means the two values are not
+          // yet separated by more than the error of the estimates (exactly
+          // repeated values differ only by rounding): orthogonalise the pair
+          // this time, as for equal values.
+          if (!(fabs(f) <= kMaxCorrB && fabs(g) <= kMaxCorrB)) {
+            f = 0.5 * Rij;
+            g = 0.5 * Sij;
+          }
         }
         local = fmax(local, fmax(fabs(f), fabs(g)));
       }

@@ -52,7 +52,7 @@ int main(void) {
   printf("cabs_cur_params %zu\ncabs_cur_result %zu\n", sizeof(cabs_cur_params), sizeof(cabs_cur_result));
   F(cabs_cur_params, kt) F(cabs_cur_params, seed) F(cabs_cur_params, prec) F(cabs_cur_params, trunc_rtol)
   F(cabs_cur_result, Ustar) F(cabs_cur_result, rows_t) F(cabs_cur_result, ranks)
-  F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma)
+  F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma) F(cabs_source, row_ptr) F(cabs_source, nnz)
   F(cabs_params, seed) F(cabs_params, upsilon_pow) F(cabs_params, trunc_rtol) F(cabs_params, flags)
   F(cabs_params, err_samples) F(cabs_params, err_seed)
   F(cabs_diag, e_rows) F(cabs_diag, e_follow_cols) F(cabs_diag, refine_final) F(cabs_diag, reserved) F(cabs_result, diag) F(cabs_result, err)

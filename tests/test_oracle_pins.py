@@ -195,3 +195,46 @@ def test_leverage_follow_up_sketch():
     assert len(set(r.cols.tolist())) == 6 and np.all(np.diff(r.cols) > 0)
     F = r.final
     assert np.allclose((F.U * F.S) @ F.V.T, A, atol=1e-8 * np.abs(A).max())
+
+
+def test_csr_source_matches_dense():
+    """The sparse source's gathers and entries (scipy's sparse slicing) equal
+    the dense source's on the densified matrix, bit for bit; rows with no
+    stored entries gather as zeros."""
+    from workloads import synth
+    ip, ix, v = synth.sparse_lowrank(300, 200, 0.03, rank=4, seed=3)
+    src = o.CSRSource(ip, ix, v, 200)
+    A = src.dense()
+    assert A.shape == (300, 200) and np.count_nonzero(A) == len(v)
+    dense = o.DenseSource(A)
+    g = np.random.default_rng(2)
+    rows = np.sort(g.choice(300, 17, replace=False))
+    cols = np.sort(g.choice(200, 13, replace=False))
+    for a, b in zip(src.gather(rows, cols), dense.gather(rows, cols)):
+        assert np.array_equal(a, b)
+    ii, jj = g.integers(0, 300, 500), g.integers(0, 200, 500)
+    assert np.array_equal(src.entries(ii, jj), dense.entries(ii, jj))
+    # sketches of the two sources agree exactly (same arithmetic downstream)
+    r1 = o.cabs(src, 12, 8, seed=5)
+    r2 = o.cabs(dense, 12, 8, seed=5)
+    assert np.array_equal(r1.rows, r2.rows) and np.array_equal(r1.cols, r2.cols)
+    assert np.array_equal(r1.final.U, r2.final.U)
+
+
+def test_sparse_error_identity():
+    """|A - L|^2 = |A|^2 - 2 <A, L>_stored + sum_pq S_p S_q (U^T U)_pq (V^T V)_pq,
+    the linear-cost form of the exact error for a sparse A, equals the dense
+    definition."""
+    from workloads import synth
+    ip, ix, v = synth.sparse_lowrank(150, 120, 0.05, rank=3, seed=8)
+    src = o.CSRSource(ip, ix, v, 120)
+    A = src.dense()
+    g = np.random.default_rng(4)
+    U, V, S = g.standard_normal((150, 6)), g.standard_normal((120, 6)), np.abs(g.standard_normal(6))
+    L = (U * S) @ V.T
+    rows = np.repeat(np.arange(150), np.diff(ip))
+    cross = np.sum(v.astype(np.float64) * L[rows, ix])
+    l2 = np.sum(np.outer(S, S) * (U.T @ U) * (V.T @ V))
+    num = np.sum(v.astype(np.float64) ** 2) - 2 * cross + l2
+    want = o.rel_fro_error_dense(A, U, S, V)
+    assert abs(np.sqrt(num / np.sum(A ** 2)) - want) < 1e-12 * want

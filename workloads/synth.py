@@ -16,6 +16,8 @@ configurations:
                         never stored; sigma = median distance over 1000 pairs.
 * ``decaying_lowrank``  A = U diag(s) V^T + N(0, noise_std^2), U and V
                         orthonormalised Gaussian, s_i = exp(-i / decay).
+* ``sparse_lowrank``    compressed-row sparse matrices like Table 1's sparse data
+                        (power-law row and column popularity, rank-r values).
 * ``batched_specs``     per-member (m, n, rank, k) for the batched workload.
 
 Random draws use numpy's Philox bit generator keyed by (seed, 3) on the host,
@@ -149,6 +151,50 @@ def sketch_factors(m: int, n: int, k: int, rank: int | None = None, seed: int = 
     if dup and r > 1:
         U[:, 1] = U[:, 0]
     return U, S, V
+
+
+def sparse_lowrank(m: int = 27000, n: int = 46000, density: float = 0.0056, rank: int = 20,
+                   seed: int = 1607, kind: str = "ratings", alpha: float = 0.5):
+    """A sparse matrix in compressed rows shaped like Table 1's sparse data:
+    "ratings" (27000 x 46000, 0.56 %: values on a 0.5-step scale from 0.5 to
+    5 around a rank-`rank` model) or "text" (18774 x 61188, 0.22 %: positive
+    log-normal weights scaled by a rank-`rank` non-negative model).
+
+    Row and column popularity follow power laws (weights (i + 1)^-alpha in a
+    random order), as rating and term counts do; each row draws its columns
+    with those weights, duplicates removed. Returns (indptr int64 m + 1,
+    indices int32 sorted within rows, data float32)."""
+    g = host_rng(seed, 6)
+    nnz_target = int(round(density * m * n))
+    rw = (np.arange(1, m + 1, dtype=np.float64) ** -alpha)[g.permutation(m)]
+    cw = (np.arange(1, n + 1, dtype=np.float64) ** -alpha)[g.permutation(n)]
+    deg = np.maximum(1, np.minimum(n // 2, np.round(rw / rw.sum() * nnz_target).astype(np.int64)))
+    pc = cw / cw.sum()
+    key = np.zeros(0, dtype=np.int64)
+    for _ in range(3):  # top rows up to their degree (repeated popular columns collapse)
+        have = np.bincount(key // n, minlength=m) if len(key) else np.zeros(m, dtype=np.int64)
+        need = np.maximum(deg - have, 0)
+        if need.sum() == 0:
+            break
+        r = np.repeat(np.arange(m, dtype=np.int64), need)
+        c = g.choice(n, size=len(r), p=pc).astype(np.int64)
+        key = np.sort(np.concatenate([key, r * n + c]))
+        key = key[np.r_[True, key[1:] != key[:-1]]]
+    rows, cols = key // n, key % n
+    U = g.standard_normal((m, rank)) / np.sqrt(rank)
+    V = g.standard_normal((n, rank))
+    base = np.empty(len(rows))
+    for s0 in range(0, len(rows), 1 << 20):
+        s1 = min(len(rows), s0 + (1 << 20))
+        base[s0:s1] = np.einsum("ij,ij->i", U[rows[s0:s1]], V[cols[s0:s1]])
+    if kind == "ratings":
+        vals = np.clip(np.round((3.5 + base + 0.5 * g.standard_normal(len(rows))) * 2) / 2, 0.5, 5.0)
+    else:
+        vals = np.exp(0.5 * g.standard_normal(len(rows))) * np.log1p(np.abs(base) + 1.0)
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(indptr, rows + 1, 1)
+    indptr = np.cumsum(indptr)
+    return indptr, cols.astype(np.int32), vals.astype(np.float32)
 
 
 def batched_specs(count: int = 512, seed: int = 1607, lo: int = 1000, hi: int = 20000,
