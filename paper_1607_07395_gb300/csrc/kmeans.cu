@@ -270,7 +270,7 @@ constexpr int kUMaxPerLane = CABS_MAX_K / 32;
 // per centre: per-chunk histograms, an offset table, a stable scatter, then
 // one CTA per centre over its own members only.
 
-constexpr int kSortChunk = 2048;  // points per histogram / scatter chunk
+constexpr int kSortChunk = 256;  // points per histogram / scatter chunk
 
 __global__ void __launch_bounds__(256) label_hist_kernel(const int* __restrict__ labels, long long M, int k2,
                                                          int* __restrict__ chunk_cnt) {

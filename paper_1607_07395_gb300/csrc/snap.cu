@@ -188,6 +188,33 @@ __global__ void __launch_bounds__(256) snap_merge_kernel(const T* __restrict__ c
 // all taken, every CTA scans its slice of rows for that centre (one warp per
 // row, lanes over dimensions), CTA 0 reduces the per-CTA minima in a fixed
 // order, and the walk continues. The taken-row bitmap lives in global memory.
+// Open-addressing set of taken rows (at most CABS_MAX_K of them) in shared
+// memory; -1 marks a free slot.
+constexpr int kTakenSlots = 4 * CABS_MAX_K;
+
+__device__ __forceinline__ unsigned taken_slot(int r) { return ((unsigned)r * 2654435761u) >> 22; }
+
+__device__ __forceinline__ bool taken_has(const int* set, int r) {
+  unsigned s = taken_slot(r);
+  for (int probe = 0; probe < kTakenSlots; ++probe, s = (s + 1) & (kTakenSlots - 1)) {
+    const int v = set[s];
+    if (v == r) return true;
+    if (v < 0) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void taken_add(int* set, int r) {
+  unsigned s = taken_slot(r);
+  for (int probe = 0; probe < kTakenSlots; ++probe, s = (s + 1) & (kTakenSlots - 1)) {
+    if (set[s] == r) return;
+    if (set[s] < 0) {
+      set[s] = r;
+      return;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
@@ -195,23 +222,34 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     int* __restrict__ sorted, int* fallbacks) {
   __shared__ T wd[kGreedyThreads / 32];
   __shared__ int wr[kGreedyThreads / 32];
+  // CTA 0's walk reads the candidate lists and the rows taken so far from
+  // shared memory: the lists are staged once, the taken rows (at most k2)
+  // live in an open-addressing set of kTakenSlots slots. The global bitmap is
+  // written too, for the CTAs' scans when a centre's list runs out.
+  __shared__ int s_top[CABS_MAX_K * kTop];
+  __shared__ int s_taken[kTakenSlots];
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
   for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < words; e += (long long)G * blockDim.x)
     taken[e] = 0u;
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < k2 * kTop; e += blockDim.x) s_top[e] = top_r[e];
+    for (int e = tid; e < kTakenSlots; e += blockDim.x) s_taken[e] = -1;
+  }
   if (!grid_sync(bar, G)) return;
   int j = 0;
   while (true) {
     if (blockIdx.x == 0 && wi == 0) {
       int jj = j;
       for (; jj < k2; ++jj) {
-        const int r = lane < kTop ? top_r[(size_t)jj * kTop + lane] : 0x7fffffff;
-        const bool ok = lane < kTop && r >= 0 && r < M && !((((volatile unsigned*)taken)[r >> 5] >> (r & 31)) & 1u);
+        const int r = lane < kTop ? s_top[jj * kTop + lane] : 0x7fffffff;
+        const bool ok = lane < kTop && r >= 0 && r < M && !taken_has(s_taken, r);
         const unsigned good = __ballot_sync(0xffffffffu, ok);
         if (!good) break;
         const int pick = __shfl_sync(0xffffffffu, r, __ffs(good) - 1);
         if (lane == 0) {
+          taken_add(s_taken, pick);
           taken[pick >> 5] |= 1u << (pick & 31);
           picks[jj] = pick;
         }
@@ -280,7 +318,10 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
           bv = cta_best[b];
           bi = cta_row[b];
         }
-      if (bi >= 0 && bi < M) taken[bi >> 5] |= 1u << (bi & 31);
+      if (bi >= 0 && bi < M) {
+        taken[bi >> 5] |= 1u << (bi & 31);
+        taken_add(s_taken, bi);
+      }
       picks[j] = bi;
       if (fallbacks) atomicAdd(fallbacks, 1);
       __threadfence();

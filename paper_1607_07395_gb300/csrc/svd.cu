@@ -675,20 +675,16 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
         // zero row of W is zero in every column the FP32 phase produces, so
         // without these the columns of U could not span R^k.
         if (blockIdx.x == 0) {
-          __shared__ int zrow[CABS_MAX_K], ncol[CABS_MAX_K], zcol[CABS_MAX_K], counts[2];
+          __shared__ int zrow[CABS_MAX_K], ncol[CABS_MAX_K], counts[2];
           {
-            // one warp per row of W and per column of U: all-zero tests by ballot
+            // one warp per row of W: all-zero test by ballot
             const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
             for (int i = threadIdx.x >> 5; i < k; i += nw) {
-              bool nzr = false, nzc = false;
-              for (int j = lane; j < k; j += 32) {
-                nzr |= a.W[(size_t)i * k + j] != 0.0;
-                nzc |= Uw[(size_t)i * k + j] != 0.0;
-              }
-              const bool anyr = __any_sync(0xffffffffu, nzr), anyc = __any_sync(0xffffffffu, nzc);
+              bool nzr = false;
+              for (int j = lane; j < k; j += 32) nzr |= a.W[(size_t)i * k + j] != 0.0;
+              const bool anyr = __any_sync(0xffffffffu, nzr);
               if (lane == 0) {
                 zrow[i] = anyr ? 0 : 1;
-                zcol[i] = anyc ? 0 : 1;
                 ncol[i] = a.d[i] > 3.814697265625e-06 * mx ? 0 : 1;
               }
             }
@@ -713,8 +709,8 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           // Null columns left over (the rank falls short of k by more than the
           // zero rows, e.g. through repeated nonzero rows) lie in the span of
           // the others or are zero, and the refinement cannot make them
-          // orthonormal. When W has zero rows or U exactly zero columns (the
-          // sparse regime) they are all replaced by Gram-Schmidt: each takes
+          // orthonormal. When W has zero rows (the sparse regime) they are all
+          // replaced by Gram-Schmidt: each takes
           // e_i for the row i least covered by the columns so far (smallest
           // rho_i = sum_b U_ib^2, so |e_i - proj|^2 = 1 - rho_i >= 1 - r / k
           // > 0), minus its projection. Elsewhere the noise columns keep their
@@ -722,8 +718,10 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           __shared__ double rho[CABS_MAX_K], qv[CABS_MAX_K], red[CABS_MAX_K];
           __shared__ int slot_s[CABS_MAX_K], nslot, istar;
           if (threadIdx.x == 0) {
-            bool sparse = counts[0] > 0;
-            for (int t2 = pairs; t2 < counts[1] && !sparse; ++t2) sparse = zcol[ncol[t2]] != 0;
+            // only zero rows keep U from spanning R^k; exactly zero columns of
+            // W alone (a zero-padded block) leave the kept columns spanning
+            // the range of W exactly, and the refinement handles the rest
+            const bool sparse = counts[0] > 0;
             int ns = 0;
             if (sparse)
               for (int t2 = pairs; t2 < counts[1]; ++t2) slot_s[ns++] = ncol[t2];
