@@ -1,24 +1,18 @@
 // Steps a3 / a4 / a8 -- the sketching routine of Section 4.1 and the pilot
 // embedding of Algorithm 2, step 2.
 //
-//  1. FP64 SVD W = U_w Sigma_w V_w^T (one-sided Jacobi, Hestenes form): the
-//     columns of W are rotated pairwise until mutually orthogonal; the
-//     accumulated rotations give V_w, the column norms Sigma_w, the normalised
-//     columns U_w. Pairs follow the round-robin (circle) schedule so the k/2
-//     pairs of a round are independent and run on different warps. The sweep
-//     stops when no pair has |w_p . w_q| > 1e-15 |w_p| |w_q|.
+//  1. SVD W = U_w Sigma_w V_w^T to FP64 accuracy (svd.cu: FP32 one-sided
+//     Jacobi on a thread-block cluster, then an FP64 refinement spread over
+//     the GPU).
 //  2. Truncation: keep sigma_i > max(trunc_rtol, k 2^-52) sigma_1; dropped
 //     components get zero columns in U_w and V_w, hence zero factors and S.
 //  3. Extrapolation a = C V_w (m x k), b = Rt U_w (n x k) on CUDA cores, in
 //     the working precision; each CTA also writes the FP64 sum of squares of
-//     its tile's columns, and the norms N_c, N_r are summed in a fixed order
-//     (deterministic).
+//     its tile's columns, and the norms N_c, N_r are reduced by one CTA per
+//     column in a fixed order (deterministic).
 //  4. Scale: S_i = N_c,i N_r,i / sigma_i (pseudo-skeleton C W^+ R, Eq. W) or
 //     S_i = sigma_i sqrt(mn)/k (stabilised form); the factors are
 //     U = a N_c^-1, V = b N_r^-1, or the embeddings P = U S^1/2, Q = V S^1/2.
-//
-// FP64 throughput on this part is 1/64 of FP32, so the SVD dominates for
-// large k; it is written for correctness first (one CTA per matrix).
 #include "common.cuh"
 #include "kernels.cuh"
 #include "profile.cuh"

@@ -15,10 +15,10 @@
 //         warp-shuffle reduction over the 32 lanes that share a point row.
 //   TF32/BF16: tensor-core contraction (separate kernel file), with near ties
 //         re-checked in FP32.
-// Update kernel: one CTA per centre; each of its 16 warps scans a fixed slice
-// of the labels (four loads in flight) and sums its members in index order;
-// the warp sums are added in a fixed order, so the centres do not depend on
-// scheduling.
+// Update: a stable counting sort of the labels lists each centre's members in
+// index order; four CTAs per centre sum contiguous parts of that list (16
+// warps each, warp sums in warp order) and a combine kernel adds the parts in
+// order, so the centres do not depend on scheduling.
 // Energies (weighted encoding errors) are per-CTA FP64 partials summed in a
 // fixed order.
 #include "common.cuh"
