@@ -39,11 +39,22 @@ def members(C):
     X, Y, sig = synth.rbf_mixture(4000, 3500, d=16, components=20, seed=3)
     out.append((C.rbf_source(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), sig),
                 C.make_params(4000, 3500, 48, iters=5, seed=7, prec="fp32")))
+    # the Section 5 variants, the SVD form and a sparse source with its exact error
+    A, _, _, _ = synth.decaying_lowrank_host(2500, 1800, rank=50, seed=21)
+    Ad = torch.from_numpy(A).cuda()
+    out.append((C.dense_source(Ad), C.make_params(2500, 1800, 40, iters=3, seed=31, prec="bf16",
+                                                  flags=C.FLAG_SVD_FORM)))
+    out.append((C.dense_source(Ad), C.make_params(2500, 1800, 40, 24, iters=3, seed=32, prec="fp32",
+                                                  flags=C.FLAG_LEVERAGE)))
+    ip, ix, v = synth.sparse_lowrank(3000, 2500, 0.02, rank=8, seed=5)
+    csr = C.csr_source(torch.from_numpy(ip).cuda(), torch.from_numpy(ix).cuda(), torch.from_numpy(v).cuda())
+    out.append((csr, C.make_params(3000, 2500, 48, iters=4, seed=33, prec="bf16", flags=C.FLAG_HARD_THRESHOLD,
+                                   err_samples=0)))
     return out
 
 
 def host(sk):
-    return [t.cpu().numpy() for t in (sk.U, sk.S, sk.V, sk.rows, sk.cols, sk.pilot_rows, sk.pilot_cols)]
+    return [t.cpu().numpy() for t in (sk.U, sk.S, sk.V, sk.rows, sk.cols, sk.pilot_rows, sk.pilot_cols, sk.err)]
 
 
 def same(a, b):
@@ -73,9 +84,11 @@ def test_batched_bit_identical_to_alone(ctx, C, use_graph, lanes):
 
 
 def test_serving_mix_equals_alone_and_overlaps(ctx, C):
-    mem = members(C) * 3
+    base = members(C)
+    nb = len(base)
+    mem = base * 3
     alone = {}
-    for i, (src, p) in enumerate(mem[:6]):
+    for i, (src, p) in enumerate(base):
         alone[i] = host(C.cabs_sketch(ctx, src, p))
     torch.cuda.synchronize()
     # an arena that cannot hold every request at once: admission must queue
@@ -86,7 +99,7 @@ def test_serving_mix_equals_alone_and_overlaps(ctx, C):
 
         def client():
             for i, (src, p) in enumerate(mem):
-                tickets.append((i % 6, srv.submit(src, p)))
+                tickets.append((i % nb, srv.submit(src, p)))
                 time.sleep(0.0005)
 
         th = threading.Thread(target=client)
