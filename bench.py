@@ -905,8 +905,8 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp32", "tf32", "bf16", "fp64"])
     ap.add_argument("--form", default="batched", choices=["batched", "plain"],
                     help="batched: --batch concurrent sketches per step over --lanes streams (captured graph)")
-    ap.add_argument("--batch", type=int, default=4)
-    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lanes", type=int, default=8)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--m", type=int, default=0, help="override the workload's rows (profiler captures)")
     ap.add_argument("--n", type=int, default=0, help="override the workload's columns (profiler captures)")

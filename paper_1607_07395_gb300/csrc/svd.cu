@@ -8,7 +8,11 @@
 //    run to convergence. For k <= 64 one CTA holds W and V in shared memory
 //    and processes the k/2 disjoint pairs of each round-robin round on its
 //    warps. For larger k a thread-block cluster holds the columns in the
-//    shared memories of its CTAs: each CTA owns two blocks of columns, rotates
+//    shared memories of its CTAs, and the Jacobi starts from X = W Q, V = Q
+//    with W^T = Q R (a blocked Householder QR across the cluster), so that
+//    X = R^T: this preconditioning cuts the sweeps by a third to a half
+//    (a W with zero rows starts from W itself). Each
+//    CTA owns two blocks of columns, rotates
 //    every pair across them (and, once per sweep, the pairs inside them), then
 //    the blocks move one step along the round-robin circle through distributed
 //    shared memory; one cluster barrier per round, double-buffered. In the
@@ -55,6 +59,7 @@ constexpr int kMaxSweepsA = 40;
 constexpr int kItersB = 8;
 constexpr double kMaxCorrB = 0.05;      // Phase B: larger first-order corrections are deferred
 constexpr double kConvB = 1e-8;         // Phase B: last iteration when max |F_ij|, |G_ij| (i != j) < this
+constexpr double kCloseOffB = 1e-13;    // ... and |T_ij| < this max |d| for every pair left undiagonalised
 constexpr int kNotDone = 0x7fffffff;
 
 __device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& q) {
@@ -292,6 +297,31 @@ __device__ __forceinline__ void emit_column(const float* w, const float* v, int 
   }
 }
 
+// Preconditioning QR (below): the panel of CTA p is its two blocks, top
+// then bottom, i.e. panel positions 2 b p + t, t < 2 b. Position -> column of
+// W^T (a row of W); >= k (or past the 2 NC blocks) is padding.
+__device__ __forceinline__ int panel_col(int pos, int b, int NC) {
+  const int pw = 2 * b, P = pos / pw, t = pos - P * pw;
+  if (P >= NC) return 0x7fffffff;
+  return (t < b ? P : 2 * NC - 1 - P) * b + (t < b ? t : t - b);
+}
+
+// emit_column for a W column whose rows are panel positions (the
+// preconditioned cluster kernel): row pos of w is row panel_col(pos) of U0.
+__device__ __forceinline__ void emit_column_perm(const float* w, const float* v, int k, int kp, int b, int NC, int gc,
+                                                 int lane, double* U0, double* V0) {
+  float a = 0.f;
+  for (int i = lane; i < kp; i += 32) a = fmaf(w[i], w[i], a);
+  a = warp_sum(a);
+  const float nrm = sqrtf(a);
+  const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+  for (int pos = lane; pos < kp; pos += 32) {
+    const int r = panel_col(pos, b, NC);
+    if (r < k) U0[(size_t)gc * k + r] = (double)(w[pos] * inv);
+  }
+  for (int i = lane; i < k; i += 32) V0[(size_t)gc * k + i] = (double)v[i];
+}
+
 // ---------------------------------------------------------- Phase A, 1 CTA
 
 __global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict__ W, int k, double* __restrict__ U0,
@@ -339,13 +369,162 @@ __global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict
 constexpr int kClusterThreads = 512;
 constexpr int kMaxBlkRot = 16;  // columns per block (b) the cluster kernel supports
 
+// Householder QR of one panel of pw = 2 b <= 32 columns held in shared
+// memory (the block at base, then the one at base + blk; kp = 32 R rows, b
+// columns each, the top block's real columns ntop). The real columns take the
+// diagonal rows row0, row0 + 1, ... in panel order (padding columns are zero
+// and take none), so the k real columns of W^T P use rows 0 ... k - 1 once
+// each. Warp w keeps columns w and w + 16 in registers (lane l owns rows
+// l + 32 i). Step t: the warp holding column t forms v from its rows >= row0
+// + t (alpha = -sign(x0) |x|, v0 = x0 - alpha, beta = 2 / v^T v = -1 /
+// (alpha v0)), stores v (zero above the diagonal) and beta for the other
+// CTAs, and every later column takes y <- y - beta (v^T y) v. A remaining
+// squared norm at or below 1e-36 (where beta would overflow) gives beta = 0
+// and no reflection. On return each column holds R's column: the entries
+// above the diagonal, alpha on it, zeros below.
+template <int R>
+__device__ void factor_panel(float* base, int b, size_t blk, int row0, int ntop, float* vout, float* beta, int warp,
+                             int lane) {
+  constexpr int kp = 32 * R;
+  const int pw = 2 * b;
+  auto col = [&](int t) { return base + (t < b ? (size_t)t * kp : blk + (size_t)(t - b) * kp); };
+  float xr[2][R];
+  const int nloc = (warp < pw ? 1 : 0) + (warp + 16 < pw ? 1 : 0);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (h < nloc)
+#pragma unroll
+      for (int i = 0; i < R; ++i) xr[h][i] = col(warp + 16 * h)[lane + 32 * i];
+  for (int t = 0; t < pw; ++t) {
+    const int row = t < b ? row0 + t : row0 + ntop + (t - b);
+    if (warp == (t & 15)) {
+      const int h = t >> 4;
+      float x[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) x[i] = h == 0 ? xr[0][i] : xr[1][i];
+      float sq = 0.f, x0l = 0.f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = lane + 32 * i;
+        if (r >= row) sq = fmaf(x[i], x[i], sq);
+        if (r == row) x0l = x[i];
+      }
+      sq = warp_sum(sq);
+      const float x0 = __shfl_sync(0xffffffffu, x0l, row & 31);
+      float al = x0, be = 0.f, v0 = 0.f;
+      if (sq > 1e-36f) {
+        al = -copysignf(sqrtf(sq), x0);
+        v0 = x0 - al;  // |x0| + |alpha|: no cancellation
+        be = -1.f / (al * v0);
+      }
+      float* v = vout + (size_t)t * kp;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = lane + 32 * i;
+        v[r] = (be == 0.f || r < row) ? 0.f : (r == row ? v0 : x[i]);
+        x[i] = r < row ? x[i] : (r == row ? al : 0.f);
+      }
+      if (lane == 0) beta[t] = be;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        if (h == 0) xr[0][i] = x[i];
+        else xr[1][i] = x[i];
+      }
+    }
+    __syncthreads();
+    const float be = beta[t];
+    if (be != 0.f) {
+      const float* v = vout + (size_t)t * kp;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h < nloc && warp + 16 * h > t) {
+          float vr[R], d = 0.f;
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            vr[i] = v[lane + 32 * i];
+            d = fmaf(vr[i], xr[h][i], d);
+          }
+          d = warp_sum(d) * be;
+#pragma unroll
+          for (int i = 0; i < R; ++i) xr[h][i] = fmaf(-d, vr[i], xr[h][i]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (h < nloc)
+#pragma unroll
+      for (int i = 0; i < R; ++i) col(warp + 16 * h)[lane + 32 * i] = xr[h][i];
+}
+
+// y <- H_{pw-1} ... H_0 y for a panel's reflectors (v zero above its
+// diagonal, so no masks); y (32 R rows) in registers, lane l owning rows
+// l + 32 i.
+// Two columns at a time (y2 may be null), so that their reductions overlap.
+template <int R>
+__device__ __forceinline__ void apply_panel(const float* V, const float* beta, int pw, float* y1, float* y2,
+                                            int lane) {
+  constexpr int kp = 32 * R;
+  float yr[R], zr[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    yr[i] = y1[lane + 32 * i];
+    zr[i] = y2 ? y2[lane + 32 * i] : 0.f;
+  }
+  for (int t = 0; t < pw; ++t) {
+    const float be = beta[t];
+    if (be == 0.f) continue;
+    const float* v = V + (size_t)t * kp;
+    float vr[R], d = 0.f, e = 0.f;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      vr[i] = v[lane + 32 * i];
+      d = fmaf(vr[i], yr[i], d);
+      e = fmaf(vr[i], zr[i], e);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, off);
+      e += __shfl_xor_sync(0xffffffffu, e, off);
+    }
+    d *= be;
+    e *= be;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      yr[i] = fmaf(-d, vr[i], yr[i]);
+      zr[i] = fmaf(-e, vr[i], zr[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    y1[lane + 32 * i] = yr[i];
+    if (y2) y2[lane + 32 * i] = zr[i];
+  }
+}
+
 // Cluster of NC CTAs; CTA c holds blocks top[c], bot[c] of b columns each.
 // Round-robin over the 2 NC blocks: block slot top[0] stays, the others move
 // one place around the circle each round.
+//
+// Preconditioning: the Jacobi does not start from W itself but from X = W Q,
+// V = Q, where W^T = Q R is a Householder QR; then X = R^T, lower triangular.
+// One-sided Jacobi then gives X J = U Sigma, i.e. W = U Sigma (Q J)^T: the same
+// outputs as before (U from the normalised columns, V accumulated), in fewer
+// sweeps, since the Gram matrix of R^T, R R^T, is much nearer to diagonal
+// than W^T W = R^T R (about 10 sweeps instead of 15 to 19 on the sketching
+// workloads). The QR runs blocked over the cluster: the owner of panel p
+// factors its b columns of W^T, one cluster barrier, and every CTA applies
+// the panel's reflectors to its later columns of W^T and to all its columns
+// of Y = Q^T (started at I). R^T and Q = Y^T are then scattered into the
+// other buffer through distributed shared memory. A W with zero rows (sparse
+// inputs) starts from W itself: its QR turns exact zeros into rounding noise,
+// and there the preconditioned Jacobi needed more sweeps, not fewer.
 template <int R>
 __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const double* __restrict__ W, int k, int b,
                                                                         double* __restrict__ U0,
-                                                                        double* __restrict__ V0, int* sweeps_out) {
+                                                                        double* __restrict__ V0, float* __restrict__ qr,
+                                                                        int* sweeps_out) {
   constexpr int kp = 32 * R;  // padded column length
   cg::cluster_group cluster = cg::this_cluster();
   const int NC = (int)cluster.num_blocks();
@@ -359,28 +538,134 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   __shared__ int rot_flag[2];
   __shared__ float2 rot_cs[kMaxBlkRot][kMaxBlkRot];  // (c, s) of step s, pair j
   __shared__ float bnorm[kMaxBlkRot];                 // squared norms of the bottom block's columns
+  __shared__ float own_beta[2 * kMaxBlkRot];          // my panel's reflectors' beta
+  __shared__ float st_beta[2 * kMaxBlkRot];           // beta of the panel being applied
+  __shared__ int zero_row;                            // one of my columns of W^T is zero
+  float* own = cs + 8 * blk;                          // my panel's reflectors (2 b columns)
+  float* stage = cs + 10 * blk;                       // another CTA's panel, being applied
+  const int pw = 2 * b;                               // panel width
+  // real columns of block B, and the first diagonal row of my panel
+  auto nreal = [&](int B) { return max(0, min(b, k - B * b)); };
+  int my_row0 = 0;
+  for (int P = 0; P < c; ++P) my_row0 += nreal(P) + nreal(2 * NC - 1 - P);
   // CTA c starts with blocks c (top) and 2 NC - 1 - c (bottom). Block 0 stays;
   // the other 2 NC - 1 move one place around the circle per round, so after
   // the 2 NC - 1 rounds of a sweep every block is back where it started and
   // every pair of blocks has met once.
-  const int ids[2] = {c, 2 * NC - 1 - c};
+  const int id_top = c, id_bot = 2 * NC - 1 - c;
   if (tid < 2) rot_flag[tid] = 0;
+  if (tid == 0) zero_row = 0;
   __syncthreads();
-  // load my two blocks into buf0
+  // buf0 <- my two blocks of W^T and of Y = I; buf1 <- 0 (R^T and Q land there)
   for (int slot = 0; slot < 2; ++slot) {
-    const int B = ids[slot];
+    const int B = slot == 0 ? id_top : id_bot;
     float* w = buf0 + slot * blk;
     float* v = buf0 + (2 + slot) * blk;
     for (int e = tid; e < (int)blk; e += blockDim.x) {
       const int j = e / kp, i = e - j * kp;
       const int gc = B * b + j;
-      w[e] = (gc < k && i < k) ? (float)W[(size_t)i * k + gc] : 0.f;
+      w[e] = (gc < k && i < k) ? (float)W[(size_t)gc * k + i] : 0.f;
       v[e] = (gc < k && i == gc) ? 1.f : 0.f;
     }
   }
+  for (int e = tid; e < (int)(4 * blk); e += blockDim.x) buf1[e] = 0.f;
+  __syncthreads();
+  // W with zero rows (sparse inputs): W^T is then rank-deficient with exact
+  // zeros that the QR would turn into rounding noise, and the Jacobi on R^T
+  // needs more sweeps than on W itself, so those start from W, V = I.
+  for (int t = warp; t < 2 * b; t += nwarps) {
+    const int slot = t / b, j = t - slot * b;
+    const int gc = (slot == 0 ? id_top : id_bot) * b + j;
+    if (gc >= k) continue;
+    const float* col = buf0 + slot * blk + (size_t)j * kp;
+    bool nz = false;
+    for (int i = lane; i < k; i += 32) nz |= col[i] != 0.f;
+    if (!__any_sync(0xffffffffu, nz) && lane == 0) zero_row = 1;
+  }
   cluster.sync();
-  float* cur = buf0;
-  float* nxt = buf1;
+  int any_zero_row = 0;
+  for (int r = 0; r < NC; ++r) any_zero_row |= *cluster.map_shared_rank(&zero_row, r);
+  const bool precondition = any_zero_row == 0;
+  if (!precondition) {
+    for (int slot = 0; slot < 2; ++slot) {
+      const int B = slot == 0 ? id_top : id_bot;
+      float* w = buf0 + slot * blk;
+      for (int e = tid; e < (int)blk; e += blockDim.x) {
+        const int j = e / kp, i = e - j * kp;
+        const int gc = B * b + j;
+        w[e] = (gc < k && i < k) ? (float)W[(size_t)i * k + gc] : 0.f;
+      }
+    }
+  }
+  // Householder QR of W^T P, panel p = CTA p's two blocks (positions
+  // p pw ... p pw + pw - 1). The owner factors its panel and publishes the
+  // reflectors through global memory (read back from L2 by every CTA: one
+  // SM's shared memory serving 15 readers was the bottleneck).
+  for (int p = 0; p < (precondition ? NC : 0); ++p) {
+    float* gv = qr + (size_t)p * pw * kp;
+    float* gb = qr + (size_t)NC * pw * kp + (size_t)p * pw;
+    if (c == p) {
+      factor_panel<R>(buf0, b, blk, my_row0, nreal(c), own, own_beta, warp, lane);
+      const float4* src = (const float4*)own;
+      float4* dst = (float4*)gv;
+      for (int e = tid; e < (int)(2 * blk / 4); e += blockDim.x) dst[e] = src[e];
+      if (tid < pw) gb[tid] = own_beta[tid];
+    }
+    cluster.sync();
+    const float* Vp = own;
+    const float* bp = own_beta;
+    if (c != p) {
+      const float4* src = (const float4*)gv;
+      float4* dst = (float4*)stage;
+      const int n4 = (int)(2 * blk / 4);
+      for (int e = tid; e < n4; e += 2 * blockDim.x) {
+        const float4 x0 = __ldcg(src + e);
+        const bool two = e + (int)blockDim.x < n4;
+        const float4 x1 = two ? __ldcg(src + e + blockDim.x) : x0;
+        dst[e] = x0;
+        if (two) dst[e + blockDim.x] = x1;
+      }
+      if (tid < pw) st_beta[tid] = __ldcg(gb + tid);
+      __syncthreads();
+      Vp = stage;
+      bp = st_beta;
+    }
+    // my columns of W^T if my panel comes later, and all my columns of Y:
+    // list entry t < pw is W^T column t, t >= pw is Y column t - pw
+    const int first = c > p ? 0 : pw;
+    const int ncols = 2 * pw - first;
+    for (int t = warp; t < ncols; t += 2 * nwarps) {
+      const int t1 = first + t, t2 = t + nwarps < ncols ? t1 + nwarps : -1;
+      float* y1 = buf0 + (size_t)(t1 / b) * blk + (size_t)(t1 % b) * kp;
+      float* y2 = t2 >= 0 ? buf0 + (size_t)(t2 / b) * blk + (size_t)(t2 % b) * kp : nullptr;
+      apply_panel<R>(Vp, bp, pw, y1, y2, lane);
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  // scatter X = R^T (X[pos, i] = R[i, pos], i <= pos, pos = my panel
+  // positions) and Q = Y^T (Q[gc, i] = Y[i, gc]) into buf1 of the owners of
+  // column i
+  for (int t = warp; t < (precondition ? pw : 0); t += nwarps) {
+    const int slot = t / b, j = t - slot * b;
+    const int gc = (slot == 0 ? id_top : id_bot) * b + j;
+    if (gc >= k) continue;
+    const int pos = c * pw + t;
+    const int prow = t < b ? my_row0 + t : my_row0 + nreal(c) + (t - b);  // its diagonal row
+    const float* wcol = buf0 + slot * blk + (size_t)j * kp;
+    const float* ycol = buf0 + (2 + slot) * blk + (size_t)j * kp;
+    for (int i = lane; i < k; i += 32) {
+      const int Bi = i / b, ji = i - Bi * b;
+      const int dr = Bi < NC ? Bi : 2 * NC - 1 - Bi;
+      const int ds = Bi < NC ? 0 : 1;
+      float* dst = cluster.map_shared_rank(buf1, dr);
+      if (i <= prow) dst[(size_t)ds * blk + (size_t)ji * kp + pos] = wcol[i];
+      dst[(size_t)(2 + ds) * blk + (size_t)ji * kp + gc] = ycol[i];
+    }
+  }
+  cluster.sync();
+  float* cur = precondition ? buf1 : buf0;
+  float* nxt = precondition ? buf0 : buf1;
   int sweep = 0;
   bool conv = false;
   while (!conv && sweep < kMaxSweepsA) {
@@ -483,8 +768,13 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
   // write out my two blocks (back at their starting places after whole sweeps)
   for (int slot = 0; slot < 2; ++slot) {
     for (int j = warp; j < b; j += nwarps) {
-      const int gc = ids[slot] * b + j;
-      if (gc < k) emit_column(cur + slot * blk + (size_t)j * kp, cur + (2 + slot) * blk + (size_t)j * kp, k, gc, lane, U0, V0);
+      const int gc = (slot == 0 ? id_top : id_bot) * b + j;
+      if (gc >= k) continue;
+      if (precondition)
+        emit_column_perm(cur + slot * blk + (size_t)j * kp, cur + (2 + slot) * blk + (size_t)j * kp, k, kp, b, NC, gc,
+                         lane, U0, V0);
+      else
+        emit_column(cur + slot * blk + (size_t)j * kp, cur + (2 + slot) * blk + (size_t)j * kp, k, gc, lane, U0, V0);
     }
   }
   if (c == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
@@ -498,7 +788,7 @@ constexpr int kGT = 16, kGK = 16;
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 __global__ void svd_flags_init_kernel(unsigned long long* maxoff, int iters, int* done_iter, GridBarrier* bar) {
-  if (threadIdx.x < iters) maxoff[threadIdx.x] = 0ull;
+  if (threadIdx.x < 2 * iters) maxoff[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
     *done_iter = kNotDone;
     bar->count = 0u;
@@ -602,6 +892,7 @@ struct RefineArgs {
   int* done_iter;
   GridBarrier* bar;
   int* status;
+  double keep_rtol;  // values at or below keep_rtol max |d| are truncated afterwards
 };
 
 // Phase B in one launch: every iteration's GEMMs are spread over the CTAs as
@@ -818,7 +1109,8 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     __syncthreads();
     if (blockIdx.x == 0)
       for (int i = threadIdx.x; i < k; i += blockDim.x) a.d[i] = dsh[i];
-    double local = 0.0;
+    double local = 0.0, lclose = 0.0;
+    const double keep2 = a.keep_rtol * a.keep_rtol * dmax2;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
          e += (long long)nb * blockDim.x) {
       const int j = (int)(e / k), i = (int)(e - (long long)j * k);
@@ -835,6 +1127,22 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
         if (fabs(den) <= 1e-13 * dmax2) {
           f = 0.5 * Rij;
           g = 0.5 * Sij;
+          double res = fabs(a.T[ij]);
+          const double db = 0.5 * (di + dj);
+          if (db * db > 1e-13 * dmax2) {
+            // A repeated value: any rotation of the pair's U and V columns
+            // together is as good, but U and V may still differ by one, which
+            // leaves the block d [[1, -t], [t, 1]]. Splitting the rotation
+            // t / 2 onto U and -t / 2 onto V (the first-order conditions with
+            // d_i = d_j) removes it; what stays is the symmetric part.
+            const double rot = (a.T[ij] - a.T[ji]) / (4.0 * db);
+            if (fabs(rot) <= kMaxCorrB) {
+              f += rot;
+              g -= rot;
+              res = 0.5 * fabs(a.T[ij] + a.T[ji]);
+            }
+          }
+          if (fmax(di * di, dj * dj) > keep2) lclose = fmax(lclose, res);
         } else {
           const double al = a.T[ij] + dj * Rij;
           const double be = a.T[ji] + dj * Sij;
@@ -847,6 +1155,7 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           if (!(fabs(f) <= kMaxCorrB && fabs(g) <= kMaxCorrB)) {
             f = 0.5 * Rij;
             g = 0.5 * Sij;
+            if (fmax(di * di, dj * dj) > keep2) lclose = fmax(lclose, fabs(a.T[ij]));
           }
         }
         local = fmax(local, fmax(fabs(f), fabs(g)));
@@ -855,7 +1164,9 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
       a.G[ij] = g;
     }
     local = warp_max(local);
+    lclose = warp_max(lclose);
     if ((threadIdx.x & 31) == 0 && local > 0.0) atomicMax(a.maxoff + t, dbits(local));
+    if ((threadIdx.x & 31) == 0 && lclose > 0.0) atomicMax(a.maxoff + kItersB + t, dbits(lclose));
     if (!grid_sync(a.bar, nb)) return;
     for (int x = blockIdx.x; x < 2 * tiles; x += nb) {
       const int which = x / tiles, y = x - which * tiles;
@@ -867,8 +1178,15 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     // the pairs that still rotate); at m < kConvB that is below the FP64
     // rounding floor and no verifying iteration is needed. Or a plateau at the
     // rounding floor (clustered values whose corrections stop shrinking).
+    // Pairs that kept only the orthogonality correction (values closer than
+    // the estimates' resolution, or not yet separated) are not diagonalised
+    // by the update, so their |T_ij| must already be at the rounding level:
+    // otherwise (a block of tiny values that the FP32 phase could not
+    // resolve) the iteration has not converged and the FP64 Jacobi takes over.
+    // Pairs whose values are both truncated afterwards do not count.
     const double m = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + t));
-    const bool conv = m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev);
+    const double mc = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + kItersB + t));
+    const bool conv = (m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev)) && mc <= kCloseOffB * sqrt(dmax2);
     prev = m;
     if (!grid_sync(a.bar, nb)) return;
     if (conv) {
@@ -1130,13 +1448,16 @@ SvdWs carve_svd(Carve& cv, int k) {
   w.F = cv.take<double>(kk);
   w.G = cv.take<double>(kk);
   w.d = cv.take<double>(k);
-  w.maxoff = cv.take<unsigned long long>(kItersB);
+  w.maxoff = cv.take<unsigned long long>(2 * kItersB);
   w.done_iter = cv.take<int>(1);
   w.pos = cv.take<int>(k);
   w.rank_tmp = cv.take<int>(1);
   w.bar = cv.take<GridBarrier>(1);
   w.Wc = cv.take<double>(kk);
   w.Vc = cv.take<double>(kk);
+  // the preconditioning QR's reflectors: <= k + 31 panel positions of
+  // kp <= 256 rows (kp = 128 up to k = 128), and their betas
+  w.qr = cv.take<float>((size_t)(k + 32) * (k <= 128 ? 128 : 256) + (k + 32));
   return w;
 }
 
@@ -1145,12 +1466,13 @@ SvdWs carve_svd(Carve& cv, int k) {
 #endif
 
 template <int R>
-static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0, int* sweeps, cudaStream_t stream) {
+static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0, float* qr, int* sweeps,
+                                  cudaStream_t stream) {
   static int nc = -1;  // cluster size actually schedulable on this device
   const int want = CABS_SVD_CLUSTER;
   auto smem_for = [&](int c) {
     int b = (k + 2 * c - 1) / (2 * c);
-    return (size_t)8 * b * 32 * R * sizeof(float);
+    return (size_t)12 * b * 32 * R * sizeof(float);  // 2 x 4 blocks + 2 panels of reflectors
   };
   if (nc < 0) {
     nc = 8;
@@ -1195,7 +1517,7 @@ static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  CABS_LAUNCH(stream, "svd32_cluster_kernel", cudaLaunchKernelEx(&cfg, svd32_cluster_kernel<R>, W, k, b, U0, V0, sweeps));
+  CABS_LAUNCH(stream, "svd32_cluster_kernel", cudaLaunchKernelEx(&cfg, svd32_cluster_kernel<R>, W, k, b, U0, V0, qr, sweeps));
   return CABS_OK;
 }
 
@@ -1209,9 +1531,9 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
     CABS_LAUNCH(stream, "svd32_cta_kernel",
                 svd32_cta_kernel<<<1, 512, smem, stream>>>(W, k, w.U[0], w.V[0], sweeps));
   } else if (k <= 128) {
-    CABS_TRY(launch_cluster<4>(W, k, w.U[0], w.V[0], sweeps, stream));
+    CABS_TRY(launch_cluster<4>(W, k, w.U[0], w.V[0], w.qr, sweeps, stream));
   } else {
-    CABS_TRY(launch_cluster<8>(W, k, w.U[0], w.V[0], sweeps, stream));
+    CABS_TRY(launch_cluster<8>(W, k, w.U[0], w.V[0], w.qr, sweeps, stream));
   }
   // ---- Phase B: FP64 refinement, one cooperative launch
   CABS_LAUNCH(stream, "svd_flags_init",
@@ -1223,7 +1545,7 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_persistent_kernel, 256, 0);
     const int grid = std::max(1, std::min(tiles, coop_grid_cap(sm_count() * std::max(per_sm, 1))));
     RefineArgs ra{k, W, w.U[0], w.U[1], w.V[0], w.V[1], w.P, w.T, w.UtU, w.VtV, w.F, w.G, w.d, w.maxoff,
-                  w.done_iter, w.bar, status};
+                  w.done_iter, w.bar, status, std::max(trunc_rtol, (double)k * 2.220446049250313e-16)};
     void* args[] = {&ra};
     CABS_LAUNCH(stream, "refine_persistent_kernel",
                 cudaLaunchCooperativeKernel((const void*)refine_persistent_kernel, dim3(grid), dim3(256), args, 0,

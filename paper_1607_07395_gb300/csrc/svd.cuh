@@ -10,11 +10,12 @@ struct SvdWs {
   double *U[2], *V[2];                 // column-major iterates
   double *P, *T, *UtU, *VtV, *F, *G;   // k x k scratch
   double* d;                           // current singular value estimates
-  unsigned long long* maxoff;          // per-iteration max |F|, |G| (as ordered bits)
+  unsigned long long* maxoff;          // per-iteration max |F|, |G| (i != j), then max |T_ij| over pairs kept undiagonalised (as ordered bits)
   int* done_iter;                      // first converged iteration, or INT_MAX
   int *pos, *rank_tmp;                 // descending position of each value; kept rank
   GridBarrier* bar;
   double *Wc, *Vc;                     // FP64 Jacobi fallback scratch
+  float* qr;                           // FP32 phase: preconditioning QR reflectors
 };
 
 SvdWs carve_svd(Carve& cv, int k);
