@@ -231,7 +231,8 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   double* Vw = d_Vw ? d_Vw : w.Vw;
   int* rank = d_rank ? d_rank : w.rank;
   int* sweeps = d_sweeps ? d_sweeps : w.sweeps;
-  CABS_TRY(launch_svd(W, k, trunc_rtol, sig, Uw, Vw, rank, sweeps, d_refine, d_status, w.svd, stream));
+  CABS_TRY(launch_svd(W, k, trunc_rtol, sizeof(T) == 8 ? 0.0 : kResolveReduced, sig, Uw, Vw, rank, sweeps, d_refine,
+                      d_status, w.svd, stream));
   const int nb1 = ceil_div(m, ExtrapTile<T>::BM), nb2 = ceil_div(n, ExtrapTile<T>::BM);
   dim3 g1(ceil_div(k, ExtrapTile<T>::BN), nb1), g2(ceil_div(k, ExtrapTile<T>::BN), nb2);
   CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));

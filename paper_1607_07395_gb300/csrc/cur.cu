@@ -99,11 +99,11 @@ CurWs carve_cur(Carve& cv, int64_t m, int64_t n, int kb, int kt, bool f64) {
 }
 
 // B^+ (c x r) of B (r x c) into out; diagnostics into rk[which], rk[2 + which], ...
-cabs_status pinv_block(const CurWs& w, const double* B, int r, int c, int K, double tol, double* out, int* rk,
-                       int which, cudaStream_t stream) {
+cabs_status pinv_block(const CurWs& w, const double* B, int r, int c, int K, double tol, double res, double* out,
+                       int* rk, int which, cudaStream_t stream) {
   const int pb = std::max(1, std::min(ceil_div(K * K, 256), 4 * sm_count()));
   CABS_LAUNCH(stream, "pad_tall_kernel", pad_tall_kernel<<<pb, 256, 0, stream>>>(B, r, c, K, w.Pad));
-  CABS_TRY(launch_svd(w.Pad, K, tol, w.sig, w.Usv, w.Vsv, &rk[which], &rk[2 + which], &rk[4 + which], &rk[6],
+  CABS_TRY(launch_svd(w.Pad, K, tol, res, w.sig, w.Usv, w.Vsv, &rk[which], &rk[2 + which], &rk[4 + which], &rk[6],
                       w.svd, stream));
   CABS_LAUNCH(stream, "recip_kernel", recip_kernel<<<1, 256, 0, stream>>>(K, w.sig, &rk[which], w.isig));
   CABS_TRY(launch_kk_gemm(K, w.Vsv, false, w.isig, w.Usv, true, nullptr, nullptr, w.Pinv, stream));
@@ -147,8 +147,9 @@ cabs_status launch_sketch_cur(const cabs_source& src, int64_t m, int64_t n, int 
   CABS_TRY(launch_rows_of(w.C, m, kb, rows_t, kt, f64, w.Cbar, stream));   // kt x kb
   // 4. pseudo-inverses and U* = (C_bar^+ M) R_bar^+
   const double tol = std::max(trunc_rtol, std::sqrt((double)K * 2.220446049250313e-16));
-  CABS_TRY(pinv_block(w, w.Cbar, kt, kb, K, tol, w.Cp, rk, 0, stream));  // kb x kt
-  CABS_TRY(pinv_block(w, w.Rbar, kb, kt, K, tol, w.Rp, rk, 1, stream));  // kt x kb
+  const double res = f64 ? 0.0 : kResolveReduced;
+  CABS_TRY(pinv_block(w, w.Cbar, kt, kb, K, tol, res, w.Cp, rk, 0, stream));  // kb x kt
+  CABS_TRY(pinv_block(w, w.Rbar, kb, kt, K, tol, res, w.Rp, rk, 1, stream));  // kt x kb
   CABS_TRY(launch_small_gemm(kb, kt, kt, w.Cp, kt, false, nullptr, w.M, kt, false, w.T, kt, stream));
   double* Us = Ustar_out ? Ustar_out : w.Ustar;
   CABS_TRY(launch_small_gemm(kb, kb, kt, w.T, kt, false, nullptr, w.Rp, kb, false, Us, kb, stream));

@@ -329,13 +329,14 @@ cabs_status orth_typed(int64_t m, int64_t n, int k, double trunc_rtol, const T* 
   const double tol_g = sizeof(T) == 8 ? 0.0 : 9.313225746154785e-10;
   CABS_TRY(gram<T>(U, m, k, (T*)w.gpart, w.Gu, stream));
   CABS_TRY(gram<T>(V, n, k, (T*)w.gpart, w.Gv, stream));
-  CABS_TRY(launch_svd(w.Gu, k, tol_g, w.lu, w.Fu, w.Eu, w.ru, w.sweeps, w.refine, d_status, w.svd, stream));
-  CABS_TRY(launch_svd(w.Gv, k, tol_g, w.lv, w.Fv, w.Ev, w.rv, w.sweeps, w.refine, d_status, w.svd, stream));
+  const double res = sizeof(T) == 8 ? 0.0 : kResolveReduced;
+  CABS_TRY(launch_svd(w.Gu, k, tol_g, res, w.lu, w.Fu, w.Eu, w.ru, w.sweeps, w.refine, d_status, w.svd, stream));
+  CABS_TRY(launch_svd(w.Gv, k, tol_g, res, w.lv, w.Fv, w.Ev, w.rv, w.sweeps, w.refine, d_status, w.svd, stream));
   CABS_LAUNCH(stream, "orth_scales_kernel",
               orth_scales_kernel<<<1, 256, 0, stream>>>(k, w.lu, w.ru, w.lv, w.rv, w.su, w.isu, w.sv, w.isv));
   // M = Lambda_u^1/2 E_u^T diag(S) E_v Lambda_v^1/2
   CABS_TRY(launch_kk_gemm(k, w.Eu, true, S, w.Ev, false, w.su, w.sv, w.Mk, stream));
-  CABS_TRY(launch_svd(w.Mk, k, trunc_rtol, s, w.P, w.Z, w.rk, w.sweeps, w.refine, d_status, w.svd, stream));
+  CABS_TRY(launch_svd(w.Mk, k, trunc_rtol, res, s, w.P, w.Z, w.rk, w.sweeps, w.refine, d_status, w.svd, stream));
   CABS_LAUNCH(stream, "orth_final_kernel", orth_final_kernel<<<1, 256, 0, stream>>>(k, w.rk, s, w.mask, d_rank));
   // T_u = E_u Lambda_u^-1/2 U_1, T_v = E_v Lambda_v^-1/2 Z (columns beyond the rank zero)
   CABS_TRY(launch_kk_gemm(k, w.Eu, false, w.isu, w.P, false, nullptr, w.mask, w.Tu, stream));

@@ -892,7 +892,8 @@ struct RefineArgs {
   int* done_iter;
   GridBarrier* bar;
   int* status;
-  double keep_rtol;  // values at or below keep_rtol max |d| are truncated afterwards
+  double keep_rtol;     // values at or below keep_rtol max |d| are truncated afterwards
+  double resolve_rtol;  // off-diagonal |T_ij| up to resolve_rtol max |d| may stay (reduced-precision data)
 };
 
 // Phase B in one launch: every iteration's GEMMs are spread over the CTAs as
@@ -1111,6 +1112,8 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
       for (int i = threadIdx.x; i < k; i += blockDim.x) a.d[i] = dsh[i];
     double local = 0.0, lclose = 0.0;
     const double keep2 = a.keep_rtol * a.keep_rtol * dmax2;
+    // a pair left undiagonalised counts unless both values are truncated
+    auto counts = [&](double di, double dj) { return fmax(di * di, dj * dj) > keep2; };
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)k * k;
          e += (long long)nb * blockDim.x) {
       const int j = (int)(e / k), i = (int)(e - (long long)j * k);
@@ -1142,7 +1145,7 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
               res = 0.5 * fabs(a.T[ij] + a.T[ji]);
             }
           }
-          if (fmax(di * di, dj * dj) > keep2) lclose = fmax(lclose, res);
+          if (counts(di, dj)) lclose = fmax(lclose, res);
         } else {
           const double al = a.T[ij] + dj * Rij;
           const double be = a.T[ji] + dj * Sij;
@@ -1155,7 +1158,6 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
           if (!(fabs(f) <= kMaxCorrB && fabs(g) <= kMaxCorrB)) {
             f = 0.5 * Rij;
             g = 0.5 * Sij;
-            if (fmax(di * di, dj * dj) > keep2) lclose = fmax(lclose, fabs(a.T[ij]));
           }
         }
         local = fmax(local, fmax(fabs(f), fabs(g)));
@@ -1178,15 +1180,21 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     // the pairs that still rotate); at m < kConvB that is below the FP64
     // rounding floor and no verifying iteration is needed. Or a plateau at the
     // rounding floor (clustered values whose corrections stop shrinking).
-    // Pairs that kept only the orthogonality correction (values closer than
-    // the estimates' resolution, or not yet separated) are not diagonalised
-    // by the update, so their |T_ij| must already be at the rounding level:
-    // otherwise (a block of tiny values that the FP32 phase could not
-    // resolve) the iteration has not converged and the FP64 Jacobi takes over.
-    // Pairs whose values are both truncated afterwards do not count.
+    // Pairs closer than the estimates' resolution keep only the
+    // orthogonality correction (and, for a repeated value, the split
+    // rotation), so the update does not diagonalise them: their remaining
+    // |T_ij| must already be at the rounding level, otherwise (a block of
+    // tiny values that the FP32 phase could not resolve) the iteration has
+    // not converged and the FP64 Jacobi takes over. Pairs whose values are
+    // both truncated afterwards do not count, and for data carried in FP32
+    // or less the bound is the data's own resolution (resolve_rtol) rather
+    // than 1e-13. Pairs deferred for a correction above kMaxCorrB are not
+    // counted either: in FP32 data they can stay deferred with |T_ij| near
+    // 1e-7, as before this check existed.
     const double m = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + t));
     const double mc = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + kItersB + t));
-    const bool conv = (m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev)) && mc <= kCloseOffB * sqrt(dmax2);
+    const bool conv = (m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev)) &&
+                      mc <= fmax(kCloseOffB, a.resolve_rtol) * sqrt(dmax2);
     prev = m;
     if (!grid_sync(a.bar, nb)) return;
     if (conv) {
@@ -1521,7 +1529,8 @@ static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0
   return CABS_OK;
 }
 
-cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, double* Uw, double* Vw, int* rank,
+cabs_status launch_svd(const double* W, int k, double trunc_rtol, double resolve_rtol, double* sig, double* Uw,
+                       double* Vw, int* rank,
                        int* sweeps, int* refine, int* status, const SvdWs& w, cudaStream_t stream) {
   // ---- Phase A: FP32 Jacobi -> U[0], V[0]
   if (k <= kCtaMaxK) {
@@ -1545,7 +1554,8 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double* sig, d
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_persistent_kernel, 256, 0);
     const int grid = std::max(1, std::min(tiles, coop_grid_cap(sm_count() * std::max(per_sm, 1))));
     RefineArgs ra{k, W, w.U[0], w.U[1], w.V[0], w.V[1], w.P, w.T, w.UtU, w.VtV, w.F, w.G, w.d, w.maxoff,
-                  w.done_iter, w.bar, status, std::max(trunc_rtol, (double)k * 2.220446049250313e-16)};
+                  w.done_iter, w.bar, status,
+                  std::max(std::max(trunc_rtol, (double)k * 2.220446049250313e-16), resolve_rtol), resolve_rtol};
     void* args[] = {&ra};
     CABS_LAUNCH(stream, "refine_persistent_kernel",
                 cudaLaunchCooperativeKernel((const void*)refine_persistent_kernel, dim3(grid), dim3(256), args, 0,
