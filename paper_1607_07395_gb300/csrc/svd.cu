@@ -31,7 +31,11 @@
 //    (and, where W has zero rows, the others completed to span R^k). Every
 //    product is an FP64 GEMM spread over all SMs. Pairs with d_i^2 ~ d_j^2,
 //    or whose correction would exceed 0.05 (values not yet separated by more
-//    than the estimates' error), keep only the orthogonality correction.
+//    than the estimates' error), keep only the orthogonality correction;
+//    a pair with d_i ~ d_j clearly above zero (a repeated value) also gets
+//    the rotation that makes U and V agree inside it. The iteration has
+//    converged when its corrections are small and every close pair left
+//    undiagonalised has |T_ij| at the rounding level of the input.
 //    Iteration t's kernels exit at once if an earlier iteration already
 //    converged (a device-side flag; no host sync).
 //  Fallback: if Phase B has not converged after its iterations, the one-CTA
