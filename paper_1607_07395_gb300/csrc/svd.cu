@@ -517,11 +517,14 @@ __device__ __forceinline__ void apply_panel(const float* V, const float* beta, i
 // outputs as before (U from the normalised columns, V accumulated), in fewer
 // sweeps, since the Gram matrix of R^T, R R^T, is much nearer to diagonal
 // than W^T W = R^T R (about 10 sweeps instead of 15 to 19 on the sketching
-// workloads). The QR runs blocked over the cluster: the owner of panel p
-// factors its b columns of W^T, one cluster barrier, and every CTA applies
-// the panel's reflectors to its later columns of W^T and to all its columns
-// of Y = Q^T (started at I). R^T and Q = Y^T are then scattered into the
-// other buffer through distributed shared memory. A W with zero rows (sparse
+// workloads). The QR runs over the cluster with one panel per CTA, its two
+// blocks: the columns of W^T are factored in CTA order, i.e. W^T P = Q R,
+// X = P^T W Q, and U comes out with its rows permuted back. CTA p factors its
+// panel (a warp per column, in registers) and publishes the reflectors in
+// global memory; after one cluster barrier every CTA reads them from L2 and
+// applies them to its later columns of W^T and to all its columns of
+// Y = Q^T (started at I). R^T and Q = Y^T are then scattered into the other
+// buffer through distributed shared memory. A W with zero rows (sparse
 // inputs) starts from W itself: its QR turns exact zeros into rounding noise,
 // and there the preconditioned Jacobi needed more sweeps, not fewer.
 template <int R>
