@@ -1449,6 +1449,11 @@ cabs_status launch_svd_jacobi_f64(const double* W, int k, double trunc_rtol, con
   return CABS_OK;
 }
 
+// Scratch of the preconditioning QR: the reflectors of every panel position
+// (2 NC b <= k + 31 for any cluster size NC, since b = ceil(k / 2 NC)) of
+// kp <= 256 rows (kp = 128 up to k = 128), and their betas.
+static size_t svd_qr_floats(int k) { return (size_t)(k + 32) * (k <= 128 ? 128 : 256) + (k + 32); }
+
 SvdWs carve_svd(Carve& cv, int k) {
   SvdWs w;
   const size_t kk = (size_t)k * k;
@@ -1470,9 +1475,7 @@ SvdWs carve_svd(Carve& cv, int k) {
   w.bar = cv.take<GridBarrier>(1);
   w.Wc = cv.take<double>(kk);
   w.Vc = cv.take<double>(kk);
-  // the preconditioning QR's reflectors: <= k + 31 panel positions of
-  // kp <= 256 rows (kp = 128 up to k = 128), and their betas
-  w.qr = cv.take<float>((size_t)(k + 32) * (k <= 128 ? 128 : 256) + (k + 32));
+  w.qr = cv.take<float>(svd_qr_floats(k));
   return w;
 }
 
@@ -1515,6 +1518,10 @@ static cabs_status launch_cluster(const double* W, int k, double* U0, double* V0
   const int b = (k + 2 * nc - 1) / (2 * nc);
   if (b > kMaxBlkRot) {
     set_error("svd: %d columns per block exceed %d (k = %d on a %d-CTA cluster)", b, kMaxBlkRot, k, nc);
+    return CABS_EINVAL;
+  }
+  if (32 * R < k || (size_t)2 * nc * b * (32 * R + 1) > svd_qr_floats(k)) {
+    set_error("svd: k = %d does not fit the %d-row cluster layout or its QR scratch", k, 32 * R);
     return CABS_EINVAL;
   }
   const size_t smem = smem_for(nc);
