@@ -57,16 +57,16 @@ def trunc_rtol(wl, k):
 
 
 WORKLOADS = {
-    # BASELINE configuration 3: dense stored FP32 A, 65536 x 32768 (8 GiB)
+    # dense stored FP32 A, 65536 x 32768 (8 GiB): the headline workload
     "dense": dict(kind="dense", m=65536, n=32768, rank=256, k=256, iters=5, core="stabilized",
                   desc="dense FP32 A 65536x32768 = U diag(exp(-i/30)) V^T (rank 256) + N(0,1e-4^2); k=256, c=5"),
-    # BASELINE configuration 2: implicit RBF matrix, 1e5 x 1e5 points in d=16
+    # implicit RBF matrix, 1e5 x 1e5 points in d=16
     "rbf": dict(kind="rbf", m=100000, n=100000, d=16, k=200, iters=10, core="pinv", samples=1000000,
                 desc="implicit RBF exp(-|x-y|^2/2s^2), 1e5 x 1e5 points d=16 (50-comp. mixture); k=200, c=10"),
-    # BASELINE configuration 1: plain FP64 2000 x 1500
+    # plain FP64 2000 x 1500 (the small case the oracle finishes in seconds)
     "plain": dict(kind="plain", m=2000, n=1500, k=20, iters=5, core="pinv",
                   desc="plain FP64 A 2000x1500 = U V^T + N(0,1e-6); k=20, c=5"),
-    # Table 1's movie-ratings shape (not a BASELINE configuration): sparse CSR
+    # Table 1's movie-ratings shape: sparse CSR
     "sparse": dict(kind="csr", m=27000, n=46000, density=0.0056, k=256, iters=5, core="stabilized",
                    desc="sparse CSR A 27000x46000, 0.56 % (ratings-like, power-law rows and columns, rank-20 "
                         "values); k=256, c=5, exact error by the linear-cost identity"),
