@@ -66,7 +66,10 @@ Readings where the paper is silent (the GPU library takes the same ones):
   to the lowest centre index; weights Upsilon(t) = t^p with 0^0 = 1; an empty
   cluster (zero total weight) keeps its centre.
 * Snap: centres processed in index order, each taking the nearest row not yet
-  taken (ties to the lowest row index); the result is then sorted.
+  taken; ties go to the lowest row index, a tie meaning a squared distance
+  within 1e-12 (d* + |z|^2) of the nearest d* (the centre of a two-row
+  cluster is equidistant from both rows, and rounding alone would otherwise
+  pick one); the result is then sorted.
 
 Every function here is pinned by tests in ``tests/test_oracle_*.py`` against
 facts the paper or mathematics fixes (numpy's independent Philox, closed-form
@@ -383,18 +386,30 @@ def encoding_error(X: np.ndarray, reps_rows, upsilon_pow: float = 0.0):
     return err, s, T
 
 
-def snap(X: np.ndarray, Z: np.ndarray):
+SNAP_TIE_RTOL = 1e-12
+
+
+def snap(X: np.ndarray, Z: np.ndarray, tie_rtol: float = SNAP_TIE_RTOL):
     """Replace each centre by its closest in-sample row of X, all distinct.
 
     Centres are taken in index order; each takes the nearest row not already
-    taken (lowest row index on ties). Returns (rows in centre order, sorted rows)."""
+    taken. Ties go to the lowest row index, where a tie is judged at the
+    resolution of the arithmetic: with d* the smallest squared distance of an
+    untaken row to the centre z, every untaken row with
+    d <= d* + tie_rtol (d* + |z|^2) is tied with the nearest. Exact ties are
+    structural here, not accidental: the centre of a cluster of two rows of
+    equal weight is their midpoint, equidistant from both, and which of the
+    two rounded distances comes out smaller depends only on the order of the
+    floating-point sum. Returns (rows in centre order, sorted rows)."""
     X = np.asarray(X, dtype=np.float64)
     taken = np.zeros(X.shape[0], dtype=bool)
     out = []
     for j in range(Z.shape[0]):
-        d = sq_dists_to(X, np.asarray(Z[j], dtype=np.float64))
+        z = np.asarray(Z[j], dtype=np.float64)
+        d = sq_dists_to(X, z)
         d[taken] = np.inf
-        l = int(np.argmin(d))
+        dstar = d.min()
+        l = int(np.flatnonzero(d <= dstar + tie_rtol * (dstar + float((z * z).sum())))[0])
         taken[l] = True
         out.append(l)
     out = np.array(out, dtype=np.int64)

@@ -3,10 +3,12 @@
 // step 3.
 //
 // Centres are taken in index order and each takes the nearest row not taken
-// before (ties to the lower row index), so the k2 follow-up rows are
-// distinct. Distances are direct differences sum_q (x_q - z_q)^2 in the
-// working precision, summed in dimension order (the same arithmetic in every
-// kernel below, so equal inputs give equal distances).
+// before, so the k2 follow-up rows are distinct. Ties go to the lower row
+// index, a tie meaning a squared distance within tie_rtol (d* + |z|^2) of the
+// nearest untaken row's d*: the centre of a two-row cluster is the midpoint
+// of the rows, exactly equidistant from both, and which rounded distance is
+// smaller would otherwise depend on the order of the sum. Distances are
+// direct differences sum_q (x_q - z_q)^2 in the working precision.
 //
 //  1. snap_cand_kernel: a CTA covers 64 rows x all centres (register tiles of
 //     8 x 8 per thread) and keeps, per centre, its 8 nearest rows of the tile.
@@ -16,9 +18,10 @@
 //     (tc_snap.cu): the 32 best rows per centre by |x|^2 - 2 x.z, then the
 //     same direct FP32 distances as step 1 decide the 8 candidates.
 //  3. snap_greedy_kernel (cooperative): CTA 0's warp 0 walks the centres in
-//     order and picks the first candidate not taken (a bitmap of taken rows);
-//     only if all 8 are taken do all CTAs scan every row for that centre.
-//     The picks are then sorted ascending.
+//     order and picks the lowest untaken candidate inside the tie window of
+//     the first untaken one (a bitmap of taken rows); only if all 8 are taken,
+//     or the window reaches the 8th, do all CTAs scan every row for that
+//     centre. The picks are then sorted ascending.
 #include "common.cuh"
 #include "grid_sync.cuh"
 #include "kernels.cuh"
@@ -29,6 +32,13 @@ namespace cabs {
 namespace {
 
 constexpr int kTop = 8;
+// Tie window of the snap (relative to d* + |z|^2): the centre of a two-row
+// cluster is equidistant from both rows, and the rounded distances differ by
+// at most about 2 u (d* + |z|^2) plus the summation error (u the unit
+// roundoff, up to d u for d dimensions). FP64: 1e-12 (35 times 256 u);
+// FP32 (every reduced-precision mode decides by FP32 distances): 2^-16.
+constexpr double kSnapTieRtolF64 = 1e-12;
+constexpr float kSnapTieRtolF32 = 1.52587890625e-5f;
 constexpr int kSM = 64, kSK = 16, kSN = 256;
 constexpr int kGreedyThreads = 512;
 
@@ -183,11 +193,18 @@ __global__ void __launch_bounds__(256) snap_merge_kernel(const T* __restrict__ c
   }
 }
 
-// Cooperative greedy pass. CTA 0's warp 0 walks the centres in order and
-// takes the first candidate not taken yet; when a centre's 8 candidates are
-// all taken, every CTA scans its slice of rows for that centre (one warp per
-// row, lanes over dimensions), CTA 0 reduces the per-CTA minima in a fixed
-// order, and the walk continues. The taken-row bitmap lives in global memory.
+// Cooperative greedy pass. CTA 0's warp 0 walks the centres in order. For
+// centre j with candidate list (d_0, r_0) <= ... <= (d_7, r_7), let d* be the
+// distance of the first candidate not taken yet; the centre takes the lowest
+// row among the untaken candidates with d <= d* + tie_rtol (d* + |z_j|^2)
+// (rows that tie with the nearest at the working precision's resolution; the
+// centre of a two-row cluster is exactly equidistant from both rows). The
+// list decides alone when every row outside it is farther than that window,
+// i.e. when d_7 lies beyond it. Otherwise -- all 8 taken, or the window
+// reaching d_7 -- every CTA scans its slice of rows for centre j (one warp per
+// row, lanes over dimensions) in two passes: the nearest untaken row (d*),
+// then the lowest untaken row inside the window; CTA 0 reduces the per-CTA
+// results in a fixed order and the walk continues.
 // Open-addressing set of taken rows (at most CABS_MAX_K of them) in shared
 // memory; -1 marks a free slot.
 constexpr int kTakenSlots = 4 * CABS_MAX_K;
@@ -215,18 +232,90 @@ __device__ __forceinline__ void taken_add(int* set, int r) {
   }
 }
 
+// One scan of rows [lo, hi) not in the taken bitmap for centre z. Pass 1
+// (lim < 0): the (distance, row) minimum. Pass 2: the lowest row with
+// distance <= lim (distance +inf if none). The distances are the same in both
+// passes (same arithmetic, same order).
+template <typename T>
+__device__ void scan_slice(const T* __restrict__ X, int d, const T* __restrict__ z, long long lo, long long hi,
+                           const unsigned* taken, T lim, bool window, T& best, int& brow) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  best = pos_inf<T>();
+  brow = 0x7fffffff;
+  for (long long l0 = lo + (long long)wi * 4; l0 < hi; l0 += (long long)nw * 4) {
+    bool skip[4];
+    T s4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long l = l0 + u;
+      skip[u] = l >= hi || ((((volatile const unsigned*)taken)[l >> 5] >> (l & 31)) & 1u);
+      s4[u] = T(0);
+    }
+    for (int q = lane; q < d; q += 32) {
+      const T zq = z[q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!skip[u]) {
+          const T t = X[(l0 + u) * d + q] - zq;
+          s4[u] = fma(t, t, s4[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T sv = warp_sum(s4[u]);
+      if (skip[u]) continue;
+      if (window) {
+        if (sv <= lim && (int)(l0 + u) < brow) {
+          best = sv;
+          brow = (int)(l0 + u);
+        }
+      } else if (lex_less(sv, (int)(l0 + u), best, brow)) {
+        best = sv;
+        brow = (int)(l0 + u);
+      }
+    }
+  }
+}
+
+// Per-CTA result of scan_slice -> cta_best[b], cta_row[b] (pass 1: the lexicographic
+// minimum over the warps; pass 2: the lowest row).
+template <typename T>
+__device__ void cta_reduce(T best, int brow, bool window, T* wd, int* wr, T* cta_best, int* cta_row) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    wd[wi] = best;
+    wr[wi] = brow;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T bv = wd[0];
+    int bi = wr[0];
+    for (int i = 1; i < nw; ++i)
+      if (window ? wr[i] < bi : lex_less(wd[i], wr[i], bv, bi)) {
+        bv = wd[i];
+        bi = wr[i];
+      }
+    cta_best[blockIdx.x] = bv;
+    cta_row[blockIdx.x] = bi;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
-    unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row, GridBarrier* bar, int* __restrict__ order,
-    int* __restrict__ sorted, int* fallbacks) {
+    const T* __restrict__ top_d, T tie_rtol, unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row,
+    T* fb_lim, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks) {
   __shared__ T wd[kGreedyThreads / 32];
   __shared__ int wr[kGreedyThreads / 32];
-  // CTA 0's walk reads the candidate lists and the rows taken so far from
-  // shared memory: the lists are staged once, the taken rows (at most k2)
-  // live in an open-addressing set of kTakenSlots slots. The global bitmap is
-  // written too, for the CTAs' scans when a centre's list runs out.
+  // CTA 0's walk reads the candidate lists, their distances, the centres'
+  // squared norms and the rows taken so far from shared memory: the lists
+  // are staged once, the taken rows (at most k2) live in an open-addressing
+  // set of kTakenSlots slots. The global bitmap is written too, for the CTAs'
+  // scans when a centre's list does not decide.
   __shared__ int s_top[CABS_MAX_K * kTop];
+  __shared__ T s_topd[CABS_MAX_K * kTop];
+  __shared__ T s_zz[CABS_MAX_K];
   __shared__ int s_taken[kTakenSlots];
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
@@ -234,8 +323,17 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
   for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < words; e += (long long)G * blockDim.x)
     taken[e] = 0u;
   if (blockIdx.x == 0) {
-    for (int e = tid; e < k2 * kTop; e += blockDim.x) s_top[e] = top_r[e];
+    for (int e = tid; e < k2 * kTop; e += blockDim.x) {
+      s_top[e] = top_r[e];
+      s_topd[e] = top_d[e];
+    }
     for (int e = tid; e < kTakenSlots; e += blockDim.x) s_taken[e] = -1;
+    for (int j = wi; j < k2; j += nw) {
+      T s = T(0);
+      for (int q = lane; q < d; q += 32) s = fma(Z[(size_t)j * d + q], Z[(size_t)j * d + q], s);
+      s = warp_sum(s);
+      if (lane == 0) s_zz[j] = s;
+    }
   }
   if (!grid_sync(bar, G)) return;
   int j = 0;
@@ -244,14 +342,21 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       int jj = j;
       for (; jj < k2; ++jj) {
         const int r = lane < kTop ? s_top[jj * kTop + lane] : 0x7fffffff;
+        const T dv = lane < kTop ? s_topd[jj * kTop + lane] : pos_inf<T>();
         const bool ok = lane < kTop && r >= 0 && r < M && !taken_has(s_taken, r);
         const unsigned good = __ballot_sync(0xffffffffu, ok);
         if (!good) break;
-        const int pick = __shfl_sync(0xffffffffu, r, __ffs(good) - 1);
+        const T dstar = __shfl_sync(0xffffffffu, dv, __ffs(good) - 1);
+        const T lim = dstar + tie_rtol * (dstar + s_zz[jj]);
+        const T dlast = __shfl_sync(0xffffffffu, dv, kTop - 1);
+        if (dlast <= lim) break;  // rows outside the list may lie inside the window
+        int cand = (ok && dv <= lim) ? r : 0x7fffffff;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, off));
         if (lane == 0) {
-          taken_add(s_taken, pick);
-          taken[pick >> 5] |= 1u << (pick & 31);
-          picks[jj] = pick;
+          taken_add(s_taken, cand);
+          taken[cand >> 5] |= 1u << (cand & 31);
+          picks[jj] = cand;
         }
         __syncwarp();
       }
@@ -260,55 +365,13 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     if (!grid_sync(bar, G)) return;
     j = *(volatile int*)next_fb;
     if (j >= k2) break;
-    // every CTA: nearest untaken row of its slice for centre j
+    // every CTA, pass 1: nearest untaken row of its slice for centre j
     const long long lo = M * blockIdx.x / G, hi = M * (blockIdx.x + 1) / G;
-    T best = pos_inf<T>();
-    int brow = 0x7fffffff;
     const T* z = Z + (size_t)j * d;
-    for (long long l0 = lo + (long long)wi * 4; l0 < hi; l0 += (long long)nw * 4) {
-      bool skip[4];
-      T s4[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const long long l = l0 + u;
-        skip[u] = l >= hi || ((((volatile unsigned*)taken)[l >> 5] >> (l & 31)) & 1u);
-        s4[u] = T(0);
-      }
-      for (int q = lane; q < d; q += 32) {
-        const T zq = z[q];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!skip[u]) {
-            const T t = X[(l0 + u) * d + q] - zq;
-            s4[u] = fma(t, t, s4[u]);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const T sv = warp_sum(s4[u]);
-        if (!skip[u] && lex_less(sv, (int)(l0 + u), best, brow)) {
-          best = sv;
-          brow = (int)(l0 + u);
-        }
-      }
-    }
-    if (lane == 0) {
-      wd[wi] = best;
-      wr[wi] = brow;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      T bv = wd[0];
-      int bi = wr[0];
-      for (int i = 1; i < nw; ++i)
-        if (lex_less(wd[i], wr[i], bv, bi)) {
-          bv = wd[i];
-          bi = wr[i];
-        }
-      cta_best[blockIdx.x] = bv;
-      cta_row[blockIdx.x] = bi;
-    }
+    T best;
+    int brow;
+    scan_slice(X, d, z, lo, hi, taken, T(-1), false, best, brow);
+    cta_reduce(best, brow, false, wd, wr, cta_best, cta_row);
     if (!grid_sync(bar, G)) return;
     if (blockIdx.x == 0 && tid == 0) {
       T bv = cta_best[0];
@@ -318,6 +381,17 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
           bv = cta_best[b];
           bi = cta_row[b];
         }
+      *(volatile T*)fb_lim = bv + tie_rtol * (bv + s_zz[j]);
+      __threadfence();
+    }
+    if (!grid_sync(bar, G)) return;
+    // pass 2: lowest untaken row of the slice inside the window
+    scan_slice(X, d, z, lo, hi, taken, *(volatile T*)fb_lim, true, best, brow);
+    cta_reduce(best, brow, true, wd, wr, cta_best, cta_row);
+    if (!grid_sync(bar, G)) return;
+    if (blockIdx.x == 0 && tid == 0) {
+      int bi = cta_row[0];
+      for (unsigned b = 1; b < G; ++b) bi = min(bi, cta_row[b]);
       if (bi >= 0 && bi < M) {
         taken[bi >> 5] |= 1u << (bi & 31);
         taken_add(s_taken, bi);
@@ -355,7 +429,7 @@ struct SnapWs {
   int* top_r;
   unsigned* bitmap;
   int *picks, *next_fb, *cta_row;
-  void* cta_best;
+  void *cta_best, *fb_lim;
   GridBarrier* bar;
   void* tc;  // tensor-core candidate search (BF16 / TF32 modes)
   size_t tc_bytes;
@@ -374,6 +448,7 @@ SnapWs carve_snap(Carve& cv, int64_t M, int d, int k2, int prec) {
   w.next_fb = cv.take<int>(1);
   w.cta_row = cv.take<int>(1024);
   w.cta_best = cv.take<char>(1024 * eb);
+  w.fb_lim = cv.take<char>(eb);
   w.bar = cv.take<GridBarrier>(1);
   w.tc = nullptr;
   w.tc_bytes = 0;
@@ -414,14 +489,18 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
   const T* Xc = X;
   const T* Zc = Z;
   const int* topr = w.top_r;
+  const T* topd = (const T*)w.top_d;
+  T tie = sizeof(T) == 8 ? T(kSnapTieRtolF64) : T(kSnapTieRtolF32);
   unsigned* bm = w.bitmap;
   int* picks = w.picks;
   int* nfb = w.next_fb;
   T* cb = (T*)w.cta_best;
   int* cr = w.cta_row;
+  T* lim = (T*)w.fb_lim;
   GridBarrier* bar = w.bar;
   long long Ml = M;
-  void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &bm, &picks, &nfb, &cb, &cr, &bar, &order, &sorted, &fallbacks};
+  void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &topd, &tie, &bm, &picks, &nfb, &cb, &cr, &lim, &bar, &order, &sorted,
+                  &fallbacks};
   CABS_LAUNCH(stream, "snap_greedy_kernel",
               cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args, 0,
                                           stream));

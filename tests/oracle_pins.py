@@ -276,10 +276,60 @@ def pin_snap_bruteforce(snap_fn, M=30, d=3, k2=6, seed=8):
     taken = []
     for j in range(k2):
         ds = [(sum((float(X[l, q]) - float(Z[j, q])) ** 2 for q in range(d)), l) for l in range(M) if l not in taken]
-        taken.append(min(ds)[1])
+        best = min(ds)
+        zz = sum(float(Z[j, q]) ** 2 for q in range(d))
+        # rows within the tie window of the nearest; these inputs have none
+        assert [l for v, l in ds if v <= best[0] + 1e-12 * (best[0] + zz)] == [best[1]]
+        taken.append(best[1])
     assert order.tolist() == taken
     assert srt.tolist() == sorted(taken)
     assert len(set(taken)) == k2
+
+
+def _midpoint_case(flip, d=7, seed=21, offset=0.0, spread=1.0):
+    """Rows a < b of a random X (offset + spread N(0, 1) entries) and their
+    midpoint z = (x_a + x_b) / 2, found so that the FP64 squared distances by
+    direct differences (summed in dimension order) come out unequal: with
+    flip, the higher row b looks strictly nearer, otherwise a does.
+    Mathematically |x_a - z| = |x_b - z|."""
+    g = np.random.default_rng(seed)
+    for _ in range(10000):
+        X = offset + spread * g.standard_normal((12, d))
+        a, b = sorted(g.choice(12, 2, replace=False).tolist())
+        z = (X[a] + X[b]) / 2.0
+        da = sum((float(X[a, q]) - float(z[q])) ** 2 for q in range(d))
+        db = sum((float(X[b, q]) - float(z[q])) ** 2 for q in range(d))
+        others = [sum((float(X[l, q]) - float(z[q])) ** 2 for q in range(d)) for l in range(12) if l not in (a, b)]
+        if min(others) > 2 * max(da, db) and ((db < da) if flip else (da < db)):
+            return X, z, a, b
+    raise AssertionError("no rounding-split midpoint found")
+
+
+def pin_snap_midpoint_tie(snap_fn):
+    """Section 3.2 replaces a centre by its closest in-sample point; the
+    centre of a two-row cluster is the midpoint of the rows, equidistant
+    from both, so the tie goes to the lower row whichever rounded distance is
+    smaller. A genuine difference of 1e-9 relative (far above FP64 rounding,
+    far below any data scale) is not a tie: the nearer row wins even when its
+    index is higher."""
+    for flip in (False, True):
+        X, z, a, b = _midpoint_case(flip)
+        order, _ = snap_fn(X, z[None, :])
+        assert order.tolist() == [a], (flip, order, a, b)
+        # a second centre at the same point takes the other row
+        order, srt = snap_fn(X, np.stack([z, z]))
+        assert order.tolist() == [a, b]
+    # far from the origin, rounding of x - z scales with |z|, not |x - z|:
+    # the window must be relative to d* + |z|^2
+    X, z, a, b = _midpoint_case(True, offset=1000.0, spread=1e-3)
+    order, _ = snap_fn(X, z[None, :])
+    assert order.tolist() == [a]
+    X, z, a, b = _midpoint_case(False)
+    u = (X[b] - X[a]) / np.linalg.norm(X[b] - X[a])
+    # moving z by e towards x_b lowers |x_b - z|^2 - |x_a - z|^2 by 4 e |x_b - x_a| / 2
+    e = 1e-9 * (float(((X[a] - z) ** 2).sum()) + float((z * z).sum())) / (2.0 * np.linalg.norm(X[b] - X[a]))
+    order, _ = snap_fn(X, (z + e * u)[None, :])
+    assert order.tolist() == [b]
 
 
 # ------------------------------------------------------------ hard threshold

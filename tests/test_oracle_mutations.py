@@ -96,13 +96,20 @@ def test_kmeans_mutants_rejected(old, new):
     assert any(rejects(c) for c in checks)
 
 
+SNAP_PICK = "l = int(np.flatnonzero(d <= dstar + tie_rtol * (dstar + float((z * z).sum())))[0])"
+
+
 @pytest.mark.parametrize("old,new", [
     ("d[taken] = np.inf", "pass"),
     ("taken[l] = True", "taken[l] = False"),
+    (SNAP_PICK, "l = int(np.argmin(d))"),                                          # rounding decides ties
+    (SNAP_PICK, SNAP_PICK.replace("[0])", "[-1])")),                                # ties to the highest row
+    (SNAP_PICK, SNAP_PICK.replace("tie_rtol *", "1e3 * tie_rtol *")),              # window wider than rounding
+    (SNAP_PICK, SNAP_PICK.replace("(dstar + float((z * z).sum()))", "dstar")),     # no |z|^2 scale
 ])
 def test_snap_mutants_rejected(old, new):
     bad = mutate(o.snap, old, new)
-    assert rejects(lambda: pins.pin_snap_bruteforce(bad))
+    assert rejects(lambda: pins.pin_snap_bruteforce(bad)) or rejects(lambda: pins.pin_snap_midpoint_tie(bad))
 
 
 def test_error_mutant_rejected():

@@ -107,6 +107,10 @@ def test_snap_bruteforce():
     pins.pin_snap_bruteforce(o.snap)
 
 
+def test_snap_midpoint_tie():
+    pins.pin_snap_midpoint_tie(o.snap)
+
+
 def test_threshold_bruteforce_and_known_scales():
     pins.pin_threshold_bruteforce(o.hard_threshold)
     pins.pin_threshold_known_scales(o.hard_threshold)
