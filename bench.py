@@ -755,7 +755,8 @@ def run_sketch_cur(args):
     src = make_source(cabs, wl, inp)
     B = 1 if args.form == "plain" else args.batch
     streams = [torch.cuda.Stream(device=device) for _ in range(B)]
-    ps = [cabs.make_cur_params(wl["m"], wl["n"], kb, kt, seed=1607 + rank * 1000 + b, prec=prec) for b in range(B)]
+    ps = [cabs.make_cur_params(wl["m"], wl["n"], kb, kt, seed=1607 + rank * 1000 + b, prec=prec,
+                               trunc_rtol=trunc_rtol(wl, max(kb, kt))) for b in range(B)]
     outs = [cabs.cabs_sketch_cur(ctx, src, p, stream=st) for p, st in zip(ps, streams)]
     main = torch.cuda.current_stream()
 

@@ -237,11 +237,17 @@ cabs_status cabs_error(cabs_ctx* ctx, const cabs_source* src, const cabs_params*
                        const cabs_result* res, int64_t samples, uint64_t seed, void* ws,
                        size_t ws_bytes, cabs_stream stream, double* rel_fro);
 
-/* The same error as cabs_error, for callers that cannot allocate device
+/* The error of cabs_error, for callers that cannot allocate device
  * memory when they need it: code running inside another framework's memory
  * pool that forbids cudaMalloc/cudaFree during a step, or programs that
  * reserve all device memory up front and have no workspace to hand out. It
- * takes no workspace and calls no allocating routine. The paper has no
+ * takes no workspace and calls no allocating routine. Its products
+ * U diag(S) V^T are FP64 in FP64 mode and FP32 CUDA-core products in every
+ * other mode: in FP64 and FP32 modes it returns cabs_error's value (to
+ * rounding, 1e-9 relative); in TF32 and BF16 modes on a dense FP32 A, where
+ * cabs_error forms the products on tensor cores from TF32 / BF16 operands,
+ * it returns the FP32-mode value for the same factors, within 1e-3 relative
+ * of cabs_error's (the tensor-core residual's bound against the exact error). The paper has no
  * counterpart; this is a service of the library. Its scratch is one fixed
  * file-scope device array (about 256 KiB on every device that loads libcabs,
  * held until the process exits). Limits: the exact error (samples == 0,

@@ -627,15 +627,16 @@ def orthogonalize(U: np.ndarray, S: np.ndarray, V: np.ndarray, trunc_rtol: float
 
 def pinv_trunc(B: np.ndarray, trunc_rtol: float = 0.0) -> np.ndarray:
     """Pseudo-inverse V diag(1/s) U^T of B = U diag(s) V^T over the singular
-    values s_i > max(trunc_rtol, sqrt(kmax 2^-52)) s_1, kmax = max(B.shape).
-    Algorithm 1 leaves the tolerance open; the floor is the square root of
-    the sketching routine's (MATLAB pinv's) k 2^-52, the resolution of
-    B^T B, through which a linear-cost implementation reaches B^+."""
+    values s_i > max(trunc_rtol, kmax 2^-52) s_1, kmax = max(B.shape).
+    Algorithm 1 leaves the tolerance open; the floor is MATLAB pinv's default
+    (the paper ran MATLAB, Section 5), the floor of the sketching routine
+    too. Data that carry less than FP64 precision pass their resolution in
+    trunc_rtol, as for the sketching routine."""
     B = np.asarray(B, dtype=np.float64)
     Ub, sb, Vbt = np.linalg.svd(B, full_matrices=False)
     if len(sb) == 0 or sb[0] == 0.0:
         return np.zeros(B.T.shape)
-    keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]
+    keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]
     return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T
 
 

@@ -14,7 +14,9 @@
 //     tall orientation of the block (B, or B^T when B is wide) padded with
 //     zero columns to K x K (K = max(k_b, k_t)): the SVD's refinement takes
 //     the kept columns of U from W V in FP64, so zero columns cost nothing
-//     in accuracy. Kept: sigma_i > max(trunc_rtol, sqrt(K 2^-52)) sigma_1.
+//     in accuracy. Kept: sigma_i > max(trunc_rtol, K 2^-52) sigma_1 (MATLAB
+//     pinv's default floor, as in the sketching routine; data carried in
+//     FP32 pass their resolution K 2^-24 in trunc_rtol).
 //     pinv(pad) = V Sigma^+ U^T holds B^+ (or (B^+)^T) in its first rows.
 //  5. A ~ C U* R returned as U = C U* (m x k_b, CUDA cores), S = 1, V = R^T.
 #include "common.cuh"
@@ -146,7 +148,7 @@ cabs_status launch_sketch_cur(const cabs_source& src, int64_t m, int64_t n, int 
   CABS_TRY(launch_rows_of(w.Ct, m, kt, rows_b, kb, f64, w.Rbar, stream));  // kb x kt
   CABS_TRY(launch_rows_of(w.C, m, kb, rows_t, kt, f64, w.Cbar, stream));   // kt x kb
   // 4. pseudo-inverses and U* = (C_bar^+ M) R_bar^+
-  const double tol = std::max(trunc_rtol, std::sqrt((double)K * 2.220446049250313e-16));
+  const double tol = std::max(trunc_rtol, (double)K * 2.220446049250313e-16);
   const double res = f64 ? 0.0 : kResolveReduced;
   CABS_TRY(pinv_block(w, w.Cbar, kt, kb, K, tol, res, w.Cp, rk, 0, stream));  // kb x kt
   CABS_TRY(pinv_block(w, w.Rbar, kb, kt, K, tol, res, w.Rp, rk, 1, stream));  // kt x kb

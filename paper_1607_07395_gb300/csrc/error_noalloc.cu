@@ -9,6 +9,12 @@
 // final sums) in one file-scope device array of fixed size, which every GPU
 // that loads libcabs holds until the process exits.
 //
+// Arithmetic: the products U diag(S) V^T are FP64 in FP64 mode and FP32
+// CUDA-core products in the FP32, TF32 and BF16 modes. cabs_error takes the
+// tensor-core residual for TF32 / BF16 on a dense FP32 A (TF32 / BF16
+// operands); there this variant returns the FP32-mode value of the same
+// factors instead, within 1e-3 relative of cabs_error's.
+//
 // Limits: the exact (dense) error uses one CTA per 64-row block of A, so
 // m <= 64 * kNoAllocMaxBlocks = 1,048,576 rows; the sampled error uses at
 // most kNoAllocMaxBlocks CTAs for any sample count. Larger m is rejected

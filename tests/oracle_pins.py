@@ -400,19 +400,48 @@ def pin_orthogonalize(orth_fn, m=60, n=45, r=6, seed=13):
 
 # ------------------------------------------------------------ BR-CUR, Sketch-CUR
 
+def pin_embed(embed_fn, sketching_fn, gather_fn):
+    """Algorithm 2, step 2: P = U S^(1/2). Closed form: orthonormal U with
+    S = (4, 9, 0) gives P = U diag(2, 3, 0). Identity: the pseudo-skeleton
+    core has U diag(S) V^T = C W^+ R (Section 2.2, Eq. W), so the two
+    embeddings satisfy P Q^T = C W^+ R, here against an LU solve for W^-1
+    on an exactly rank-3 matrix with rank(W) = 3, whose P Q^T is A itself."""
+    g = np.random.default_rng(17)
+    U, _ = np.linalg.qr(g.standard_normal((6, 3)))
+    P = embed_fn(U, np.array([4.0, 9.0, 0.0]))
+    assert np.allclose(P, U * np.array([2.0, 3.0, 0.0]), rtol=0, atol=1e-15)
+    A = synth.exact_lowrank_int(40, 30, 3, seed=5)
+    rows, cols = np.array([2, 11, 29]), np.array([0, 7, 21])
+    C, Rt, W = gather_fn(A, rows, cols)
+    assert np.linalg.matrix_rank(W) == 3
+    sk = sketching_fn(C, Rt, W, 40, 30, "pinv")
+    Pm, Qm = embed_fn(sk.U, sk.S), embed_fn(sk.V, sk.S)
+    want = C @ np.linalg.solve(W, Rt.T)
+    assert np.linalg.norm(Pm @ Qm.T - want) <= 1e-10 * np.linalg.norm(want)
+    assert np.linalg.norm(Pm @ Qm.T - A) <= 1e-10 * np.linalg.norm(A)
+
+
 def pin_pinv_trunc(pinv_fn):
-    """Closed form on a matrix with known singular values: 5 x 3,
-    s = (1, 1e-3, 3e-8); the floor sqrt(5 x 2^-52) = 3.33e-8 drops the third
-    (sqrt(3 x 2^-52) = 2.58e-8 would keep it)."""
+    """Closed forms on matrices with known singular values. 5 x 3 with
+    s = (1, 1e-3, 3e-8): the floor 5 x 2^-52 = 1.1e-15 keeps all three (its
+    square root, 3.3e-8, would drop the third); 50 x 3 with
+    s = (1, 1e-3, 3e-15): the floor 50 x 2^-52 = 1.1e-14 drops the third
+    (3 x 2^-52 = 6.7e-16, from the smaller dimension, would keep it); a
+    tolerance of 1e-2 keeps the first only."""
     g = np.random.default_rng(3)
     Q1, _ = np.linalg.qr(g.standard_normal((5, 3)))
     Q2, _ = np.linalg.qr(g.standard_normal((3, 3)))
     s = np.array([1.0, 1e-3, 3e-8])
     B = (Q1 * s) @ Q2.T
-    want = (Q2[:, :2] / s[:2]) @ Q1[:, :2].T
-    assert np.allclose(pinv_fn(B), want, rtol=0, atol=1e-9)
+    want = (Q2 / s) @ Q1.T
+    assert np.linalg.norm(pinv_fn(B) - want) <= 1e-6 * np.linalg.norm(want)
     want_t = (Q2[:, :1] / s[:1]) @ Q1[:, :1].T
     assert np.allclose(pinv_fn(B, 1e-2), want_t, rtol=0, atol=1e-12)
+    Q3, _ = np.linalg.qr(g.standard_normal((50, 3)))
+    s2 = np.array([1.0, 1e-3, 3e-15])
+    B2 = (Q3 * s2) @ Q2.T
+    want2 = (Q2[:, :2] / s2[:2]) @ Q3[:, :2].T
+    assert np.allclose(pinv_fn(B2), want2, rtol=0, atol=1e-9)
     # full rank square: the inverse (LU, an independent routine)
     W = g.standard_normal((6, 6)) + 3 * np.eye(6)
     assert np.allclose(pinv_fn(W), np.linalg.solve(W, np.eye(6)), atol=1e-12)

@@ -5,8 +5,8 @@ Bars: the four index draws bit-exact. U* = C_bar^+ M R_bar^+ solves a least
 squares problem with a residual, whose solution moves by up to about
 eps (kappa_C^2 + kappa_R^2) relative when the pseudo-inverses are perturbed at
 the level eps (kappa: the condition number of the kept part of C_bar, R_bar);
-the GPU reaches them through Gram matrices, whose FP64 eigendecomposition
-carries exactly such an error. So U* must agree to
+the GPU reaches them through the FP64-accurate SVD of each block padded to
+K x K, whose singular vectors carry exactly such an error. So U* must agree to
 tol_U = 50 K 2^-52 (kappa_C^2 + kappa_R^2) relative (K = max(kb, kt); the 50
 covers the constants of the two SVDs' backward errors and the four products), and the
 product C U* R to tol_U |C| |U*| |R| / |A|. An exactly low-rank matrix is
@@ -51,7 +51,7 @@ def tol_u(ref, A_entries, trunc_rtol=0.0):
     kap = []
     for B in (Cbar, Rbar):
         sv = np.linalg.svd(B, compute_uv=False)
-        kept = sv[sv > max(trunc_rtol, np.sqrt(K * 2.0 ** -52)) * sv[0]]
+        kept = sv[sv > max(trunc_rtol, K * 2.0 ** -52) * sv[0]]
         kap.append(kept[0] / kept[-1])
     return 50 * K * 2.0 ** -52 * (kap[0] ** 2 + kap[1] ** 2)
 

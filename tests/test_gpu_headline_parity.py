@@ -156,3 +156,20 @@ def test_snap_two_row_cluster_ties(ctx, C, prec):
     got = to_np(order).tolist()
     assert got[:40] == [a for a, _ in pairs]
     assert got[40:] == [b for _, b in pairs[:10]]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_reduced_precision_excess_headline(ctx, C, dense_slice, prec):
+    """The precision bar at the dense benchmark's k = 256 (stabilised core,
+    truncation k 2^-24) on its slice: |err_mode / err_FP64 - 1| <= 1e-3, with
+    the FP64 mode's error equal to the oracle's (checked above)."""
+    A, Ad = dense_slice
+    m, n = A.shape
+    src = C.dense_source(Ad)
+    errs = {}
+    for pr in ("fp64", prec):
+        p = C.make_params(m, n, 256, iters=5, seed=1607, prec=pr, core="stabilized", trunc_rtol=256 * U_FP32,
+                          err_samples=0)
+        sk = C.cabs_sketch(ctx, src, p)
+        errs[pr] = float(to_np(sk.err)[0])
+    assert abs(errs[prec] / errs["fp64"] - 1) <= 1e-3, errs

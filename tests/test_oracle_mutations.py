@@ -112,6 +112,16 @@ def test_snap_mutants_rejected(old, new):
     assert rejects(lambda: pins.pin_snap_bruteforce(bad)) or rejects(lambda: pins.pin_snap_midpoint_tie(bad))
 
 
+@pytest.mark.parametrize("old,new", [
+    ("return U * np.sqrt(S)[None, :]", "return U * S[None, :]"),            # U S
+    ("return U * np.sqrt(S)[None, :]", "return U * (S ** 2)[None, :]"),     # U S^2
+    ("return U * np.sqrt(S)[None, :]", "return U * np.sqrt(S[::-1])[None, :]"),  # scales on the wrong columns
+])
+def test_embed_mutants_rejected(old, new):
+    bad = mutate(o.embed, old, new)
+    assert rejects(lambda: pins.pin_embed(bad, o.sketching, o.gather_dense))
+
+
 def test_error_mutant_rejected():
     bad = mutate(o.rel_fro_error_dense, "return math.sqrt(num / den) if den > 0 else 0.0",
                  "return num / den if den > 0 else 0.0")
@@ -157,10 +167,10 @@ CUR_MUTANTS = [
 ]
 
 PINV_MUTANTS = [
-    ("keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]",
-     "keep = sb > max(trunc_rtol, math.sqrt(min(B.shape) * EPS64)) * sb[0]"),
-    ("keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]",
-     "keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]"),
+    ("keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]",
+     "keep = sb > max(trunc_rtol, min(B.shape) * EPS64) * sb[0]"),
+    ("keep = sb > max(trunc_rtol, max(B.shape) * EPS64) * sb[0]",
+     "keep = sb > max(trunc_rtol, math.sqrt(max(B.shape) * EPS64)) * sb[0]"),
     ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep].T * sb[keep]) @ Ub[:, keep].T"),
     ("return (Vbt[keep].T / sb[keep]) @ Ub[:, keep].T", "return (Vbt[keep] / sb[keep][:, None]).T @ Ub[:, keep].T[::-1]"),
 ]

@@ -86,6 +86,10 @@ def test_unit_columns_truncation_and_svd():
     pins.pin_unit_columns_and_truncation(o.gather_dense, o.sketching)
 
 
+def test_embed_closed_form_and_pseudoskeleton():
+    pins.pin_embed(o.embed, o.sketching, o.gather_dense)
+
+
 def test_kmeans_bruteforce_optimum():
     pins.pin_kmeans_bruteforce_optimum(o.weighted_kmeans)
 

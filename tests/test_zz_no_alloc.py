@@ -4,7 +4,11 @@ during a step, or a program that reserved all device memory up front).
 
 It must return what cabs_error returns, call after call: its scratch is a
 fixed device array shared by every call, so two calls in a row also check
-that nothing left over from the first call leaks into the second. This file
+that nothing left over from the first call leaks into the second. In the
+TF32 and BF16 modes on a dense FP32 A, cabs_error forms the products on
+tensor cores while this variant uses FP32 CUDA-core products: there it must
+equal the FP32-mode value of the same factors and lie within 1e-3 relative
+of cabs_error's. This file
 is collected last on purpose; it also passes on its own in a fresh process.
 """
 import numpy as np
@@ -52,6 +56,22 @@ def test_fp32_exact_and_sampled_twice(ctx, C):
         for _ in range(2):
             got = C.cabs_error_noalloc(ctx, src, p, sk, samples=samples, seed=9)
             assert abs(got - want) <= 1e-9 * want, (samples, got, want)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_reduced_precision_exact_twice(ctx, C, prec):
+    A, _, _, _ = synth.decaying_lowrank_host(3000, 1700, rank=64, seed=3)
+    Ad = torch.from_numpy(A).cuda()
+    src = C.dense_source(Ad)
+    p = C.make_params(3000, 1700, 48, iters=3, seed=5, prec=prec, core="stabilized")
+    sk = C.cabs_sketch(ctx, src, p)
+    want_tc = C.cabs_error(ctx, src, p, sk)                     # tensor-core residual
+    p32 = C.make_params(3000, 1700, 48, iters=3, seed=5, prec="fp32", core="stabilized")
+    want_32 = C.cabs_error(ctx, src, p32, sk)                   # FP32 products, same factors
+    for _ in range(2):
+        got = C.cabs_error_noalloc(ctx, src, p, sk)
+        assert abs(got - want_32) <= 1e-9 * want_32, (got, want_32)
+        assert abs(got - want_tc) <= 1e-3 * want_tc, (got, want_tc)
 
 
 def test_rbf_sampled_twice(ctx, C):
