@@ -194,6 +194,19 @@ const char* cabs_last_error(cabs_ctx* ctx);
 /* Library version string. */
 const char* cabs_version(void);
 
+/* Polls a grid-wide barrier of a cooperative kernel (the FP64 refinement of
+ * the core SVD, the snap's greedy walk) makes before it gives up; a barrier
+ * that gives up sets bit 2 of cabs_diag.status, and every CTA of that kernel
+ * leaves it (the sketch's results are then not valid, but the context and
+ * the device stay usable). The paper has no counterpart: this is a control
+ * for tests of the bounded waits (a limit of 0 makes a wait give up at its
+ * first unsuccessful poll). polls >= 0 sets the limit for kernels enqueued
+ * from now on by every context of the process (a captured CUDA graph keeps
+ * the limit it was captured with); polls < 0 restores the default,
+ * CABS_WAIT_LIMIT_DEFAULT (about a second of polling). ctx must be non-NULL. */
+#define CABS_WAIT_LIMIT_DEFAULT 16777216
+cabs_status cabs_set_wait_limit(cabs_ctx* ctx, int64_t polls);
+
 /* ------------------------------------------------------- whole sketch */
 
 /* Bytes of device workspace cabs_sketch needs for these parameters. */

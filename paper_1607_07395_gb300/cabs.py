@@ -123,6 +123,7 @@ def lib():
         "cabs_profile_read": ([vp, C.c_char_p, i32, P(i64), P(f64), i32, i32], i32),
         "cabs_launch_count": ([], i64),
         "cabs_error_noalloc": ([vp, P(cabs_source), P(cabs_params), P(cabs_result), i64, u64, vp, P(f64)], i32),
+        "cabs_set_wait_limit": ([vp, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -140,7 +141,7 @@ def exported_names():
             "cabs_orthogonalize_workspace_size", "cabs_orthogonalize", "cabs_sketch_cur_workspace_size",
             "cabs_sketch_cur", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
-            "cabs_launch_count", "cabs_error_noalloc"]
+            "cabs_launch_count", "cabs_error_noalloc", "cabs_set_wait_limit"]
 
 
 def _check(status, ctx=None):
@@ -201,6 +202,15 @@ class Context:
 
 def cabs_version():
     return lib().cabs_version().decode()
+
+
+WAIT_LIMIT_DEFAULT = 16777216
+
+
+def cabs_set_wait_limit(ctx: Context, polls: int):
+    """Polls before a grid-wide barrier gives up (kernels enqueued from now
+    on); polls < 0 restores the default. A test control of the bounded waits."""
+    _check(lib().cabs_set_wait_limit(ctx.h, int(polls)), ctx.h)
 
 
 # ------------------------------------------------------------------ sources

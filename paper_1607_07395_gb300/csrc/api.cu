@@ -1,6 +1,7 @@
 // The C ABI of libcabs (declared in include/cabs.h): argument checks,
 // workspace layout, and the order in which one sketch (Algorithm 2) launches
 // the step kernels. No step runs on the host.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -57,6 +58,9 @@ SharersScope::SharersScope(int sharers) : prev(t_sharers) { t_sharers = sharers 
 SharersScope::~SharersScope() { t_sharers = prev; }
 
 int coop_grid_cap(int full) { return std::max(16, full / t_sharers); }
+
+static std::atomic<long long> g_wait_limit{CABS_WAIT_LIMIT_DEFAULT};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 DeviceGuard::DeviceGuard(int dev) {
   ok = cudaGetDevice(&prev) == cudaSuccess;
@@ -241,9 +245,9 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
     CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
                            &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, s));
     CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes,
-                         &dg->snap_fallbacks, s));
+                         &dg->snap_fallbacks, &dg->status, s));
     CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
-                         &dg->snap_fallbacks, s));
+                         &dg->snap_fallbacks, &dg->status, s));
   }
   if (p.flags & CABS_FLAG_FOLLOW_ERR) {
     CABS_TRY(launch_encoding_error(w.P, m, k1, out.rows, k2, p.prec, p.upsilon_pow, &dg->e_follow_rows, w.side_r,
@@ -326,6 +330,13 @@ void cabs_destroy(cabs_ctx* ctx) {
   for (cudaEvent_t e : ctx->lane_events) cudaEventDestroy(e);
   if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
   delete ctx;
+}
+
+cabs_status cabs_set_wait_limit(cabs_ctx* ctx, int64_t polls) {
+  clear_error();
+  CABS_REQUIRE(ctx != nullptr, "ctx is NULL");
+  g_wait_limit.store(polls < 0 ? (long long)CABS_WAIT_LIMIT_DEFAULT : (long long)polls, std::memory_order_relaxed);
+  return CABS_OK;
 }
 
 cabs_status cabs_workspace_size(const cabs_source* src, const cabs_params* p, size_t* bytes) {
@@ -501,7 +512,7 @@ cabs_status cabs_snap(cabs_ctx* ctx, const void* X, int64_t M, int32_t d, const 
   CABS_REQUIRE(X && Z && d_order && d_sorted, "NULL input or output");
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
-  return launch_snap(X, M, d, Z, k2, prec, d_order, d_sorted, ws, ws_bytes, nullptr, (cudaStream_t)stream);
+  return launch_snap(X, M, d, Z, k2, prec, d_order, d_sorted, ws, ws_bytes, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 cabs_status cabs_threshold_workspace_size(int64_t M, size_t* bytes) {

@@ -1,9 +1,11 @@
 // Grid-wide barrier for cooperative launches, with a bounded wait (internal).
 //
 // All CTAs of a cooperative launch arrive on a counter; the last one bumps a
-// generation word the others poll. A poll gives up after ~2^24 tries (about a
-// second), raising bar->err so that every CTA can leave the kernel instead of
-// hanging the GPU.
+// generation word the others poll. A poll gives up after bar->limit tries
+// (2^24 by default, about a second), raising bar->err so that every CTA can
+// leave the kernel instead of hanging the GPU. The limit is set when the
+// barrier is initialised (wait_limit(), settable through cabs_set_wait_limit
+// so that tests can make a wait run out).
 #pragma once
 
 #include "common.cuh"
@@ -15,7 +17,12 @@ struct GridBarrier {
   unsigned count;
   unsigned gen;
   int err;
+  int pad;
+  long long limit;  // polls before a wait gives up
 };
+
+// Poll limit for grid barriers initialised from now on (host).
+long long wait_limit();
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks) {
   __shared__ int ok;
@@ -31,8 +38,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks) {
       atomicAdd(&bar->gen, 1u);
     } else {
       long long spins = 0;
+      const long long limit = *(volatile long long*)&bar->limit;
       while (*vgen == g) {
-        if (++spins > (1ll << 24) || *(volatile int*)&bar->err) {
+        if (++spins > limit || *(volatile int*)&bar->err) {
           atomicOr(&bar->err, 1);
           ok = 0;
           break;

@@ -58,8 +58,9 @@ cabs_status launch_encoding_error(const void* X, int64_t M, int d, const int* re
 
 // a6: snap.
 size_t snap_ws_bytes(int64_t M, int d, int k2, int prec);
+// status (may be NULL): bit 2 is set when a grid barrier of the walk gave up.
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
-                        void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream);
+                        void* ws, size_t ws_bytes, int* fallbacks, int* status, cudaStream_t stream);
 
 // Section 5 follow-up variant (f): the k2 largest-norm rows of X, sorted.
 size_t threshold_ws_bytes(int64_t M);

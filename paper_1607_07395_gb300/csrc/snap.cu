@@ -305,7 +305,7 @@ template <typename T>
 __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
     const T* __restrict__ top_d, T tie_rtol, unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row,
-    T* fb_lim, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks) {
+    T* fb_lim, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks, int* status) {
   __shared__ T wd[kGreedyThreads / 32];
   __shared__ int wr[kGreedyThreads / 32];
   // CTA 0's walk reads the candidate lists, their distances, the centres'
@@ -320,6 +320,10 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
+  // a barrier that gave up: report it (diagnostics status bit 2) and leave
+  auto gave_up = [&]() {
+    if (tid == 0 && status) atomicOr(status, 4);
+  };
   for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < words; e += (long long)G * blockDim.x)
     taken[e] = 0u;
   if (blockIdx.x == 0) {
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       if (lane == 0) s_zz[j] = s;
     }
   }
-  if (!grid_sync(bar, G)) return;
+  if (!grid_sync(bar, G)) return gave_up();
   int j = 0;
   while (true) {
     if (blockIdx.x == 0 && wi == 0) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       }
       if (lane == 0) *next_fb = jj;
     }
-    if (!grid_sync(bar, G)) return;
+    if (!grid_sync(bar, G)) return gave_up();
     j = *(volatile int*)next_fb;
     if (j >= k2) break;
     // every CTA, pass 1: nearest untaken row of its slice for centre j
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     int brow;
     scan_slice(X, d, z, lo, hi, taken, T(-1), false, best, brow);
     cta_reduce(best, brow, false, wd, wr, cta_best, cta_row);
-    if (!grid_sync(bar, G)) return;
+    if (!grid_sync(bar, G)) return gave_up();
     if (blockIdx.x == 0 && tid == 0) {
       T bv = cta_best[0];
       int bi = cta_row[0];
@@ -384,11 +388,11 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       *(volatile T*)fb_lim = bv + tie_rtol * (bv + s_zz[j]);
       __threadfence();
     }
-    if (!grid_sync(bar, G)) return;
+    if (!grid_sync(bar, G)) return gave_up();
     // pass 2: lowest untaken row of the slice inside the window
     scan_slice(X, d, z, lo, hi, taken, *(volatile T*)fb_lim, true, best, brow);
     cta_reduce(best, brow, true, wd, wr, cta_best, cta_row);
-    if (!grid_sync(bar, G)) return;
+    if (!grid_sync(bar, G)) return gave_up();
     if (blockIdx.x == 0 && tid == 0) {
       int bi = cta_row[0];
       for (unsigned b = 1; b < G; ++b) bi = min(bi, cta_row[b]);
@@ -415,10 +419,11 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
   }
 }
 
-__global__ void snap_state_init_kernel(GridBarrier* bar, int* next_fb) {
+__global__ void snap_state_init_kernel(GridBarrier* bar, int* next_fb, long long limit) {
   bar->count = 0u;
   bar->gen = 0u;
   bar->err = 0;
+  bar->limit = limit;
   *next_fb = 0;
 }
 
@@ -461,7 +466,7 @@ SnapWs carve_snap(Carve& cv, int64_t M, int d, int k2, int prec) {
 
 template <typename T>
 cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int prec, int* order, int* sorted, void* ws,
-                       size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
+                       size_t ws_bytes, int* fallbacks, int* status, cudaStream_t stream) {
   Carve cv(ws, ws_bytes);
   SnapWs w = carve_snap(cv, M, d, k2, prec);
   if (!cv.fits()) {
@@ -485,7 +490,7 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
   const int G = std::max(1, std::min({(int)ceil_div(M, 2048), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
-  CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb));
+  CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb, wait_limit()));
   const T* Xc = X;
   const T* Zc = Z;
   const int* topr = w.top_r;
@@ -500,7 +505,7 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
   GridBarrier* bar = w.bar;
   long long Ml = M;
   void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &topd, &tie, &bm, &picks, &nfb, &cb, &cr, &lim, &bar, &order, &sorted,
-                  &fallbacks};
+                  &fallbacks, &status};
   CABS_LAUNCH(stream, "snap_greedy_kernel",
               cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args, 0,
                                           stream));
@@ -516,12 +521,12 @@ size_t snap_ws_bytes(int64_t M, int d, int k2, int prec) {
 }
 
 cabs_status launch_snap(const void* X, int64_t M, int d, const void* Z, int k2, int prec, int* order, int* sorted,
-                        void* ws, size_t ws_bytes, int* fallbacks, cudaStream_t stream) {
+                        void* ws, size_t ws_bytes, int* fallbacks, int* status, cudaStream_t stream) {
   if (prec == CABS_PREC_FP64)
     return snap_typed<double>((const double*)X, M, d, (const double*)Z, k2, prec, order, sorted, ws, ws_bytes,
-                              fallbacks, stream);
+                              fallbacks, status, stream);
   return snap_typed<float>((const float*)X, M, d, (const float*)Z, k2, prec, order, sorted, ws, ws_bytes, fallbacks,
-                           stream);
+                           status, stream);
 }
 
 }  // namespace cabs

@@ -794,13 +794,15 @@ constexpr int kGT = 16, kGK = 16;
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-__global__ void svd_flags_init_kernel(unsigned long long* maxoff, int iters, int* done_iter, GridBarrier* bar) {
+__global__ void svd_flags_init_kernel(unsigned long long* maxoff, int iters, int* done_iter, GridBarrier* bar,
+                                      long long limit) {
   if (threadIdx.x < 2 * iters) maxoff[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
     *done_iter = kNotDone;
     bar->count = 0u;
     bar->gen = 0u;
     bar->err = 0;
+    bar->limit = limit;
   }
 }
 
@@ -1560,7 +1562,7 @@ cabs_status launch_svd(const double* W, int k, double trunc_rtol, double resolve
   }
   // ---- Phase B: FP64 refinement, one cooperative launch
   CABS_LAUNCH(stream, "svd_flags_init",
-              svd_flags_init_kernel<<<1, 32, 0, stream>>>(w.maxoff, kItersB, w.done_iter, w.bar));
+              svd_flags_init_kernel<<<1, 32, 0, stream>>>(w.maxoff, kItersB, w.done_iter, w.bar, wait_limit()));
   {
     const int nt = ceil_div(k, kGT);
     const int tiles = nt * nt + nt * (nt + 1);  // work units of the widest phase
