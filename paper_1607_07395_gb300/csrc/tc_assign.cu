@@ -3,9 +3,12 @@
 //
 // The distance contraction x . z for all points x (rows of P or Q) and all
 // k2 <= 256 centres z is one tcgen05 MMA chain per 128-point tile: points
-// stream through a TMA ring, the centres (BF16, or TF32 when k <= 128) stay
-// resident in shared memory, and a 128 x 256 FP32 accumulator sits in TMEM
-// (two of them, so the epilogue of one tile overlaps the MMAs of the next).
+// stream through a TMA ring, the centres stay resident in shared memory, and
+// a 128 x 256 FP32 accumulator sits in TMEM (two of them, so the epilogue of
+// one tile overlaps the MMAs of the next). 256 TF32 centres of width above
+// 128 do not fit in shared memory: there the centres form two column blocks
+// of 128, each unit (row tile, block) keeps its block's two best per row,
+// and a per-row pass merges the blocks in order.
 // Epilogue warps read a row of accumulators per thread and form
 // |z|^2 - 2 x . z, keeping the best and second-best centre; warps holding
 // the two column halves of a row merge through shared memory. When the two
@@ -66,18 +69,34 @@ __device__ __forceinline__ void best2_push(Best2& s, float v, int j) {
   }
 }
 
+// Near-tie bound of the two best distances of a row (see the file comment).
 template <bool kTF32>
+__device__ __forceinline__ int near_tie_alt(const Best2& s, int k2, float xl, const float* __restrict__ zn) {
+  // the difference of two rounded contractions 2 x.z_a - 2 x.z_b is off by at
+  // most 4 u |x| (|z_a| + |z_b|) for operand rounding u (2^-8 BF16, 2^-10
+  // TF32); a 1.25x margin covers the FP32 accumulation
+  constexpr float rel = kTF32 ? 0.0048828125f : 0.01953125f;
+  if (s.j2 >= k2) return -1;
+  const float bound = rel * sqrtf(fmaxf(xl, 0.f)) * (sqrtf(fmaxf(zn[s.j1], 0.f)) + sqrtf(fmaxf(zn[s.j2], 0.f)));
+  return s.b2 - s.b1 <= bound ? s.j2 : -1;
+}
+
+// One CTA per SM over units (column block cb, row tile rt), column-block
+// major. BN = 256: every centre in one column block, labels written
+// directly. BN = 128 (TF32 with d > 128, where 256 resident TF32 centres do
+// not fit in shared memory): each unit leaves its block's best and second
+// best per row in part[l * ncb + cb], merged by tc_assign_merge_kernel.
+template <bool kTF32, int BN>
 __global__ void __launch_bounds__(tc::kThreads, 1)
     tc_assign_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                     const float* __restrict__ zn, const float* __restrict__ xn, const float* __restrict__ w,
-                     const float* __restrict__ X, const float* __restrict__ Z, int d, int M, int k2, int nch,
-                     int units, int* __restrict__ labels, int* __restrict__ alt, int* err) {
+                     const float* __restrict__ zn, const float* __restrict__ xn, int M, int k2, int nch, int MT,
+                     int units, int* __restrict__ labels, int* __restrict__ alt, Best2* __restrict__ part, int ncb,
+                     int* err) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ tc::Barriers bars;
   __shared__ Best2 xchg[4][32];
   uint8_t *Bres, *Aring;
-  tc::setup<kBN>(smem_raw, nch, Bres, Aring, &bars);
-  const int MT = units;  // one column block: every unit is a row tile
+  tc::setup<BN>(smem_raw, nch, Bres, Aring, &bars);
   const int u0 = (int)((long long)units * blockIdx.x / gridDim.x);
   const int u1 = (int)((long long)units * (blockIdx.x + 1) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -85,21 +104,18 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
     if (lane == 0) {
       tc::prefetch_tmap(&tmA);
       tc::prefetch_tmap(&tmB);
-      tc::producer_loop<kBN>(&tmA, &tmB, Bres, Aring, &bars, u0, u1, MT, nch, AsgCfg<kTF32>::KC);
+      tc::producer_loop<BN>(&tmA, &tmB, Bres, Aring, &bars, u0, u1, MT, nch, AsgCfg<kTF32>::KC);
     }
   } else if (warp == 1) {
-    if (lane == 0) tc::mma_loop<kTF32, kBN>(Bres, Aring, &bars, u0, u1, MT, nch);
+    if (lane == 0) tc::mma_loop<kTF32, BN>(Bres, Aring, &bars, u0, u1, MT, nch);
   } else if (warp >= tc::kEpiWarp0) {
     const int e = warp - tc::kEpiWarp0;
     const int sub = warp & 3, half = e >> 2;
     const int row = sub * 32 + lane;
-    // the difference of two rounded contractions 2 x.z_a - 2 x.z_b is off by at
-    // most 4 u |x| (|z_a| + |z_b|) for operand rounding u (2^-8 BF16, 2^-10
-    // TF32); a 1.25x margin covers the FP32 accumulation
-    const float rel = kTF32 ? 0.0048828125f : 0.01953125f;
     int ab = 0;
     uint32_t accph[2] = {0, 0};
     for (int u = u0; u < u1; ++u) {
+      const int cb = u / MT, rt = u - cb * MT;
       // every epilogue warp must leave together: they share named barrier 1
       const int fail = tc::mbar_wait(&bars.accfull[ab], accph[ab], &bars.abort) ? 0 : 1;
       int anyfail;
@@ -113,11 +129,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       tc::fence_after_sync();
       Best2 s{__int_as_float(0x7f800000), __int_as_float(0x7f800000), 0x7fffffff, 0x7fffffff};
 #pragma unroll 1
-      for (int j = 0; j < kBN / 2 / 32; ++j) {
-        const int c0 = half * (kBN / 2) + j * 32;
-        if (c0 >= k2) break;  // warp-uniform
+      for (int j = 0; j < BN / 2 / 32; ++j) {
+        const int lc = half * (BN / 2) + j * 32;  // column inside the block
+        const int c0 = cb * BN + lc;              // centre index
+        if (c0 >= k2) break;                      // warp-uniform
         float v[32];
-        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * kBN + c0) + ((uint32_t)(sub * 32) << 16), v);
+        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * BN + lc) + ((uint32_t)(sub * 32) << 16), v);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const int jj = c0 + q;
@@ -135,22 +152,39 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         const Best2 o = xchg[sub][lane];
         best2_push(s, o.b1, o.j1);
         best2_push(s, o.b2, o.j2);
-        const long long l = (long long)u * tc::kBM + row;
+        const long long l = (long long)rt * tc::kBM + row;
         if (l < M) {
-          int a2 = -1;
-          if (s.j2 < k2) {
-            const float xl = xn[l];
-            const float bound = rel * sqrtf(fmaxf(xl, 0.f)) * (sqrtf(fmaxf(zn[s.j1], 0.f)) + sqrtf(fmaxf(zn[s.j2], 0.f)));
-            if (s.b2 - s.b1 <= bound) a2 = s.j2;
+          if (part) {
+            part[l * ncb + cb] = s;
+          } else {
+            labels[l] = s.j1;
+            alt[l] = near_tie_alt<kTF32>(s, k2, xn[l], zn);
           }
-          labels[l] = s.j1;
-          alt[l] = a2;
         }
       }
       asm volatile("bar.sync 1, %0;" ::"n"(tc::kEpiWarps * 32));
     }
   }
-  tc::teardown<kBN>(&bars, err);
+  tc::teardown<BN>(&bars, err);
+}
+
+// Per row: the column blocks' best and second best merged in block order
+// (ties to the lower centre), then the label and the near-tie flag.
+template <bool kTF32>
+__global__ void __launch_bounds__(256) tc_assign_merge_kernel(const Best2* __restrict__ part, int ncb, long long M,
+                                                              int k2, const float* __restrict__ xn,
+                                                              const float* __restrict__ zn, int* __restrict__ labels,
+                                                              int* __restrict__ alt) {
+  for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < M; l += (long long)gridDim.x * blockDim.x) {
+    Best2 s = part[l * ncb];
+    for (int cb = 1; cb < ncb; ++cb) {
+      const Best2 o = part[l * ncb + cb];
+      best2_push(s, o.b1, o.j1);
+      best2_push(s, o.b2, o.j2);
+    }
+    labels[l] = s.j1;
+    alt[l] = near_tie_alt<kTF32>(s, k2, xn[l], zn);
+  }
 }
 
 // Rows whose two best centres were closer than the operand rounding bound:
@@ -195,12 +229,17 @@ __global__ void __launch_bounds__(256) assign_resolve_kernel(const float* __rest
 struct TcWs {
   void *Pp, *Zp;
   int *alt, *err;
+  Best2* part;  // per-row, per-column-block best two (two-block TF32 form)
 };
 
 int kp_of(int d, bool tf32) {
   const int KC = tf32 ? 32 : 64;
   return (d + KC - 1) / KC * KC;
 }
+
+// Centres per column block: all 256 when their operand block fits in 128 KB
+// of shared memory (BF16 up to d = 256, TF32 up to d = 128), else 128.
+int block_n(int d, bool tf32) { return (size_t)kp_of(d, tf32) / (tf32 ? 32 : 64) * kBN * 128 > 128 * 1024 ? 128 : kBN; }
 
 TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
   const int Kp = kp_of(d, tf32);
@@ -210,21 +249,40 @@ TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
   w.Zp = cv.take<char>((size_t)kBN * Kp * es);
   w.alt = cv.take<int>(M);
   w.err = cv.take<int>(1);
+  w.part = cv.take<Best2>((size_t)M * (kBN / 128));
   return w;
+}
+
+template <bool kTF32, int BN>
+cabs_status launch_assign(const CUtensorMap& tmA, const CUtensorMap& tmB, const float* zn, const float* xn, int64_t M,
+                          int k2, int nch, int* labels, TcWs& t, cudaStream_t stream) {
+  const int MT = ceil_div(M, tc::kBM);
+  const int ncb = ceil_div(k2, BN);
+  const int units = MT * ncb;
+  const int grid = std::max(1, std::min(units, sm_count()));
+  const size_t smem = tc::smem_bytes(nch, BN);
+  cudaFuncSetAttribute(tc_assign_kernel<kTF32, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  Best2* part = BN == kBN ? nullptr : t.part;
+  CABS_LAUNCH(stream, "tc_assign_kernel",
+              (tc_assign_kernel<kTF32, BN><<<grid, tc::kThreads, smem, stream>>>(
+                  tmA, tmB, zn, xn, (int)M, k2, nch, MT, units, labels, t.alt, part, ncb, t.err)));
+  if (part)
+    CABS_LAUNCH(stream, "tc_assign_merge_kernel",
+                tc_assign_merge_kernel<kTF32><<<std::max(1, std::min(ceil_div(M, 256), sm_count() * 4)), 256, 0,
+                                                stream>>>(part, ncb, M, k2, xn, zn, labels, t.alt));
+  return CABS_OK;
 }
 
 template <bool kTF32>
 cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, const float* zn, int k2, const float* xn,
                             const float* w, int* labels, int* d_recheck, bool prep_points, void* tcws,
                             cudaStream_t stream) {
+  (void)w;
   Carve cv(tcws, (size_t)-1);
   TcWs t = carve_tc(cv, M, d, k2, kTF32);
   const int Kp = kp_of(d, kTF32);
   const int nch = Kp / AsgCfg<kTF32>::KC;
-  if (kTF32 && nch * kBN * 128 > 128 * 1024) {
-    set_error("TF32 k-means assignment supports embedding widths up to 128 (got %d); use BF16", d);
-    return CABS_EINVAL;
-  }
+  const int BN = block_n(d, kTF32);
   const int sms = sm_count();
   if (prep_points)
     CABS_LAUNCH(stream, "tc_assign_points_prep",
@@ -237,14 +295,12 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
   CUtensorMap tmA, tmB;
   const int dt = kTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   CABS_TRY(make_tmap_2d(&tmA, t.Pp, dt, M, Kp, (uint64_t)Kp * AsgCfg<kTF32>::ES, AsgCfg<kTF32>::KC, tc::kBM));
-  CABS_TRY(make_tmap_2d(&tmB, t.Zp, dt, k2, Kp, (uint64_t)Kp * AsgCfg<kTF32>::ES, AsgCfg<kTF32>::KC, kBN));
-  const int units = ceil_div(M, tc::kBM);
-  const int grid = tc_assign_blocks(M);
-  const size_t smem = tc::smem_bytes(nch, kBN);
-  cudaFuncSetAttribute(tc_assign_kernel<kTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  CABS_LAUNCH(stream, "tc_assign_kernel",
-              tc_assign_kernel<kTF32><<<grid, tc::kThreads, smem, stream>>>(
-                  tmA, tmB, zn, xn, w, X, Z, d, (int)M, k2, nch, units, labels, t.alt, t.err));
+  // rows of a block's box at or beyond k2 lie outside the map and load as zeros
+  CABS_TRY(make_tmap_2d(&tmB, t.Zp, dt, k2, Kp, (uint64_t)Kp * AsgCfg<kTF32>::ES, AsgCfg<kTF32>::KC, BN));
+  if (BN == kBN)
+    CABS_TRY((launch_assign<kTF32, kBN>(tmA, tmB, zn, xn, M, k2, nch, labels, t, stream)));
+  else
+    CABS_TRY((launch_assign<kTF32, 128>(tmA, tmB, zn, xn, M, k2, nch, labels, t, stream)));
   CABS_LAUNCH(stream, "assign_resolve_kernel",
               assign_resolve_kernel<<<std::max(1, std::min(ceil_div(M, 256), sms * 8)), 256, 0, stream>>>(
                   X, M, d, Z, labels, t.alt, d_recheck));

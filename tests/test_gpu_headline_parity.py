@@ -158,7 +158,7 @@ def test_snap_two_row_cluster_ties(ctx, C, prec):
     assert got[40:] == [b for _, b in pairs[:10]]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_reduced_precision_excess_headline(ctx, C, dense_slice, prec):
     """The precision bar at the dense benchmark's k = 256 (stabilised core,
     truncation k 2^-24) on its slice: |err_mode / err_FP64 - 1| <= 1e-3, with

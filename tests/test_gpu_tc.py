@@ -66,7 +66,8 @@ def test_tc_residual_matches_exact(ctx, C, prec, m, n, lda, k):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
-@pytest.mark.parametrize("M,d,k2", [(2000, 20, 20), (9000, 64, 64), (4099, 128, 100), (70000, 64, 256)])
+@pytest.mark.parametrize("M,d,k2", [(2000, 20, 20), (9000, 64, 64), (4099, 128, 100), (70000, 64, 256),
+                                    (9001, 256, 256), (5000, 200, 200), (3001, 160, 129), (2000, 256, 100)])
 def test_tc_assign_matches_oracle(ctx, C, prec, M, d, k2):
     g = np.random.default_rng(M + d)
     centers = 3.0 * g.standard_normal((50, d))
