@@ -227,7 +227,8 @@ cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params
 /* `count` independent sketches of different sizes in one call. Member i uses
  * src[i], p[i], out[i] and the workspace slice ws + ws_offsets[i] (host array
  * of byte offsets, each 256-aligned, slices of cabs_workspace_size bytes).
- * Members are scheduled largest-first over `lanes` (1..16) internal streams
+ * Members are scheduled largest-first over `lanes` (1..16; 0 = the lanes
+ * cabs_autotune chose for this context, else 8) internal streams
  * forked from and joined back to `stream`; with CUDA graphs enabled
  * (use_graph != 0) the launch sequence of the batch is captured once per
  * distinct batch layout and replayed. Results are bit-identical to running
@@ -236,6 +237,54 @@ cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const cabs_source*
                                 const cabs_params* p, void* ws, const size_t* ws_offsets,
                                 const cabs_result* out, int32_t lanes, int32_t use_graph,
                                 cabs_stream stream);
+
+/* ------------------------------------------------------------ launch shapes
+ *
+ * The paper has no counterpart: these choose how the kernels split their work
+ * over the GPU, never what they compute. Every choice gives results bit-
+ * identical to the defaults (each output keeps its summation order). A
+ * context keeps one cabs_tune per shape bucket -- (prec, ceil(k2 / 32),
+ * floor(log2(m + n))) -- which cabs_sketch, cabs_sketch_batched and the
+ * serving loop use for every sketch of that bucket; buckets without an entry
+ * use the defaults. cabs_autotune fills the table from timed trials. */
+typedef struct {
+  int32_t extrap_tn;    /* extrapolation GEMMs (C V_w, R^T U_w): output columns per
+                         * thread, 16 extrap_tn per CTA: 2, 4 or 8 (8 in FP32 modes
+                         * only); 0 = default (8 FP32, 4 FP64) */
+  int32_t gather_rows;  /* dense column gather: rows of A per warp in flight: 2, 4 or
+                         * 8; 0 = default (4) */
+  int32_t assign_bn;    /* TF32 / BF16 k-means assignment: centres per tensor-core
+                         * column block, 128 or 256 (128 always for TF32 widths above
+                         * 128); 0 = default (256) */
+  int32_t reserved;     /* 0 */
+} cabs_tune;
+
+/* Sets (t != NULL) or removes (t == NULL) the entry of the bucket of (prec, k2,
+ * m, n). CABS_EINVAL for a value outside the ranges above. */
+cabs_status cabs_tune_set(cabs_ctx* ctx, int32_t prec, int32_t k2, int64_t m, int64_t n, const cabs_tune* t);
+/* The entry in force for (prec, k2, m, n): the bucket's, else the defaults
+ * (all fields 0). *found (may be NULL) is 1 for a bucket entry. */
+cabs_status cabs_tune_get(cabs_ctx* ctx, int32_t prec, int32_t k2, int64_t m, int64_t n, cabs_tune* t,
+                          int32_t* found);
+/* Writes the table and the tuned lanes to a text file (one line per bucket:
+ * "bucket prec kb sb extrap_tn gather_rows assign_bn"; a "lanes L" line), or
+ * replaces the context's table with a file's. CABS_EINVAL for an unreadable,
+ * unwritable or malformed file (the table is then unchanged). */
+cabs_status cabs_tune_save(cabs_ctx* ctx, const char* path);
+cabs_status cabs_tune_load(cabs_ctx* ctx, const char* path);
+/* Autotuner. For every shape bucket among the `count` members (as for
+ * cabs_sketch_batched: their sources, parameters, workspace slices and
+ * outputs, which it overwrites), times one representative member's whole
+ * sketch on `stream` under each candidate launch shape -- coordinate descent
+ * over extrap_tn, gather_rows and assign_bn, the fastest of 5 runs per
+ * candidate, a change kept only if it is at least 2 % faster -- and stores
+ * the winner in the table. Then it times the whole batch (no graph) at 4, 8,
+ * 12 and 16 lanes and keeps the fastest for cabs_sketch_batched with lanes
+ * == 0. *lanes_out (may be NULL) receives it. Synchronises `stream`; takes
+ * a few seconds for a batch of hundreds of members. */
+cabs_status cabs_autotune(cabs_ctx* ctx, int32_t count, const cabs_source* src, const cabs_params* p, void* ws,
+                          const size_t* ws_offsets, const cabs_result* out, cabs_stream stream,
+                          int32_t* lanes_out);
 
 /* Relative Frobenius error |A - U diag(S) V^T|_F / |A|_F (Section 5).
  * samples == 0: exact, over every entry (dense sources only; FP64 sums of

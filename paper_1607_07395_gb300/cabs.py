@@ -63,6 +63,10 @@ class cabs_result(C.Structure):
                 ("diag", C.c_void_p), ("err", C.c_void_p)]
 
 
+class cabs_tune(C.Structure):
+    _fields_ = [("extrap_tn", C.c_int32), ("gather_rows", C.c_int32), ("assign_bn", C.c_int32), ("reserved", C.c_int32)]
+
+
 class cabs_cur_params(C.Structure):
     _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("kb", C.c_int32), ("kt", C.c_int32), ("seed", C.c_uint64),
                 ("prec", C.c_int32), ("trunc_rtol", C.c_double)]
@@ -124,6 +128,11 @@ def lib():
         "cabs_launch_count": ([], i64),
         "cabs_error_noalloc": ([vp, P(cabs_source), P(cabs_params), P(cabs_result), i64, u64, vp, P(f64)], i32),
         "cabs_set_wait_limit": ([vp, i64], i32),
+        "cabs_tune_set": ([vp, i32, i32, i64, i64, P(cabs_tune)], i32),
+        "cabs_tune_get": ([vp, i32, i32, i64, i64, P(cabs_tune), P(i32)], i32),
+        "cabs_tune_save": ([vp, C.c_char_p], i32),
+        "cabs_tune_load": ([vp, C.c_char_p], i32),
+        "cabs_autotune": ([vp, i32, P(cabs_source), P(cabs_params), vp, P(sz), P(cabs_result), vp, P(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -141,7 +150,8 @@ def exported_names():
             "cabs_orthogonalize_workspace_size", "cabs_orthogonalize", "cabs_sketch_cur_workspace_size",
             "cabs_sketch_cur", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
-            "cabs_launch_count", "cabs_error_noalloc", "cabs_set_wait_limit"]
+            "cabs_launch_count", "cabs_error_noalloc", "cabs_set_wait_limit", "cabs_tune_set", "cabs_tune_get",
+            "cabs_tune_save", "cabs_tune_load", "cabs_autotune"]
 
 
 def _check(status, ctx=None):
@@ -336,6 +346,45 @@ def cabs_sketch_batched(ctx: Context, srcs, params, outs, ws, offsets, lanes=4, 
     OA = (C.c_size_t * n)(*offsets)
     wp, _ = _aligned(ws)
     _check(lib().cabs_sketch_batched(ctx.h, n, SA, PA, wp, OA, RA, lanes, int(use_graph), _stream(stream)), ctx.h)
+
+
+def cabs_tune_set(ctx: Context, p: cabs_params, tune=None):
+    """Sets (tune: a cabs_tune or a dict of its fields) or removes (None) the
+    launch shape of the bucket of p's (prec, k2, m, n)."""
+    t = None
+    if tune is not None:
+        t = tune if isinstance(tune, cabs_tune) else cabs_tune(**tune)
+    _check(lib().cabs_tune_set(ctx.h, p.prec, p.k2, p.m, p.n, C.byref(t) if t is not None else None), ctx.h)
+
+
+def cabs_tune_get(ctx: Context, p: cabs_params):
+    """(dict of the launch shape in force for p's bucket, found)."""
+    t = cabs_tune()
+    f = C.c_int32()
+    _check(lib().cabs_tune_get(ctx.h, p.prec, p.k2, p.m, p.n, C.byref(t), C.byref(f)), ctx.h)
+    return dict(extrap_tn=t.extrap_tn, gather_rows=t.gather_rows, assign_bn=t.assign_bn), bool(f.value)
+
+
+def cabs_tune_save(ctx: Context, path: str):
+    _check(lib().cabs_tune_save(ctx.h, path.encode()), ctx.h)
+
+
+def cabs_tune_load(ctx: Context, path: str):
+    _check(lib().cabs_tune_load(ctx.h, path.encode()), ctx.h)
+
+
+def cabs_autotune(ctx: Context, srcs, params, outs, ws, offsets, stream=None) -> int:
+    """Fills the context's launch-shape table from timed trials on the batch
+    (whose outputs it overwrites) and returns the lanes it chose."""
+    n = len(srcs)
+    SA = (cabs_source * n)(*[s.c for s in srcs])
+    PA = (cabs_params * n)(*params)
+    RA = (cabs_result * n)(*[o.result for o in outs])
+    OA = (C.c_size_t * n)(*offsets)
+    wp, _ = _aligned(ws)
+    lanes = C.c_int32()
+    _check(lib().cabs_autotune(ctx.h, n, SA, PA, wp, OA, RA, _stream(stream), C.byref(lanes)), ctx.h)
+    return lanes.value
 
 
 def batched_layout(srcs, params):

@@ -367,6 +367,7 @@ cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params
     set_error("cannot select CUDA device %d", ctx->device);
     return CABS_ECUDA;
   }
+  TuneScope shape(tune_lookup(ctx, *p));
   return sketch_enqueue(*src, *p, ws, ws_bytes, (cudaStream_t)stream, *out);
 }
 
@@ -630,7 +631,7 @@ static uint64_t batch_key(int count, const cabs_source* src, const cabs_params* 
   return h;
 }
 
-static cabs_status ensure_lanes(cabs_ctx* ctx, int lanes) {
+cabs_status ensure_lanes(cabs_ctx* ctx, int lanes) {
   while ((int)ctx->lanes.size() < lanes) {
     cudaStream_t s;
     cudaEvent_t e;
@@ -642,7 +643,7 @@ static cabs_status ensure_lanes(cabs_ctx* ctx, int lanes) {
   return CABS_OK;
 }
 
-static cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* src, const cabs_params* p, void* ws,
+cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* src, const cabs_params* p, void* ws,
                                    const size_t* off, const cabs_result* out, int lanes, cudaStream_t s) {
   // largest members first, dealt round-robin to the lanes
   std::vector<int> order(count);
@@ -659,6 +660,7 @@ static cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* 
   for (int t = 0; t < count; ++t) {
     const int i = order[t];
     const size_t need = sketch_ws_bytes(src[i], p[i]);
+    TuneScope shape(tune_lookup(ctx, p[i]));
     CABS_TRY(sketch_enqueue(src[i], p[i], (char*)ws + off[i], need, ctx->lanes[t % lanes], out[i]));
   }
   for (int l = 0; l < lanes; ++l) {
@@ -678,7 +680,11 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
   CABS_REQUIRE(count >= 0, "count < 0");
   if (count == 0) return CABS_OK;
   CABS_REQUIRE(src && p && out && ws && ws_offsets, "NULL array");
-  CABS_REQUIRE(lanes >= 1 && lanes <= 16, "lanes outside [1, 16]");
+  CABS_REQUIRE(lanes >= 0 && lanes <= 16, "lanes outside [0, 16]");
+  if (lanes == 0) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    lanes = ctx->tuned_lanes > 0 ? ctx->tuned_lanes : 8;
+  }
   for (int i = 0; i < count; ++i) {
     CABS_TRY(validate_params(&p[i]));
     CABS_TRY(validate_source(&src[i], p[i].m, p[i].n));
@@ -691,7 +697,11 @@ extern "C" cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const c
   cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph) return batched_enqueue(ctx, count, src, p, ws, ws_offsets, out, lanes, s);
   CABS_REQUIRE(s != nullptr, "graph replay needs a non-default stream");
-  const uint64_t key = batch_key(count, src, p, ws, ws_offsets, out, lanes);
+  uint64_t key = batch_key(count, src, p, ws, ws_offsets, out, lanes);
+  {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    key = mix(key, ctx->tune_version);  // launch shapes changed: capture again
+  }
   std::lock_guard<std::mutex> lock(ctx->graph_mu);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {

@@ -51,12 +51,26 @@ cabs_status validate_params(const cabs_params* p);
 cabs_status validate_result(const cabs_result* out);
 cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
                            const cabs_result& out);
+// Batched form: members largest first over `lanes` internal streams forked
+// from and joined back to s (each member under its bucket's launch shape).
+cabs_status ensure_lanes(cabs_ctx* ctx, int lanes);
+cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* src, const cabs_params* p, void* ws,
+                            const size_t* off, const cabs_result* out, int lanes, cudaStream_t s);
+// The tuning-table bucket of a sketch shape and the entry in force for it.
+uint32_t tune_bucket(int prec, int k, int64_t m, int64_t n);
+cabs_tune tune_lookup(cabs_ctx* ctx, const cabs_params& p);
 
 }  // namespace cabs
 
 // The opaque context of the ABI.
 struct cabs_ctx {
   int device = 0;
+  // launch shapes per shape bucket (cabs_tune_set / cabs_autotune) and the
+  // lanes cabs_autotune chose for batches; version bumps invalidate graphs
+  std::mutex tune_mu;
+  std::unordered_map<uint32_t, cabs_tune> tune;
+  int tuned_lanes = 0;
+  uint64_t tune_version = 0;
   std::mutex graph_mu;
   std::unordered_map<uint64_t, cabs::GraphEntry> graphs;
   std::vector<cudaStream_t> lanes;

@@ -203,4 +203,16 @@ struct SharersScope {
   int prev;
 };
 
+// Launch shapes of the tunable kernels for the sketch being enqueued on the
+// calling thread (cabs_tune of the ABI, 0 = the kernel's default). The ABI
+// layer looks up the shape bucket of each sketch in its context's table and
+// holds a TuneScope while it enqueues that sketch. No choice here changes a
+// result: only which thread computes which output.
+const cabs_tune& current_tune();
+struct TuneScope {
+  explicit TuneScope(const cabs_tune& t);
+  ~TuneScope();
+  cabs_tune prev;
+};
+
 }  // namespace cabs

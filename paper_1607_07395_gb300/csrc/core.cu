@@ -29,6 +29,8 @@ namespace {
 // per TM TN multiply-adds. Every output sums over K in ascending order, as a
 // plain loop would, whatever the tile shape.
 constexpr int kGBK = 16;
+// The output columns per thread (TN) are a launch shape: the row tiling (TM,
+// BM) fixes the per-CTA column partials, so any TN gives identical results.
 template <typename T>
 struct ExtrapTile {
   static constexpr int TM = sizeof(T) == 4 ? 8 : 4;
@@ -36,12 +38,12 @@ struct ExtrapTile {
   static constexpr int BM = 16 * TM, BN = 16 * TN;
 };
 
-template <typename T>
+template <typename T, int TN = ExtrapTile<T>::TN>
 __global__ void __launch_bounds__(256) extrap_gemm_kernel(const T* __restrict__ X, long long M, int K,
                                                          const double* __restrict__ B, int N, T* __restrict__ out,
                                                          double* __restrict__ part) {
-  constexpr int TM = ExtrapTile<T>::TM, TN = ExtrapTile<T>::TN;
-  constexpr int BM = ExtrapTile<T>::BM, BN = ExtrapTile<T>::BN;
+  constexpr int TM = ExtrapTile<T>::TM;
+  constexpr int BM = ExtrapTile<T>::BM, BN = 16 * TN;
   constexpr int LA = BM * kGBK / 256, LB = BN * kGBK / 256;  // elements each thread stages per chunk
   // A and B double buffers; the column sums reuse the space after the loop
   constexpr size_t kAB = sizeof(T) * 2 * kGBK * ((BM + 4) + (BN + 4));
@@ -215,6 +217,30 @@ CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
   return w;
 }
 
+// The two extrapolation products C V_w and R^T U_w with TN output columns
+// per thread (the launch shape of the sketch's bucket; 0 = the default).
+template <typename T, int TN>
+cabs_status extrap_pair_tn(const T* C, int64_t m, const T* Rt, int64_t n, int k, const double* Vw, const double* Uw,
+                           T* out1, T* out2, double* part1, double* part2, cudaStream_t stream) {
+  constexpr int BM = ExtrapTile<T>::BM, BN = 16 * TN;
+  dim3 g1(ceil_div(k, BN), ceil_div(m, BM)), g2(ceil_div(k, BN), ceil_div(n, BM));
+  CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)",
+              (extrap_gemm_kernel<T, TN><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, part1)));
+  CABS_LAUNCH(stream, "extrap_gemm_kernel(Rt U_w)",
+              (extrap_gemm_kernel<T, TN><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, part2)));
+  return CABS_OK;
+}
+
+template <typename T>
+cabs_status extrap_pair(int tn, const T* C, int64_t m, const T* Rt, int64_t n, int k, const double* Vw,
+                        const double* Uw, T* out1, T* out2, double* part1, double* part2, cudaStream_t stream) {
+  if (tn == 2) return extrap_pair_tn<T, 2>(C, m, Rt, n, k, Vw, Uw, out1, out2, part1, part2, stream);
+  if (tn == 4) return extrap_pair_tn<T, 4>(C, m, Rt, n, k, Vw, Uw, out1, out2, part1, part2, stream);
+  if constexpr (sizeof(T) == 4)
+    if (tn == 8) return extrap_pair_tn<T, 8>(C, m, Rt, n, k, Vw, Uw, out1, out2, part1, part2, stream);
+  return extrap_pair_tn<T, ExtrapTile<T>::TN>(C, m, Rt, n, k, Vw, Uw, out1, out2, part1, part2, stream);
+}
+
 template <typename T>
 cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol, const T* C, const T* Rt,
                        const double* W, bool embed, T* out1, double* S, T* out2, int* d_rank, int* d_sweeps,
@@ -234,9 +260,8 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   CABS_TRY(launch_svd(W, k, trunc_rtol, sizeof(T) == 8 ? 0.0 : kResolveReduced, sig, Uw, Vw, rank, sweeps, d_refine,
                       d_status, w.svd, stream));
   const int nb1 = ceil_div(m, ExtrapTile<T>::BM), nb2 = ceil_div(n, ExtrapTile<T>::BM);
-  dim3 g1(ceil_div(k, ExtrapTile<T>::BN), nb1), g2(ceil_div(k, ExtrapTile<T>::BN), nb2);
-  CABS_LAUNCH(stream, "extrap_gemm_kernel(C V_w)", extrap_gemm_kernel<T><<<g1, 256, 0, stream>>>(C, m, k, Vw, k, out1, w.part1));
-  CABS_LAUNCH(stream, "extrap_gemm_kernel(Rt U_w)", extrap_gemm_kernel<T><<<g2, 256, 0, stream>>>(Rt, n, k, Uw, k, out2, w.part2));
+  const int tn = current_tune().extrap_tn;
+  CABS_TRY(extrap_pair<T>(tn, C, m, Rt, n, k, Vw, Uw, out1, out2, w.part1, w.part2, stream));
   const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);
   CABS_LAUNCH(stream, "core_finalize_kernel",
               core_finalize_kernel<<<k, 256, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,

@@ -32,7 +32,8 @@ constexpr int kGatherThreads = 256;
 constexpr int kRowsPerWarp = 4;
 constexpr int kMaxColsPerLane = CABS_MAX_K / 32;
 
-template <typename Tin, typename Tout>
+// kRows rows per warp (the launch shape: loads in flight per thread).
+template <typename Tin, typename Tout, int kRows = kRowsPerWarp>
 __global__ void __launch_bounds__(kGatherThreads) gather_cols_kernel(const Tin* __restrict__ A, long long lda,
                                                                      long long m, long long n,
                                                                      const int* __restrict__ cols, int kc,
@@ -49,10 +50,10 @@ __global__ void __launch_bounds__(kGatherThreads) gather_cols_kernel(const Tin* 
     const int t = lane + 32 * q;
     col[q] = t < kc ? cs[t] : 0;
   }
-  for (long long i0 = warp * kRowsPerWarp; i0 < m; i0 += nwarps * kRowsPerWarp) {
-    Tin v[kRowsPerWarp][kMaxColsPerLane];
+  for (long long i0 = warp * kRows; i0 < m; i0 += nwarps * kRows) {
+    Tin v[kRows][kMaxColsPerLane];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
+    for (int r = 0; r < kRows; ++r) {
       const long long i = i0 + r;
       const Tin* row = A + (i < m ? i : 0) * lda;
 #pragma unroll
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kGatherThreads) gather_cols_kernel(const Tin* 
       }
     }
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
+    for (int r = 0; r < kRows; ++r) {
       const long long i = i0 + r;
       if (i >= m) break;
       Tout* out = C + i * kc;
@@ -208,18 +209,31 @@ __global__ void zero_kernel(Tout* __restrict__ x, long long count) {
     x[e] = Tout(0);
 }
 
+template <typename Tout, int kRows>
+cabs_status gather_cols_dense(const cabs_source& src, int64_t m, int64_t n, const int* cols, int kc, Tout* C,
+                              cudaStream_t stream) {
+  const int blocks = std::max(1, std::min(ceil_div(m, (kGatherThreads / 32) * kRows), sm_count() * 8));
+  CABS_LAUNCH(stream, "gather_cols_kernel",
+              if (src.a_is_f64)(gather_cols_kernel<double, Tout, kRows><<<blocks, kGatherThreads, 0, stream>>>(
+                  (const double*)src.A, src.lda, m, n, cols, kc, C));
+              else(gather_cols_kernel<float, Tout, kRows><<<blocks, kGatherThreads, 0, stream>>>(
+                  (const float*)src.A, src.lda, m, n, cols, kc, C)));
+  return CABS_OK;
+}
+
 template <typename Tout>
 cabs_status gather_typed(const cabs_source& src, int64_t m, int64_t n, const int* rows, int kr, const int* cols,
                          int kc, Tout* C, Tout* Rt, double* W, cudaStream_t stream) {
   const int sms = sm_count();
   if (src.kind == CABS_SRC_DENSE) {
     if (C && kc > 0) {
-      const int blocks = std::max(1, std::min(ceil_div(m, (kGatherThreads / 32) * kRowsPerWarp), sms * 8));
-      CABS_LAUNCH(stream, "gather_cols_kernel",
-                  if (src.a_is_f64) gather_cols_kernel<double, Tout><<<blocks, kGatherThreads, 0, stream>>>(
-                      (const double*)src.A, src.lda, m, n, cols, kc, C);
-                  else gather_cols_kernel<float, Tout><<<blocks, kGatherThreads, 0, stream>>>(
-                      (const float*)src.A, src.lda, m, n, cols, kc, C));
+      const int gr = current_tune().gather_rows;
+      if (gr == 2)
+        CABS_TRY((gather_cols_dense<Tout, 2>(src, m, n, cols, kc, C, stream)));
+      else if (gr == 8)
+        CABS_TRY((gather_cols_dense<Tout, 8>(src, m, n, cols, kc, C, stream)));
+      else
+        CABS_TRY((gather_cols_dense<Tout, kRowsPerWarp>(src, m, n, cols, kc, C, stream)));
     }
     if (Rt && kr > 0) {
       const int py = ceil_div(kr, kTileP);

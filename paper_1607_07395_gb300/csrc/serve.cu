@@ -82,6 +82,7 @@ struct Request {
   cabs_status status = CABS_OK;
   size_t res_off = 0, res_bytes = 0, ws_off = 0, ws_bytes = 0;
   cabs_result res{};
+  cabs_tune tune{};  // launch shape of the request's bucket, taken at submission
   int slot = -1;
   Clock::time_point t_submit, t_done;
 };
@@ -177,6 +178,7 @@ static void schedule_once(ServeState* st) {
     r.slot = slot;
     r.state = ReqState::Running;
     SharersScope sharing((int)st->streams.size());
+    TuneScope shape(r.tune);
     const cabs_status s = sketch_enqueue(r.src, r.p, st->arena + woff, r.ws_bytes, st->streams[slot], r.res);
     if (s != CABS_OK || cudaEventRecord(st->events[slot], st->streams[slot]) != cudaSuccess) {
       cudaGetLastError();
@@ -259,6 +261,7 @@ cabs_status cabs_serve_submit(cabs_ctx* ctx, const cabs_source* src, const cabs_
   r.p = *p;
   r.res_bytes = result_bytes(*p);
   r.ws_bytes = sketch_ws_bytes(*src, *p);
+  r.tune = tune_lookup(ctx, *p);
   if (align256(r.res_bytes) + align256(r.ws_bytes) > st->arena_bytes) {
     set_error("request footprint %zu bytes exceeds the arena (%zu bytes)", r.res_bytes + r.ws_bytes,
               st->arena_bytes);

@@ -238,7 +238,9 @@ int kp_of(int d, bool tf32) {
 }
 
 // Centres per column block: all 256 when their operand block fits in 128 KB
-// of shared memory (BF16 up to d = 256, TF32 up to d = 128), else 128.
+// of shared memory (BF16 up to d = 256, TF32 up to d = 128), else 128. The
+// launch shape may also choose 128 (half the MMA columns when k2 <= 128;
+// the per-row merge of two blocks keeps the same answer).
 int block_n(int d, bool tf32) { return (size_t)kp_of(d, tf32) / (tf32 ? 32 : 64) * kBN * 128 > 128 * 1024 ? 128 : kBN; }
 
 TcWs carve_tc(Carve& cv, int64_t M, int d, int k2, bool tf32) {
@@ -282,7 +284,8 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
   TcWs t = carve_tc(cv, M, d, k2, kTF32);
   const int Kp = kp_of(d, kTF32);
   const int nch = Kp / AsgCfg<kTF32>::KC;
-  const int BN = block_n(d, kTF32);
+  // 128 where 256 resident centres do not fit, else the launch shape's choice
+  const int BN = block_n(d, kTF32) == 128 || current_tune().assign_bn == 128 ? 128 : kBN;
   const int sms = sm_count();
   if (prep_points)
     CABS_LAUNCH(stream, "tc_assign_points_prep",

@@ -50,6 +50,8 @@ int main(void) {
   printf("cabs_source %zu\ncabs_params %zu\ncabs_diag %zu\ncabs_result %zu\n", sizeof(cabs_source),
          sizeof(cabs_params), sizeof(cabs_diag), sizeof(cabs_result));
   printf("cabs_cur_params %zu\ncabs_cur_result %zu\n", sizeof(cabs_cur_params), sizeof(cabs_cur_result));
+  printf("cabs_tune %zu\n", sizeof(cabs_tune));
+  F(cabs_tune, gather_rows) F(cabs_tune, assign_bn) F(cabs_tune, reserved)
   F(cabs_cur_params, kt) F(cabs_cur_params, seed) F(cabs_cur_params, prec) F(cabs_cur_params, trunc_rtol)
   F(cabs_cur_result, Ustar) F(cabs_cur_result, rows_t) F(cabs_cur_result, ranks)
   F(cabs_source, lda) F(cabs_source, X) F(cabs_source, sigma) F(cabs_source, row_ptr) F(cabs_source, nnz)
@@ -67,7 +69,8 @@ int main(void) {
                                                                 check=True).stdout.split("\n") if ln)
     for name, cls in [("cabs_source", cabs.cabs_source), ("cabs_params", cabs.cabs_params),
                       ("cabs_diag", cabs.cabs_diag), ("cabs_result", cabs.cabs_result),
-                      ("cabs_cur_params", cabs.cabs_cur_params), ("cabs_cur_result", cabs.cabs_cur_result)]:
+                      ("cabs_cur_params", cabs.cabs_cur_params), ("cabs_cur_result", cabs.cabs_cur_result),
+                      ("cabs_tune", cabs.cabs_tune)]:
         assert int(lines[name]) == C.sizeof(cls), name
     for key, val in lines.items():
         if "." in key:
