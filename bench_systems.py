@@ -1,11 +1,14 @@
 """The two systems workloads of bench.py (imported by it; not run alone).
 
 batched  512 independent dense FP32 sketches of uneven size, one captured
-         graph per step over 16 lanes (`cabs_sketch_batched`): m, n ~ U[1000,
-         20000], rank ~ U[10, 100], k ~ U[16, 128], each matrix built like the
-         dense workload (U diag(exp(-i/30)) V^T + N(0, 1e-4^2)). Each member also
-         computes its exact relative error. Compared with the same members run
-         one by one in FP32 (one launch sequence each, no graph).
+         graph per step (`cabs_sketch_batched`): m, n ~ U[1000, 20000], rank ~
+         U[10, 100], k ~ U[16, 128], each matrix built like the dense workload
+         (U diag(exp(-i/30)) V^T + N(0, 1e-4^2)). Each member also computes its
+         exact relative error. The fixed form (16 lanes, default launch shapes)
+         is timed first; then `cabs_autotune` picks the launch shapes per shape
+         bucket and the lanes from timed trials, and the tuned form is the
+         line's value. Compared with the same members run one by one in FP32
+         (one launch sequence each, no graph).
 serve    continuous batching (`cabs_serve_*`): a Poisson stream of requests at
          200 per second for 60 s after a 5 s warm-up, admitted by HBM footprint
          into a fixed arena, their factors kept resident until read. The mix:
@@ -64,10 +67,26 @@ def run_batched(args, cabs, torch, device, ctx, timed_steps, barrier, ClockSampl
             cabs.cabs_sketch_batched(ctx, srcs, params, outs, ws, offs, lanes=lanes, use_graph=True, stream=stream)
             return torch.cat([o.err for o in outs]).cpu().tolist()
 
+    steps = args.steps if args.steps > 0 else 3
+    # fixed form: 16 lanes, default launch shapes
     for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize()
-    steps = args.steps if args.steps > 0 else 3
+    _, fixed_ms, _ = timed_steps(ctx, cabs, step, steps, stream, 1, barrier)
+    # autotuner (untimed): launch shapes per bucket and the lanes
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        tuned_lanes = cabs.cabs_autotune(ctx, srcs, params, outs, ws, offs, stream=stream)
+    tune_s = time.perf_counter() - t0
+    shapes = {}
+    for p in params:
+        sh, _ = cabs.cabs_tune_get(ctx, p)
+        key = f"k<={((p.k2 + 31) // 32) * 32},m+n~2^{int(math.log2(p.m + p.n))}"
+        shapes[key] = sh
+    lanes = 0  # the autotuner's lanes
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
     sampler = ClockSampler(device.index or 0)
     l0 = cabs.cabs_launch_count()
     sampler.start()
@@ -97,10 +116,14 @@ def run_batched(args, cabs, torch, device, ctx, timed_steps, barrier, ClockSampl
                 ms_per_step=round(total_ms / steps, 4), gpu_launches=int(launches), clocks=clocks,
                 latency_ms=dict(step_p50=round(statistics.median(per_step), 4), step_p99=round(_pct(per_step, 0.99), 4)),
                 rel_fro_error=dict(median=statistics.median(all_errs), max=max(all_errs)),
+                fixed=dict(value=round(job_value(1, count, steps, fixed_ms), 4), unit="sketches/s", lanes=16,
+                           shapes="defaults"),
+                autotune=dict(seconds=round(tune_s, 2), lanes=tuned_lanes, buckets=len(shapes), shapes=shapes),
                 plain_fp32=dict(value=round(count / (ptot / 1e3), 4), unit="sketches/s",
                                 rel_fro_error=dict(median=statistics.median(perrs[0]), max=max(perrs[0])),
                                 form="one sketch per launch sequence, one stream, no graph"),
-                config=dict(workload="batched", members=count, lanes=lanes, graph=True, prec=args.prec,
+                config=dict(workload="batched", members=count, lanes=tuned_lanes, graph=True, prec=args.prec,
+                            shapes="autotuned",
                             core="stabilized", matrices_gib=round(total_bytes / 2**30, 1),
                             desc="512 dense FP32 U diag(exp(-i/30)) V^T + noise, m, n ~ U[1000, 20000], "
                                  "rank ~ U[10, 100], k ~ U[16, 128], c=5",
@@ -154,7 +177,7 @@ def serve_requests(cabs, pool, rate, seconds, seed, prec):
             s, _ = pool.plain
             p = cabs.make_params(2000, 1500, 20, iters=5, seed=int(seed + i), prec="fp64", core="pinv",
                                  err_samples=0, err_seed=3)
-        out.append((t, s, p))
+        out.append((t, s, p, "dense" if u < 0.50 else ("rbf" if u < 0.95 else "plain")))
         i += 1
     return out
 
@@ -163,11 +186,11 @@ def run_serve(args, cabs, torch, device, ctx, ClockSampler):
     rate, warm, seconds = 200.0, 5.0, args.serve_seconds
     pool = _Pool(cabs, torch, device, 1607)
     reqs = serve_requests(cabs, pool, rate, warm + seconds, 1607, args.prec)
-    need = max(cabs.cabs_workspace_size(s, p) for _, s, p in reqs)
+    need = max(cabs.cabs_workspace_size(s, p) for _, s, p, _ in reqs)
     free, _ = torch.cuda.mem_get_info(device)
     arena = int(min(0.6 * free, max(16 * need, 8 << 30)))
     srv = cabs.Server(ctx, arena_bytes=arena, max_slots=8)
-    lat, done_t, errs, pending = [], [], [], []
+    lat, done_t, errs, pending, kinds, ivals = [], [], [], [], [], []
     sampler = ClockSampler(device.index or 0)
     l0 = cabs.cabs_launch_count()
     try:
@@ -177,20 +200,22 @@ def run_serve(args, cabs, torch, device, ctx, ClockSampler):
         while i < len(reqs) or pending:
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i][0] <= now:
-                at, s, p = reqs[i]
-                pending.append((srv.submit(s, p), at, p))
+                at, s, p, kind = reqs[i]
+                pending.append((srv.submit(s, p), at, p, kind))
                 i += 1
             still = []
-            for tk, at, p in pending:
+            for tk, at, p, kind in pending:
                 r = srv.poll(tk, timeout_ms=0)
                 if r is None:
-                    still.append((tk, at, p))
+                    still.append((tk, at, p, kind))
                     continue
                 res, ms = r
                 if at >= warm:
                     lat.append(ms)
                     done_t.append(time.perf_counter() - t0)
                     errs.append(cabs.result_err(res, device))
+                    kinds.append(kind)
+                    ivals.append(srv.times(tk))
                 srv.release(tk)
             pending = still
             if i < len(reqs):
@@ -202,9 +227,42 @@ def run_serve(args, cabs, torch, device, ctx, ClockSampler):
         srv.stop()
     launches = cabs.cabs_launch_count() - l0
     window = max(done_t) - warm if done_t else float("nan")
+    per_kind = {}
+    for kd in ("dense", "rbf", "plain"):
+        e = [x for x, y in zip(errs, kinds) if y == kd]
+        lk = [x for x, y in zip(lat, kinds) if y == kd]
+        if e:
+            per_kind[kd] = dict(requests=len(e), err_median=statistics.median(e), err_max=max(e),
+                                lat_p50_ms=round(statistics.median(lk), 3), lat_p99_ms=round(_pct(lk, 0.99), 3))
+    # device-time overlap: requests whose interval intersects another's
+    iv = sorted(ivals)
+    overlapped, reach = 0, -1.0
+    flags = [False] * len(iv)
+    for j, (a, b) in enumerate(iv):
+        if a < reach:
+            flags[j] = True
+            flags[jmax] = True
+        if b > reach:
+            reach, jmax = b, j
+    overlapped = sum(flags)
+
+    # capacity: a fresh burst of the same request mix submitted all at once
+    # (saturating arrivals), completions per second of wall time
+    burst = [(s, p) for at, s, p, _ in reqs if at >= warm][:600]
+    srv = cabs.Server(ctx, arena_bytes=arena, max_slots=8)
+    try:
+        t0 = time.perf_counter()
+        tks = [srv.submit(s, p) for s, p in burst]
+        for tk in tks:
+            while srv.poll(tk, timeout_ms=100) is None:
+                pass
+            srv.release(tk)
+        cap_s = time.perf_counter() - t0
+    finally:
+        srv.stop()
 
     # the plain FP32 form: the measured requests one at a time, back to back
-    meas = [(s, p) for at, s, p in reqs if at >= warm][:400]
+    meas = [(s, p) for at, s, p, _ in reqs if at >= warm][:400]
     plain_ms = []
     qs = [cabs.make_params(p.m, p.n, p.k1, iters=p.iters, seed=p.seed,
                            prec="fp64" if p.prec == cabs.PRECS["fp64"] else "fp32", core=p.core,
@@ -224,6 +282,12 @@ def run_serve(args, cabs, torch, device, ctx, ClockSampler):
                 latency_ms=dict(p50=round(statistics.median(lat), 3), p99=round(_pct(lat, 0.99), 3),
                                 mean=round(statistics.mean(lat), 3)),
                 rel_fro_error=dict(median=statistics.median(errs), max=max(errs)) if errs else None,
+                per_kind=per_kind,
+                capacity=dict(value=round(len(burst) / cap_s, 4), unit="sketches/s", requests=len(burst),
+                              form="the measured mix submitted at once (saturating arrivals), 8 slots"),
+                overlap=dict(requests=len(iv), overlapped=overlapped,
+                             note="requests whose device-side interval (CUDA events on the slot stream) "
+                                  "intersects another request's"),
                 clocks=clocks, gpu_launches=int(launches),
                 plain_fp32=dict(value=round(1e3 / mean_plain, 4), unit="sketches/s",
                                 mean_service_ms=round(mean_plain, 3), sample=len(plain_ms),

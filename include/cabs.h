@@ -495,6 +495,14 @@ cabs_status cabs_serve_submit(cabs_ctx* ctx, const cabs_source* src, const cabs_
  * submit-to-completion time. CABS_EBUSY: not finished yet. */
 cabs_status cabs_serve_poll(cabs_ctx* ctx, uint64_t ticket, cabs_result* res, double* latency_ms,
                             int32_t timeout_ms);
+/* Device-side interval of a finished request: *start_ms and *end_ms are the
+ * times (ms since cabs_serve_start) at which its slot stream reached the
+ * request's first and passed its last kernel, from CUDA events on that
+ * stream. Two requests whose intervals intersect had work on the GPU at the
+ * same time. CABS_EBUSY while the request is queued or running,
+ * CABS_ENOTFOUND after cabs_serve_release. The paper has no counterpart. */
+cabs_status cabs_serve_times(cabs_ctx* ctx, uint64_t ticket, double* start_ms, double* end_ms);
+
 /* Frees a finished request's resident results. */
 cabs_status cabs_serve_release(cabs_ctx* ctx, uint64_t ticket);
 /* Stops admitting, waits for requests on the device, joins the loop. */

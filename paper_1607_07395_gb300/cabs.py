@@ -133,6 +133,7 @@ def lib():
         "cabs_tune_save": ([vp, C.c_char_p], i32),
         "cabs_tune_load": ([vp, C.c_char_p], i32),
         "cabs_autotune": ([vp, i32, P(cabs_source), P(cabs_params), vp, P(sz), P(cabs_result), vp, P(i32)], i32),
+        "cabs_serve_times": ([vp, u64, P(f64), P(f64)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -151,7 +152,7 @@ def exported_names():
             "cabs_sketch_cur", "cabs_serve_start", "cabs_serve_submit", "cabs_serve_poll",
             "cabs_serve_release", "cabs_serve_stop", "cabs_profile_enable", "cabs_profile_read",
             "cabs_launch_count", "cabs_error_noalloc", "cabs_set_wait_limit", "cabs_tune_set", "cabs_tune_get",
-            "cabs_tune_save", "cabs_tune_load", "cabs_autotune"]
+            "cabs_tune_save", "cabs_tune_load", "cabs_autotune", "cabs_serve_times"]
 
 
 def _check(status, ctx=None):
@@ -631,6 +632,12 @@ class Server:
             return None
         _check(st, self.ctx.h)
         return res, lat.value
+
+    def times(self, ticket: int):
+        """(start_ms, end_ms): the finished request's device-side interval since the loop started."""
+        a, b = C.c_double(), C.c_double()
+        _check(lib().cabs_serve_times(self.ctx.h, ticket, C.byref(a), C.byref(b)), self.ctx.h)
+        return a.value, b.value
 
     def release(self, ticket: int):
         _check(lib().cabs_serve_release(self.ctx.h, ticket), self.ctx.h)

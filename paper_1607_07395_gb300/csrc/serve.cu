@@ -83,6 +83,7 @@ struct Request {
   size_t res_off = 0, res_bytes = 0, ws_off = 0, ws_bytes = 0;
   cabs_result res{};
   cabs_tune tune{};  // launch shape of the request's bucket, taken at submission
+  double dev_start_ms = -1.0, dev_end_ms = -1.0;  // device-side interval, ms since the loop's epoch
   int slot = -1;
   Clock::time_point t_submit, t_done;
 };
@@ -93,7 +94,9 @@ struct ServeState {
   int device = 0;
   ArenaAlloc alloc;
   std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> events;
+  std::vector<cudaEvent_t> events;       // end of the slot's request (timing event)
+  std::vector<cudaEvent_t> start_events; // start of the slot's request
+  cudaEvent_t epoch = nullptr;           // recorded when the loop starts
   std::vector<uint64_t> slot_ticket;  // 0 = free
   std::deque<uint64_t> queue;
   std::map<uint64_t, Request> reqs;
@@ -146,6 +149,14 @@ static void schedule_once(ServeState* st) {
     r.t_done = Clock::now();
     if (q == cudaSuccess) {
       r.state = ReqState::Done;
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, st->epoch, st->start_events[s]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, st->epoch, st->events[s]) == cudaSuccess) {
+        r.dev_start_ms = a;
+        r.dev_end_ms = b;
+      } else {
+        cudaGetLastError();
+      }
     } else {
       cudaGetLastError();
       r.state = ReqState::Failed;
@@ -179,6 +190,7 @@ static void schedule_once(ServeState* st) {
     r.state = ReqState::Running;
     SharersScope sharing((int)st->streams.size());
     TuneScope shape(r.tune);
+    cudaEventRecord(st->start_events[slot], st->streams[slot]);
     const cabs_status s = sketch_enqueue(r.src, r.p, st->arena + woff, r.ws_bytes, st->streams[slot], r.res);
     if (s != CABS_OK || cudaEventRecord(st->events[slot], st->streams[slot]) != cudaSuccess) {
       cudaGetLastError();
@@ -230,16 +242,26 @@ cabs_status cabs_serve_start(cabs_ctx* ctx, void* arena, size_t arena_bytes, int
   st->alloc.reset(arena_bytes);
   for (int i = 0; i < max_slots; ++i) {
     cudaStream_t s;
-    cudaEvent_t e;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEvent_t e, e0;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess) {
       for (cudaStream_t x : st->streams) cudaStreamDestroy(x);
       for (cudaEvent_t x : st->events) cudaEventDestroy(x);
+      for (cudaEvent_t x : st->start_events) cudaEventDestroy(x);
       delete st;
       return check_cuda("serve stream/event");
     }
     st->streams.push_back(s);
     st->events.push_back(e);
+    st->start_events.push_back(e0);
+  }
+  if (cudaEventCreate(&st->epoch) != cudaSuccess || cudaEventRecord(st->epoch, st->streams[0]) != cudaSuccess ||
+      cudaEventSynchronize(st->epoch) != cudaSuccess) {
+    for (cudaStream_t x : st->streams) cudaStreamDestroy(x);
+    for (cudaEvent_t x : st->events) cudaEventDestroy(x);
+    for (cudaEvent_t x : st->start_events) cudaEventDestroy(x);
+    delete st;
+    return check_cuda("serve epoch event");
   }
   st->slot_ticket.assign(max_slots, 0);
   st->thread = std::thread(serve_loop, st);
@@ -309,6 +331,26 @@ cabs_status cabs_serve_poll(cabs_ctx* ctx, uint64_t ticket, cabs_result* res, do
   return CABS_OK;
 }
 
+cabs_status cabs_serve_times(cabs_ctx* ctx, uint64_t ticket, double* start_ms, double* end_ms) {
+  clear_error();
+  CABS_REQUIRE(ctx != nullptr && ctx->serve != nullptr, "the serving loop is not running");
+  CABS_REQUIRE(start_ms != nullptr && end_ms != nullptr, "start_ms and end_ms must be non-NULL");
+  ServeState* st = ctx->serve;
+  std::lock_guard<std::mutex> lk(st->mu);
+  auto it = st->reqs.find(ticket);
+  if (it == st->reqs.end()) {
+    set_error("unknown ticket %llu", (unsigned long long)ticket);
+    return CABS_ENOTFOUND;
+  }
+  const Request& r = it->second;
+  if (r.state == ReqState::Queued || r.state == ReqState::Running) return CABS_EBUSY;
+  CABS_REQUIRE(r.state == ReqState::Done && r.dev_start_ms >= 0.0, "request %llu did not finish normally",
+               (unsigned long long)ticket);
+  *start_ms = r.dev_start_ms;
+  *end_ms = r.dev_end_ms;
+  return CABS_OK;
+}
+
 cabs_status cabs_serve_release(cabs_ctx* ctx, uint64_t ticket) {
   clear_error();
   CABS_REQUIRE(ctx != nullptr && ctx->serve != nullptr, "the serving loop is not running");
@@ -349,6 +391,8 @@ cabs_status cabs_serve_stop(cabs_ctx* ctx) {
   DeviceGuard g(st->device);
   for (cudaStream_t s : st->streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : st->start_events) cudaEventDestroy(e);
+  if (st->epoch) cudaEventDestroy(st->epoch);
   ctx->serve = nullptr;
   delete st;
   return CABS_OK;

@@ -105,7 +105,7 @@ def test_serving_mix_equals_alone_and_overlaps(ctx, C):
         th = threading.Thread(target=client)
         th.start()
         th.join()
-        lat = []
+        lat, ivals = [], []
         for idx, t in tickets:
             r = None
             for _ in range(2000):
@@ -115,11 +115,16 @@ def test_serving_mix_equals_alone_and_overlaps(ctx, C):
             assert r is not None, "request never finished"
             res, ms = r
             lat.append(ms)
+            ivals.append(srv.times(t))
             U, S, V, rows, cols = C.result_tensors(res, mem[idx][1])
             got = [x.cpu().numpy() for x in (U, S, V, rows, cols)]
             assert same(got, alone[idx][:5]), idx
             srv.release(t)
         assert all(x > 0 for x in lat)
+        assert all(0 <= a <= b for a, b in ivals)
+        # at least two requests had work on the GPU at the same time
+        ivals.sort()
+        assert any(ivals[j][0] < ivals[i][1] for i in range(len(ivals)) for j in range(i + 1, len(ivals))), ivals
     finally:
         srv.stop()
 
