@@ -59,6 +59,13 @@ constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
 #define CABS_SVD_TOL_A 1e-5f
 #endif
 constexpr float kTolA = CABS_SVD_TOL_A;  // Phase A rotation threshold |g| > tol sqrt(a b)
+// Phase A stops after a sweep in which no pair had |g| > kStopA sqrt(a b):
+// cyclic Jacobi converges quadratically there, so the next sweep would find
+// every |g| near kStopA^2 times a small constant, at the rotation threshold
+// (a CPU model of the kernel on the sketching workloads: 6.7e-4 in the last
+// sweep that rotated, 1e-5 in the next, which then rotated nothing), and
+// the FP64 refinement takes the factors from there.
+constexpr float kStopA = 1e-3f;
 constexpr int kMaxSweepsA = 40;
 constexpr int kItersB = 8;
 constexpr double kMaxCorrB = 0.05;      // Phase B: larger first-order corrections are deferred
@@ -84,13 +91,15 @@ __device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& 
 // The Hestenes rotation that makes two columns with squared norms a, b and
 // inner product g orthogonal: zeta = (b - a) / 2g,
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
-// Returns false (no rotation) unless |g| > tol sqrt(a b), tested as
-// g^2 > tol^2 a b. Phase A needs only approximate rotations -- c and s form
+// Returns 0 (no rotation) unless |g| > tol sqrt(a b), tested as
+// g^2 > tol^2 a b; else 1, or 3 when |g| > kStopA sqrt(a b) (the sweep is
+// not the last one). Phase A needs only approximate rotations -- c and s form
 // an exact rotation for any t, and the FP64 refinement finishes the job -- so
 // the divisions and square roots are the fast hardware approximations,
 // which shortens the dependent chain of every rotation step.
-__device__ __forceinline__ bool jacobi_cs(float a, float b, float g, float& c, float& s) {
-  if (!(g * g > kTolA * kTolA * a * b)) return false;
+__device__ __forceinline__ int jacobi_cs(float a, float b, float g, float& c, float& s) {
+  const float ab = a * b, g2 = g * g;
+  if (!(g2 > kTolA * kTolA * ab)) return 0;
   const float zeta = __fdividef(b - a, 2.f * g);
   const float az = fabsf(zeta);
   float t;
@@ -102,13 +111,13 @@ __device__ __forceinline__ bool jacobi_cs(float a, float b, float g, float& c, f
   }
   c = rsqrtf(fmaf(t, t, 1.f));
   s = c * t;
-  return true;
+  return g2 > kStopA * kStopA * ab ? 3 : 1;
 }
 
 // Rotates columns x, y (length k, lane-strided) so that they become
-// orthogonal; returns true if a rotation was applied. x, y, vx, vy may live
-// in shared or distributed shared memory.
-__device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, float* vy, int k, int lane) {
+// orthogonal; returns jacobi_cs's code (0: no rotation). x, y, vx, vy may
+// live in shared or distributed shared memory.
+__device__ __forceinline__ int rotate_pair_f32(float* x, float* y, float* vx, float* vy, int k, int lane) {
   float a = 0.f, b = 0.f, g = 0.f;
   for (int i = lane; i < k; i += 32) {
     const float u = x[i], v = y[i];
@@ -120,7 +129,8 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
   b = warp_sum(b);
   g = warp_sum(g);
   float c, s;
-  if (!jacobi_cs(a, b, g, c, s)) return false;
+  const int code = jacobi_cs(a, b, g, c, s);
+  if (!code) return 0;
   for (int i = lane; i < k; i += 32) {
     const float u = x[i], v = y[i];
     x[i] = c * u - s * v;
@@ -129,7 +139,7 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
     vx[i] = c * p - s * q;
     vy[i] = s * p + c * q;
   }
-  return true;
+  return code;
 }
 
 // Same rotation with each lane owning R rows of a column padded to 32 R
@@ -138,7 +148,7 @@ __device__ __forceinline__ bool rotate_pair_f32(float* x, float* y, float* vx, f
 // accesses are consecutive and free of bank conflicts): the two columns are
 // read once, rotated in registers and written back once.
 template <int R>
-__device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, float* vy, int lane) {
+__device__ __forceinline__ int rotate_pair_reg(float* x, float* y, float* vx, float* vy, int lane) {
   float xr[R], yr[R];
   const float4* x4 = (const float4*)x;
   const float4* y4 = (const float4*)y;
@@ -171,7 +181,8 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
     g += __shfl_xor_sync(0xffffffffu, g, off);
   }
   float c, s;
-  if (!jacobi_cs(a, b, g, c, s)) return false;
+  const int code = jacobi_cs(a, b, g, c, s);
+  if (!code) return 0;
   float4* xo = (float4*)x;
   float4* yo = (float4*)y;
 #pragma unroll
@@ -197,7 +208,7 @@ __device__ __forceinline__ bool rotate_pair_reg(float* x, float* y, float* vx, f
     vxo[lane + 32 * i] = p2;
     vyo[lane + 32 * i] = q2;
   }
-  return true;
+  return code;
 }
 
 template <int R>
@@ -226,7 +237,7 @@ __device__ __forceinline__ void store_col(float* x, int lane, const float* xr) {
 // step reduces only the inner product g across the warp. They are
 // recomputed from the columns at the start of every round.
 template <int R>
-__device__ __forceinline__ bool rotate_top_reg(float* xr, float& a, float* y, float* bn, int lane, float2* cs) {
+__device__ __forceinline__ int rotate_top_reg(float* xr, float& a, float* y, float* bn, int lane, float2* cs) {
   float yr[R];
   load_col<R>(y, lane, yr);
   // every lane reads b before the shuffles below, which lane 0 must pass
@@ -238,9 +249,10 @@ __device__ __forceinline__ bool rotate_top_reg(float* xr, float& a, float* y, fl
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
   float c, s;
-  if (!jacobi_cs(a, b, g, c, s)) {
+  const int code = jacobi_cs(a, b, g, c, s);
+  if (!code) {
     if (lane == 0) *cs = make_float2(1.f, 0.f);
-    return false;
+    return 0;
   }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -256,7 +268,7 @@ __device__ __forceinline__ bool rotate_top_reg(float* xr, float& a, float* y, fl
     *cs = make_float2(c, s);
   }
   a = a2;
-  return true;
+  return code;
 }
 
 // Squared norm of a column held as in load_col.
@@ -351,9 +363,9 @@ __global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict
         int p, q;
         rr_pair(round, pr, kk, p, q);
         if (q >= k) continue;
-        if (rotate_pair_f32(Wc + (size_t)p * k, Wc + (size_t)q * k, Vc + (size_t)p * k, Vc + (size_t)q * k, k, lane) &&
-            lane == 0)
-          rotated = 1;
+        const int code =
+            rotate_pair_f32(Wc + (size_t)p * k, Wc + (size_t)q * k, Vc + (size_t)p * k, Vc + (size_t)q * k, k, lane);
+        if (code && lane == 0) atomicOr(&rotated, code);
       }
       __syncthreads();
     }
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(512) svd32_cta_kernel(const double* __restrict
     __syncthreads();
     if (tid == 0) rotated = 0;
     __syncthreads();
-    conv = any == 0;
+    conv = (any & 2) == 0;  // no rotation, or only small ones (kStopA)
   }
   for (int j = warp; j < k; j += nwarps) emit_column(Wc + (size_t)j * k, Vc + (size_t)j * k, k, j, lane, U0, V0);
   if (tid == 0 && sweeps_out) *sweeps_out = sweep;
@@ -528,7 +540,7 @@ __device__ __forceinline__ void apply_panel(const float* V, const float* beta, i
 // inputs) starts from W itself: its QR turns exact zeros into rounding noise,
 // and there the preconditioned Jacobi needed more sweeps, not fewer.
 template <int R>
-__global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const double* __restrict__ W, int k, int b,
+__global__ void __launch_bounds__(kClusterThreads, 1) svd32_cluster_kernel(const double* __restrict__ W, int k, int b,
                                                                         double* __restrict__ U0,
                                                                         double* __restrict__ V0, float* __restrict__ qr,
                                                                         int* sweeps_out) {
@@ -765,11 +777,11 @@ __global__ void __launch_bounds__(kClusterThreads) svd32_cluster_kernel(const do
       nxt = t;
     }
     // cluster-wide "any rotation in this sweep"
-    if (my_rot) atomicOr(&rot_flag[sweep & 1], 1);
+    if (my_rot) atomicOr(&rot_flag[sweep & 1], my_rot);
     cluster.sync();
     int any = 0;
     for (int r = 0; r < NC; ++r) any |= *cluster.map_shared_rank(&rot_flag[sweep & 1], r);
-    conv = any == 0;
+    conv = (any & 2) == 0;  // no rotation, or only small ones (kStopA)
     ++sweep;
   }
   // write out my two blocks (back at their starting places after whole sweeps)
