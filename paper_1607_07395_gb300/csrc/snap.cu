@@ -232,13 +232,12 @@ __device__ __forceinline__ void taken_add(int* set, int r) {
   }
 }
 
-// One scan of rows [lo, hi) not in the taken bitmap for centre z. Pass 1
-// (lim < 0): the (distance, row) minimum. Pass 2: the lowest row with
-// distance <= lim (distance +inf if none). The distances are the same in both
-// passes (same arithmetic, same order).
+// Pass 1 of a full scan: the (distance, row) minimum over rows [lo, hi) not
+// in the taken bitmap, for centre z; each computed distance is also stored
+// in dist[l] for pass 2.
 template <typename T>
 __device__ void scan_slice(const T* __restrict__ X, int d, const T* __restrict__ z, long long lo, long long hi,
-                           const unsigned* taken, T lim, bool window, T& best, int& brow) {
+                           const unsigned* taken, T* __restrict__ dist, T& best, int& brow) {
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
   best = pos_inf<T>();
   brow = 0x7fffffff;
@@ -265,15 +264,39 @@ __device__ void scan_slice(const T* __restrict__ X, int d, const T* __restrict__
     for (int u = 0; u < 4; ++u) {
       const T sv = warp_sum(s4[u]);
       if (skip[u]) continue;
-      if (window) {
-        if (sv <= lim && (int)(l0 + u) < brow) {
-          best = sv;
-          brow = (int)(l0 + u);
-        }
-      } else if (lex_less(sv, (int)(l0 + u), best, brow)) {
+      if (lane == 0) dist[l0 + u] = sv;
+      if (lex_less(sv, (int)(l0 + u), best, brow)) {
         best = sv;
         brow = (int)(l0 + u);
       }
+    }
+  }
+}
+
+// Pass 2: the lowest untaken row of [lo, hi) whose pass-1 distance is <= lim
+// (one thread per row; +inf, 0x7fffffff if none).
+template <typename T>
+__device__ void window_slice(long long lo, long long hi, const unsigned* taken, const T* __restrict__ dist, T lim,
+                             T& best, int& brow) {
+  best = pos_inf<T>();
+  brow = 0x7fffffff;
+  for (long long l = lo + threadIdx.x; l < hi; l += blockDim.x) {
+    if ((((volatile const unsigned*)taken)[l >> 5] >> (l & 31)) & 1u) continue;
+    const T v = ((volatile const T*)dist)[l];
+    if (v <= lim) {
+      best = v;
+      brow = (int)l;
+      break;  // rows rise with l: the first hit is this thread's lowest
+    }
+  }
+  // lowest row over the warp
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+    const T ov = __shfl_xor_sync(0xffffffffu, best, off);
+    if (orow < brow) {
+      brow = orow;
+      best = ov;
     }
   }
 }
@@ -305,7 +328,8 @@ template <typename T>
 __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
     const T* __restrict__ top_d, T tie_rtol, unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row,
-    T* fb_lim, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks, int* status) {
+    T* fb_lim, T* dist, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks,
+    int* status) {
   __shared__ T wd[kGreedyThreads / 32];
   __shared__ int wr[kGreedyThreads / 32];
   // CTA 0's walk reads the candidate lists, their distances, the centres'
@@ -313,10 +337,12 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
   // are staged once, the taken rows (at most k2) live in an open-addressing
   // set of kTakenSlots slots. The global bitmap is written too, for the CTAs'
   // scans when a centre's list does not decide.
-  __shared__ int s_top[CABS_MAX_K * kTop];
-  __shared__ T s_topd[CABS_MAX_K * kTop];
-  __shared__ T s_zz[CABS_MAX_K];
-  __shared__ int s_taken[kTakenSlots];
+  // dynamic shared memory: s_topd[k2 kTop], s_zz[k2] (T), s_top[k2 kTop], s_taken (int)
+  extern __shared__ __align__(16) unsigned char greedy_smem[];
+  T* s_topd = (T*)greedy_smem;
+  T* s_zz = s_topd + (size_t)CABS_MAX_K * kTop;
+  int* s_top = (int*)(s_zz + CABS_MAX_K);
+  int* s_taken = s_top + (size_t)CABS_MAX_K * kTop;
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
@@ -374,7 +400,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     const T* z = Z + (size_t)j * d;
     T best;
     int brow;
-    scan_slice(X, d, z, lo, hi, taken, T(-1), false, best, brow);
+    scan_slice(X, d, z, lo, hi, taken, dist, best, brow);
     cta_reduce(best, brow, false, wd, wr, cta_best, cta_row);
     if (!grid_sync(bar, G)) return gave_up();
     if (blockIdx.x == 0 && tid == 0) {
@@ -390,7 +416,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
     }
     if (!grid_sync(bar, G)) return gave_up();
     // pass 2: lowest untaken row of the slice inside the window
-    scan_slice(X, d, z, lo, hi, taken, *(volatile T*)fb_lim, true, best, brow);
+    window_slice(lo, hi, taken, dist, *(volatile T*)fb_lim, best, brow);
     cta_reduce(best, brow, true, wd, wr, cta_best, cta_row);
     if (!grid_sync(bar, G)) return gave_up();
     if (blockIdx.x == 0 && tid == 0) {
@@ -434,7 +460,7 @@ struct SnapWs {
   int* top_r;
   unsigned* bitmap;
   int *picks, *next_fb, *cta_row;
-  void *cta_best, *fb_lim;
+  void *cta_best, *fb_lim, *dist;
   GridBarrier* bar;
   void* tc;  // tensor-core candidate search (BF16 / TF32 modes)
   size_t tc_bytes;
@@ -454,6 +480,7 @@ SnapWs carve_snap(Carve& cv, int64_t M, int d, int k2, int prec) {
   w.cta_row = cv.take<int>(1024);
   w.cta_best = cv.take<char>(1024 * eb);
   w.fb_lim = cv.take<char>(eb);
+  w.dist = cv.take<char>((size_t)M * eb);
   w.bar = cv.take<GridBarrier>(1);
   w.tc = nullptr;
   w.tc_bytes = 0;
@@ -487,8 +514,10 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
     CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
     CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
   }
+  const size_t gsmem = (size_t)CABS_MAX_K * (kTop + 1) * sizeof(T) + (size_t)(CABS_MAX_K * kTop + kTakenSlots) * 4;
+  cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, gsmem);
   const int G = std::max(1, std::min({(int)ceil_div(M, 2048), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
   CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb, wait_limit()));
   const T* Xc = X;
@@ -502,13 +531,14 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
   T* cb = (T*)w.cta_best;
   int* cr = w.cta_row;
   T* lim = (T*)w.fb_lim;
+  T* dst = (T*)w.dist;
   GridBarrier* bar = w.bar;
   long long Ml = M;
-  void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &topd, &tie, &bm, &picks, &nfb, &cb, &cr, &lim, &bar, &order, &sorted,
-                  &fallbacks, &status};
+  void* args[] = {&Xc, &Ml, &d, &Zc, &k2, &topr, &topd, &tie, &bm, &picks, &nfb, &cb, &cr, &lim, &dst, &bar, &order,
+                  &sorted, &fallbacks, &status};
   CABS_LAUNCH(stream, "snap_greedy_kernel",
-              cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args, 0,
-                                          stream));
+              cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args,
+                                          gsmem, stream));
   return CABS_OK;
 }
 
