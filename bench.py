@@ -892,7 +892,7 @@ def run_systems(args):
                latency_ms=r["latency_ms"], rel_fro_error=r["rel_fro_error"], plain_fp32=r["plain_fp32"],
                gpu_launches=r.get("gpu_launches"), clocks=r["clocks"],
                e2e=None, e2e_note="inputs stay resident by design (serving keeps its matrices and factors in HBM)")
-    for key in ("fixed", "autotune", "per_kind", "capacity", "overlap"):
+    for key in ("fixed", "autotune", "no_graph", "per_kind", "capacity", "overlap"):
         if key in r:
             out[key] = r[key]
     return out

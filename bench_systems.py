@@ -68,6 +68,16 @@ def run_batched(args, cabs, torch, device, ctx, timed_steps, barrier, ClockSampl
             return torch.cat([o.err for o in outs]).cpu().tolist()
 
     steps = args.steps if args.steps > 0 else 3
+
+    def step_nograph():
+        with torch.cuda.stream(stream):
+            cabs.cabs_sketch_batched(ctx, srcs, params, outs, ws, offs, lanes=16, use_graph=False, stream=stream)
+            return torch.cat([o.err for o in outs]).cpu().tolist()
+
+    # the same batch launched kernel by kernel (no graph): what launch overhead costs
+    step_nograph()
+    torch.cuda.synchronize()
+    _, nograph_ms, _ = timed_steps(ctx, cabs, step_nograph, steps, stream, 1, barrier)
     # fixed form: 16 lanes, default launch shapes
     for _ in range(max(args.warmup, 1)):
         step()
@@ -118,6 +128,9 @@ def run_batched(args, cabs, torch, device, ctx, timed_steps, barrier, ClockSampl
                 rel_fro_error=dict(median=statistics.median(all_errs), max=max(all_errs)),
                 fixed=dict(value=round(job_value(1, count, steps, fixed_ms), 4), unit="sketches/s", lanes=16,
                            shapes="defaults"),
+                no_graph=dict(value=round(job_value(1, count, steps, nograph_ms), 4), unit="sketches/s", lanes=16,
+                              launches_per_step=int(launches / steps),
+                              form="the same batch launched kernel by kernel over 16 lanes, no graph"),
                 autotune=dict(seconds=round(tune_s, 2), lanes=tuned_lanes, buckets=len(shapes), shapes=shapes),
                 plain_fp32=dict(value=round(count / (ptot / 1e3), 4), unit="sketches/s",
                                 rel_fro_error=dict(median=statistics.median(perrs[0]), max=max(perrs[0])),
