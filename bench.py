@@ -73,10 +73,47 @@ WORKLOADS = {
 }
 
 # Peaks: measured copy bandwidth and BF16 GEMM from MEASURED_PEAKS.json; the
-# FP32 / FP64 CUDA-core peaks are derived from unit counts and the maximum
-# clock (152 SMs x 128 FP32 lanes or 2 FP64 lanes x 2 flops x 2.07 GHz).
+# FP32, TF32 and FP64 peaks are measured at start-up the same way (a timed
+# cuBLAS GEMM through torch, see measure_alu_peaks). The unit-count figures
+# (152 SMs x 128 FP32 lanes or 2 FP64 lanes x 2 flops x 2.07 GHz) are
+# reported beside them, and used only when the measurement fails.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measure_alu_peaks(device):
+    """FP32 (no TF32), TF32 and FP64 GEMM throughput of this GPU: torch.matmul
+    of n x n operands (n = 8192 FP32/TF32, 4096 FP64), 2 n^3 flops, fastest of
+    5 after 2 warm-up products, CUDA events on the current stream."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32, n in (("fp32", torch.float32, False, 8192), ("tf32", torch.float32, True, 8192),
+                                  ("fp64", torch.float64, False, 4096)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            g = torch.Generator(device=device)
+            g.manual_seed(5)
+            a = torch.randn(n, n, device=device, dtype=dt, generator=g)
+            b = torch.randn(n, n, device=device, dtype=dt, generator=g)
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name + "_tflops"] = round(2.0 * n ** 3 / best / 1e12, 2)
+            del a, b
+    except Exception as e:  # noqa: BLE001 -- the derived figures stand in
+        out["error"] = str(e)[:200]
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():
@@ -269,14 +306,27 @@ def roofline_of(name, launches, ms, wl, k, iters, elem_bytes, svd_sweeps, steps,
     if bound == "hbm":
         peak, src = peaks["hbm_gbs"], peaks["source"] + " copy"
     elif bound == "tensor":
-        peak = peaks["bf16_tflops_sustained"] if prec == "bf16" else peaks["bf16_tflops_sustained"] / 2
-        src = peaks["source"] + (" bf16 sustained" if prec == "bf16" else " bf16 sustained / 2 (tf32 nominal ratio)")
+        if prec == "bf16" or "tf32_tflops" not in peaks:
+            peak = peaks["bf16_tflops_sustained"] if prec == "bf16" else peaks["bf16_tflops_sustained"] / 2
+            src = peaks["source"] + (" bf16 sustained" if prec == "bf16" else " bf16 sustained / 2 (tf32 nominal ratio)")
+        else:
+            peak, src = peaks["tf32_tflops"], "measured cuBLAS TF32 GEMM 8192^3 (torch.matmul, start-up)"
     else:
         fp64 = name in ("svd_jacobi_kernel", "refine_persistent_kernel") or (prec == "fp64" and not name.startswith("svd32"))
-        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
-        src = "derived from unit counts x 2.07 GHz"
+        key = "fp64_tflops" if fp64 else "fp32_tflops"
+        if key in peaks:
+            peak = peaks[key]
+            src = (f"measured cuBLAS {'D' if fp64 else 'S'}GEMM {'4096' if fp64 else '8192'}^3 (torch.matmul, "
+                   f"start-up); unit-count figure {FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS:.2f}")
+        else:
+            peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+            src = "derived from unit counts x 2.07 GHz"
     tr = kernel_traffic(name, workload)
-    return dict(kernel=name, bound=bound, achieved=round(achieved, 4), peak=round(peak, 3), unit=unit,
+    extra = {}
+    if name.startswith("svd32_cluster"):
+        # one 16-CTA cluster: the fraction of the peak of the SMs it occupies
+        extra = dict(sms_used=16, frac_of_sms_used=round(achieved / (peak * 16 / 152), 5))
+    return dict(kernel=name, bound=bound, achieved=round(achieved, 4), peak=round(peak, 3), unit=unit, **extra,
                 frac=round(achieved / peak, 5), traffic=tr["bytes"] if tr else None, peak_source=src,
                 avg_launch_ms=round(ms / max(launches, 1), 5),
                 traffic_source=(f"ncu capture ({tr['captured_on']})" + (f", {tr['scaled']}" if tr.get("scaled") else ""))
@@ -665,11 +715,43 @@ def run_cabs(args):
                      ms_per_sketch=round(ptot / psteps, 4), rel_fro_error=perrs[-1], prec="fp32",
                      form="one sketch per launch sequence, one stream, no graph")
 
+    # ---- the FP64 mode (the paper's arithmetic) at the same configuration, same
+    # form (B sketches over the lanes, graph); without the error, whose exact
+    # FP64 form costs 2 m n k FP64 flops
+    fp64_mode = None
+    if prec != "fp64" and not args.no_fp64_mode:
+        p64 = [cabs.make_params(wl["m"], wl["n"], k, iters=iters, seed=1607 + rank * 1000 + b, prec="fp64",
+                                trunc_rtol=trunc_rtol(wl, k), flags=flags, core=wl["core"]) for b in range(B)]
+        o64 = [cabs.alloc_result(q, device) for q in p64]
+        off64, tot64 = cabs.batched_layout(srcs, p64)
+        ws64 = torch.empty(tot64 + 512, dtype=torch.uint8, device=device)
+
+        def step64():
+            with torch.cuda.stream(stream):
+                if B == 1:
+                    cabs.cabs_sketch(ctx, src, p64[0], ws=ws64, out=o64[0], stream=stream)
+                else:
+                    cabs.cabs_sketch_batched(ctx, srcs, p64, o64, ws64, off64, lanes=args.lanes, use_graph=True,
+                                             stream=stream)
+            return []
+
+        step64()
+        torch.cuda.synchronize()
+        n64 = 2
+        _, t64, _ = timed_steps(ctx, cabs, step64, n64, stream, world, barrier, flush)
+        fp64_mode = dict(value=round(job_value(world, B, n64, t64), 4), unit="sketches/s", steps=n64,
+                         ms_per_step=round(t64 / n64, 3), prec="fp64", error_included=False,
+                         form=f"{B} sketches over {args.lanes if B > 1 else 1} lanes, graph; no error")
+        del ws64, o64
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return None
     peaks = load_peaks()
+    alu = measure_alu_peaks(device)  # after the timed region
+    peaks.update({k_: v for k_, v in alu.items() if k_.endswith("_tflops")})
     eb = 8 if prec == "fp64" else 4
     roof, table, roof_next = roofline(prof, wl, k, iters, eb, sweeps, args.steps * B, peaks, prec,
                                       args.workload if not (args.m or args.n) else None,
@@ -709,7 +791,11 @@ def run_cabs(args):
                roofline=roof, roofline_next=roof_next, kernels=table,
                kernel_timing=("serial profiled pass of the same batch after the timed region" if B > 1
                               else "timed region"),
-               gather=gather, plain_fp32=plain, e2e=e2e, clocks=clocks)
+               gather=gather, plain_fp32=plain, fp64_mode=fp64_mode, e2e=e2e, clocks=clocks,
+               peaks=dict(hbm_gbs=peaks["hbm_gbs"], bf16_tflops=peaks["bf16_tflops"],
+                          bf16_tflops_sustained=peaks["bf16_tflops_sustained"], source=peaks["source"],
+                          measured_here=alu, derived_fp32_tflops=round(FP32_PEAK_TFLOPS, 2),
+                          derived_fp64_tflops=round(FP64_PEAK_TFLOPS, 3)))
     if wl["kind"] == "dense" and "L" in inp:
         res["rel_fro_error_noiseless"] = noiseless_error(inp["L"], outs[0])
     if wl["kind"] != "plain" and not (args.m or args.n) and not args.no_precision:
@@ -835,6 +921,56 @@ def run_sketch_cur(args):
                 e2e_note="Sketch-CUR is a comparison row: device-resident inputs only")
 
 
+def run_oracle_full(args):
+    """The oracle once on the whole dense workload (65536 x 32768, k = 256, c = 5,
+    stabilised core, trunc k 2^-24) on the host, beside the GPU's FP64-mode
+    sketch of the same matrix and seed: pilot and follow-up indices compared
+    bit for bit, U S V^T on 64 sampled rows, and both exact errors. One JSON
+    line; minutes of host time (not part of the default run)."""
+    import numpy as np
+    import torch
+
+    from oracle import cabs_ref as o
+    from paper_1607_07395_gb300 import cabs
+    wl = WORKLOADS["dense"]
+    device = torch.device("cuda", 0)
+    inp = make_inputs(wl, device, seed=1607)
+    A = inp["A"]
+    k = wl["k"]
+    tr = trunc_rtol(wl, k)
+    ctx = cabs.Context(0)
+    src = cabs.dense_source(A)
+    p = cabs.make_params(wl["m"], wl["n"], k, iters=wl["iters"], seed=1607, prec="fp64", core=wl["core"],
+                         trunc_rtol=tr, err_samples=0, err_seed=3)
+    t0 = time.perf_counter()
+    sk = cabs.cabs_sketch(ctx, src, p)
+    torch.cuda.synchronize()
+    gpu_s = time.perf_counter() - t0
+    gpu_err = float(sk.err.cpu().item())
+    Ah = A.cpu().numpy()
+    del inp
+    t0 = time.perf_counter()
+    ref = o.cabs(o.DenseSource(Ah), k, iters=wl["iters"], seed=1607, mode=wl["core"], trunc_rtol=tr)
+    t1 = time.perf_counter()
+    ref_err = o.rel_fro_error_dense(Ah, ref.final.U, ref.final.S, ref.final.V)
+    t2 = time.perf_counter()
+    rows = np.arange(0, wl["m"], wl["m"] // 64)
+    U, S, V = (t.cpu().numpy() for t in (sk.U, sk.S, sk.V))
+    got = (U[rows] * S) @ V.T
+    want = (ref.final.U[rows] * ref.final.S) @ ref.final.V.T
+    return dict(workload="dense 65536x32768 FP32, k=256, c=5, stabilised, trunc k 2^-24, seed 1607",
+                threads=int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+                oracle_sketch_s=round(t1 - t0, 2), oracle_error_s=round(t2 - t1, 2), oracle_error=ref_err,
+                gpu_fp64_error=gpu_err, gpu_fp64_sketch_and_error_s=round(gpu_s, 3),
+                error_rel_diff=abs(gpu_err - ref_err) / ref_err,
+                pilot_rows_equal=sk.pilot_rows.cpu().numpy().tolist() == ref.pilot_rows.tolist(),
+                pilot_cols_equal=sk.pilot_cols.cpu().numpy().tolist() == ref.pilot_cols.tolist(),
+                rows_equal=sk.rows.cpu().numpy().tolist() == ref.rows.tolist(),
+                cols_equal=sk.cols.cpu().numpy().tolist() == ref.cols.tolist(),
+                factors_rel_diff_sampled_rows=float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                rank=[int(ref.pilot.rank), int(ref.final.rank)])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -917,6 +1053,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-mode error report on the slice")
+    ap.add_argument("--no-fp64-mode", action="store_true", help="skip the FP64-mode throughput leg")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="run the oracle once on the whole dense workload beside the GPU FP64 sketch (minutes)")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--batch-count", type=int, default=512, help="members of the batched workload")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="measured seconds of the serving workload")
@@ -932,7 +1071,9 @@ def main():
     if args.cpu_worker:
         cpu_worker(args.workload, args.steps)
         return
-    if args.workload in ("batched", "serve"):
+    if args.oracle_full:
+        res = run_oracle_full(args)
+    elif args.workload in ("batched", "serve"):
         res = run_systems(args)
     elif args.impl == "reference":
         res = run_reference(args)
