@@ -17,8 +17,10 @@
 //    the blocks move one step along the round-robin circle through distributed
 //    shared memory; one cluster barrier per round, double-buffered. In the
 //    cross-block steps a warp keeps its top column in registers for the whole
-//    round, and the V columns receive each step's rotations one step later on
-//    otherwise idle warps, off the dependent chain of W rotations.
+//    round, and the same warp applies each step's rotation to the V columns
+//    one step later, off the dependent chain of W rotations (measured on
+//    GB300: slightly faster than giving V its own warps, which compete with
+//    the W chain for issue slots).
 //  Phase B (FP64, refinement): from U0, V0, iterate
 //      T = U^T W V,  R = I - U^T U,  S = I - V^T V,
 //      d_i = T_ii / (1 - (R_ii + S_ii) / 2),
@@ -89,29 +91,32 @@ __device__ __forceinline__ void rr_pair(int round, int pr, int kk, int& p, int& 
 }
 
 // The Hestenes rotation that makes two columns with squared norms a, b and
-// inner product g orthogonal: zeta = (b - a) / 2g,
-// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t.
-// Returns 0 (no rotation) unless |g| > tol sqrt(a b), tested as
+// inner product g orthogonal, |angle| <= pi/4: with d = b - a and
+// r = sqrt(d^2 + 4 g^2), cos 2t = |d| / r, so c = sqrt((1 + |d| / r) / 2) and
+// s = sign(d) g / (r c) (the same c, s as t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), zeta = d / 2g, c = 1 / sqrt(1 + t^2), s = c t). Two
+// reciprocal square roots and no division or branch keep the dependent
+// chain of a rotation step short; c^2 + s^2 = 1 up to rounding, and Phase A
+// needs only approximate rotations (the FP64 refinement finishes the job).
+// Returns 0 (c = 1, s = 0: no rotation) unless |g| > tol sqrt(a b), tested as
 // g^2 > tol^2 a b; else 1, or 3 when |g| > kStopA sqrt(a b) (the sweep is
-// not the last one). Phase A needs only approximate rotations -- c and s form
-// an exact rotation for any t, and the FP64 refinement finishes the job -- so
-// the divisions and square roots are the fast hardware approximations,
-// which shortens the dependent chain of every rotation step.
+// not the last one). c and s depend only on the ratio d : g, so d and g are
+// first scaled by 2^-100 or 2^100 when the larger of them is above 1e18 or
+// below 1e-18, keeping d^2 + 4 g^2 clear of overflow and of the subnormal
+// range.
 __device__ __forceinline__ int jacobi_cs(float a, float b, float g, float& c, float& s) {
   const float ab = a * b, g2 = g * g;
-  if (!(g2 > kTolA * kTolA * ab)) return 0;
-  const float zeta = __fdividef(b - a, 2.f * g);
-  const float az = fabsf(zeta);
-  float t;
-  if (az > 1e18f) {
-    t = __fdividef(0.5f, zeta);
-  } else {
-    const float q = fmaf(zeta, zeta, 1.f);
-    t = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
-  }
-  c = rsqrtf(fmaf(t, t, 1.f));
-  s = c * t;
-  return g2 > kStopA * kStopA * ab ? 3 : 1;
+  const float big = fmaxf(fabsf(b - a), fabsf(g));
+  const float sc = big > 1e18f ? 7.888609052210118e-31f : (big < 1e-18f ? 1.2676506002282294e30f : 1.f);
+  const float d = (b - a) * sc, gs = g * sc;
+  const float q1 = rsqrtf(fmaf(4.f * gs, gs, d * d));
+  const float h = fmaf(0.5f * fabsf(d), q1, 0.5f);
+  const float q2 = rsqrtf(h);
+  const float sg = (d < 0.f ? -gs : gs) * q1;
+  const int code = g2 > kTolA * kTolA * ab ? (g2 > kStopA * kStopA * ab ? 3 : 1) : 0;
+  c = code ? h * q2 : 1.f;
+  s = code ? sg * q2 : 0.f;
+  return code;
 }
 
 // Rotates columns x, y (length k, lane-strided) so that they become
@@ -714,10 +719,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) svd32_cluster_kernel(const
       // every column of the top block against every column of the bottom block:
       // in step s warp j rotates W columns (top j, bottom (j + s) % b), keeping
       // top column j in registers for the whole round, and records (c, s); the
-      // same rotation reaches the V columns one step later on another warp
-      // (or the same warp when there are no spare warps), off the critical path
+      // same warp applies that rotation to the V columns one step later, off
+      // the critical path
       {
-        const bool spare = 2 * b <= nwarps;
         float xr[R];
         float an = 0.f;
         if (warp < b) {
@@ -731,13 +735,12 @@ __global__ void __launch_bounds__(kClusterThreads, 1) svd32_cluster_kernel(const
         }
         for (int s = 0; s <= b; ++s) {
           if (warp < b && s < b) {
-            const int q = (warp + s) % b;
+            const int q = warp + s - (warp + s >= b ? b : 0);  // (warp + s) mod b, both < b
             my_rot |= rotate_top_reg<R>(xr, an, Wb + (size_t)q * kp, &bnorm[q], lane, &rot_cs[s][warp]);
           }
-          const int vw = spare ? warp - b : warp;
-          if (s >= 1 && vw >= 0 && vw < b) {
-            const int q = (vw + s - 1) % b;
-            apply_rot_v<R>(Vt + (size_t)vw * kp, Vb + (size_t)q * kp, lane, rot_cs[s - 1][vw]);
+          if (s >= 1 && warp < b) {
+            const int q = warp + s - 1 - (warp + s - 1 >= b ? b : 0);
+            apply_rot_v<R>(Vt + (size_t)warp * kp, Vb + (size_t)q * kp, lane, rot_cs[s - 1][warp]);
           }
           __syncthreads();
         }
