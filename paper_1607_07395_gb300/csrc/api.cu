@@ -71,6 +71,10 @@ DeviceGuard::~DeviceGuard() {
   if (ok && prev != target) cudaSetDevice(prev);
 }
 
+// The BF16 and TF32 modes take the extrapolation products on the tensor
+// cores (3 x TF32, FP32-level); FP32 and FP64 keep CUDA-core arithmetic.
+static bool tc_extrap_ok(int prec) { return prec == CABS_PREC_BF16 || prec == CABS_PREC_TF32; }
+
 // ------------------------------------------------------------- validation
 
 static bool finite(double x) { return std::isfinite(x); }
@@ -221,7 +225,7 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   CABS_TRY(launch_draw2(p.seed, 0, m, k1, w.pr_drawn, out.pilot_rows, 1, n, k1, w.pc_drawn, out.pilot_cols, s));
   CABS_TRY(launch_gather(src, m, n, out.pilot_rows, k1, out.pilot_cols, k1, f64, w.C, w.Rt, w.W, s));
   // step 2: pilot sketching and embeddings P, Q
-  CABS_TRY(launch_core(m, n, k1, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, true, w.P, w.S_pilot, w.Q,
+  CABS_TRY(launch_core(m, n, k1, f64, tc_extrap_ok(p.prec), p.core, p.trunc_rtol, w.C, w.Rt, w.W, true, w.P, w.S_pilot, w.Q,
                        &dg->rank_pilot, &dg->sweeps_pilot, &dg->refine_pilot, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
   if (p.flags & CABS_FLAG_HARD_THRESHOLD) {
@@ -262,7 +266,7 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
   void* U1 = svd_form ? w.P : out.U;
   void* V1 = svd_form ? w.Q : out.V;
   double* S1 = svd_form ? w.S_pilot : out.S;
-  CABS_TRY(launch_core(m, n, k2, f64, p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, U1, S1, V1, &dg->rank_final,
+  CABS_TRY(launch_core(m, n, k2, f64, tc_extrap_ok(p.prec), p.core, p.trunc_rtol, w.C, w.Rt, w.W, false, U1, S1, V1, &dg->rank_final,
                        &dg->sweeps_final, &dg->refine_final, &dg->status, nullptr, nullptr, nullptr, w.core,
                        w.core_bytes, s));
   // supplementary Section 3: orthogonalisation into SVD form
@@ -463,7 +467,7 @@ cabs_status cabs_sketching(cabs_ctx* ctx, int64_t m, int64_t n, int32_t k, int32
   CABS_REQUIRE(std::isfinite(trunc_rtol) && trunc_rtol >= 0.0, "bad trunc_rtol");
   CABS_REQUIRE(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be non-NULL and 256-byte aligned");
   DeviceGuard g(ctx->device);
-  return launch_core(m, n, k, prec == CABS_PREC_FP64, core, trunc_rtol, C, Rt, W, embed != 0, out1, S, out2, d_rank,
+  return launch_core(m, n, k, prec == CABS_PREC_FP64, tc_extrap_ok(prec), core, trunc_rtol, C, Rt, W, embed != 0, out1, S, out2, d_rank,
                      d_sweeps, nullptr, nullptr, d_sig, d_Uw, d_Vw, ws, ws_bytes, (cudaStream_t)stream);
 }
 

@@ -6,10 +6,12 @@
 //     the GPU).
 //  2. Truncation: keep sigma_i > max(trunc_rtol, k 2^-52) sigma_1; dropped
 //     components get zero columns in U_w and V_w, hence zero factors and S.
-//  3. Extrapolation a = C V_w (m x k), b = Rt U_w (n x k) on CUDA cores, in
-//     the working precision; each CTA also writes the FP64 sum of squares of
-//     its tile's columns, and the norms N_c, N_r are reduced by one CTA per
-//     column in a fixed order (deterministic).
+//  3. Extrapolation a = C V_w (m x k), b = Rt U_w (n x k): on CUDA cores in
+//     the working precision (FP64, FP32 modes), or on the tensor cores as
+//     three TF32 products to FP32-level accuracy in the BF16 and TF32 modes
+//     (tc_extrap.cu, k <= 256); each CTA also writes the FP64 sum of squares
+//     of its 128-row tile's columns, and the norms N_c, N_r are reduced by
+//     one CTA per column in a fixed order (deterministic).
 //  4. Scale: S_i = N_c,i N_r,i / sigma_i (pseudo-skeleton C W^+ R, Eq. W) or
 //     S_i = sigma_i sqrt(mn)/k (stabilised form); the factors are
 //     U = a N_c^-1, V = b N_r^-1, or the embeddings P = U S^1/2, Q = V S^1/2.
@@ -199,6 +201,7 @@ struct CoreWs {
   SvdWs svd;
   double *sig, *Uw, *Vw, *part1, *part2, *f1, *f2;
   int *rank, *sweeps;
+  void* img;  // tensor-core extrapolation: B images
 };
 
 CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
@@ -214,6 +217,7 @@ CoreWs carve_core(Carve& cv, int64_t m, int64_t n, int k) {
   w.f2 = cv.take<double>(k);
   w.rank = cv.take<int>(1);
   w.sweeps = cv.take<int>(1);
+  w.img = k <= 256 ? (void*)cv.take<char>(tc_extrap_img_bytes(k)) : nullptr;
   return w;
 }
 
@@ -242,7 +246,7 @@ cabs_status extrap_pair(int tn, const T* C, int64_t m, const T* Rt, int64_t n, i
 }
 
 template <typename T>
-cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol, const T* C, const T* Rt,
+cabs_status core_typed(int64_t m, int64_t n, int k, bool tc_ok, int core, double trunc_rtol, const T* C, const T* Rt,
                        const double* W, bool embed, T* out1, double* S, T* out2, int* d_rank, int* d_sweeps,
                        int* d_refine, int* d_status, double* d_sig, double* d_Uw, double* d_Vw, void* ws, size_t ws_bytes,
                        cudaStream_t stream) {
@@ -260,8 +264,18 @@ cabs_status core_typed(int64_t m, int64_t n, int k, int core, double trunc_rtol,
   CABS_TRY(launch_svd(W, k, trunc_rtol, sizeof(T) == 8 ? 0.0 : kResolveReduced, sig, Uw, Vw, rank, sweeps, d_refine,
                       d_status, w.svd, stream));
   const int nb1 = ceil_div(m, ExtrapTile<T>::BM), nb2 = ceil_div(n, ExtrapTile<T>::BM);
-  const int tn = current_tune().extrap_tn;
-  CABS_TRY(extrap_pair<T>(tn, C, m, Rt, n, k, Vw, Uw, out1, out2, w.part1, w.part2, stream));
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (tc_ok && k <= 256) {
+      // 128-row blocks, as the FP32 CUDA-core tile (nb1, nb2 above)
+      CABS_TRY(launch_tc_extrap_pair(C, m, Rt, n, k, Vw, Uw, out1, out2, w.part1, w.part2, w.img, d_status, stream));
+      done = true;
+    }
+  }
+  if (!done) {
+    const int tn = current_tune().extrap_tn;
+    CABS_TRY(extrap_pair<T>(tn, C, m, Rt, n, k, Vw, Uw, out1, out2, w.part1, w.part2, stream));
+  }
   const double mn_over_kk = (double)m * (double)n / ((double)k * (double)k);
   CABS_LAUNCH(stream, "core_finalize_kernel",
               core_finalize_kernel<<<k, 256, 0, stream>>>(w.part1, nb1, w.part2, nb2, k, sig, rank, core, embed ? 1 : 0,
@@ -298,15 +312,15 @@ size_t core_ws_bytes(int64_t m, int64_t n, int k, bool /*elem_f64*/) {
   return cv.used;
 }
 
-cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
-                        const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
+cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, bool tc_ok, int core, double trunc_rtol,
+                        const void* C, const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
                         int* d_rank, int* d_sweeps, int* d_refine, int* d_status, double* d_sig, double* d_Uw,
                         double* d_Vw, void* ws, size_t ws_bytes, cudaStream_t stream) {
   if (elem_f64)
-    return core_typed<double>(m, n, k, core, trunc_rtol, (const double*)C, (const double*)Rt, W, embed,
+    return core_typed<double>(m, n, k, false, core, trunc_rtol, (const double*)C, (const double*)Rt, W, embed,
                               (double*)out1, S, (double*)out2, d_rank, d_sweeps, d_refine, d_status, d_sig, d_Uw, d_Vw, ws,
                               ws_bytes, stream);
-  return core_typed<float>(m, n, k, core, trunc_rtol, (const float*)C, (const float*)Rt, W, embed, (float*)out1, S,
+  return core_typed<float>(m, n, k, tc_ok, core, trunc_rtol, (const float*)C, (const float*)Rt, W, embed, (float*)out1, S,
                            (float*)out2, d_rank, d_sweeps, d_refine, d_status, d_sig, d_Uw, d_Vw, ws, ws_bytes, stream);
 }
 

@@ -17,8 +17,10 @@ cabs_status launch_gather(const cabs_source& src, int64_t m, int64_t n, const in
 
 // a3/a4/a8: the sketching routine. Workspace bytes for (m, n, k, elem).
 size_t core_ws_bytes(int64_t m, int64_t n, int k, bool elem_f64);
-cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, double trunc_rtol, const void* C,
-                        const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
+// tc_ok: an FP32 (not FP64) sketch in the BF16 or TF32 mode, whose
+// extrapolation products may run on the tensor cores (3 x TF32, k <= 256).
+cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, bool tc_ok, int core, double trunc_rtol,
+                        const void* C, const void* Rt, const double* W, bool embed, void* out1, double* S, void* out2,
                         int* d_rank, int* d_sweeps, int* d_refine, int* d_status, double* d_sig, double* d_Uw,
                         double* d_Vw, void* ws, size_t ws_bytes, cudaStream_t stream);
 
@@ -28,6 +30,15 @@ cabs_status launch_core(int64_t m, int64_t n, int k, bool elem_f64, int core, do
 int extrap_row_blocks(int64_t M, bool elem_f64);
 cabs_status launch_extrap_gemm(const void* X, int64_t M, int K, const double* B, int N, bool elem_f64, void* out,
                                double* part, const char* name, cudaStream_t stream);
+
+// The two extrapolation products a = C V_w (m x k) and b = Rt U_w (n x k) on
+// the tensor cores, 3 x TF32 (k <= 256); parts as launch_extrap_gemm with
+// 128-row blocks; img: tc_extrap_img_bytes(k) of scratch; a wait that runs
+// out sets bit value 4 of *status (may be NULL).
+size_t tc_extrap_img_bytes(int k);
+cabs_status launch_tc_extrap_pair(const float* C, int64_t m, const float* Rt, int64_t n, int k, const double* Vw,
+                                  const double* Uw, float* out1, float* out2, double* part1, double* part2, void* img,
+                                  int* status, cudaStream_t stream);
 
 // G = X^T X (K x K, FP64) of a tall X (M x K, elem); part: gram_ws_bytes(M, K) of scratch.
 size_t gram_ws_bytes(int64_t M, int K, bool elem_f64);

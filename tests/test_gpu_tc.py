@@ -132,3 +132,38 @@ def test_tc_snap_fallback_when_candidates_taken(ctx, C, prec):
     want_o, _ = o.snap(X.astype(np.float64), Z.astype(np.float64))
     assert to_np(order).tolist() == want_o.tolist()
     assert len(set(to_np(order).tolist())) == Z.shape[0]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("m,n,k,core", [(1000, 700, 256, "pinv"), (777, 1333, 200, "stabilized"),
+                                        (300, 129, 65, "pinv"), (5000, 257, 33, "stabilized"), (130, 300, 8, "pinv")])
+def test_tc_extrapolation_matches_fp64(ctx, C, prec, m, n, k, core):
+    """The extrapolation products a = C V_w, b = R^T U_w of the sketching
+    routine (Section 4.1) on the tensor cores (three TF32 products, BF16 and
+    TF32 modes): U = a N_c^-1, V = b N_r^-1 and S against the same products
+    in FP64 from the GPU's own V_w, U_w, to 2e-5 per column (the FP32
+    CUDA-core path is held to the same bar). Row counts are not multiples of
+    the 128-row tile, and k = 65, 33 exercise widths that are not multiples
+    of 4."""
+    g = np.random.default_rng(m + n + k)
+    Cm = (g.standard_normal((m, k)) * g.uniform(0.1, 10.0, size=k)).astype(np.float32)
+    Rt = (g.standard_normal((n, k)) * g.uniform(0.1, 10.0, size=k)).astype(np.float32)
+    W = Cm[:k].astype(np.float64)  # FP64, as the routine takes it (the FP32 values)
+    res = {}
+    for pr in (prec, "fp32"):
+        out = C.cabs_sketching(ctx, dev(Cm), dev(Rt), dev(W), m, n, prec=pr, core=core, trunc_rtol=k * 2.0 ** -24)
+        torch.cuda.synchronize()
+        r = int(out["rank"].item())
+        Uw, Vw, sig = (out[x].cpu().numpy() for x in ("Uw", "Vw", "sig"))
+        a = Cm.astype(np.float64) @ Vw
+        b = Rt.astype(np.float64) @ Uw
+        nc, nr = np.linalg.norm(a, axis=0), np.linalg.norm(b, axis=0)
+        S_ref = np.zeros(k)
+        S_ref[:r] = sig[:r] * np.sqrt(m * n) / k if core == "stabilized" else nc[:r] * nr[:r] / sig[:r]
+        U, V, S = out["out1"].cpu().numpy(), out["out2"].cpu().numpy(), out["S"].cpu().numpy()
+        eu = np.linalg.norm(U[:, :r] - a[:, :r] / nc[:r], axis=0).max()
+        ev = np.linalg.norm(V[:, :r] - b[:, :r] / nr[:r], axis=0).max()
+        es = np.abs(S[:r] / S_ref[:r] - 1).max()
+        assert np.all(U[:, r:] == 0) and np.all(V[:, r:] == 0) and np.all(S[r:] == 0)
+        res[pr] = (eu, ev, es)
+        assert max(eu, ev, es) <= 2e-5, (pr, eu, ev, es)
