@@ -62,12 +62,17 @@ constexpr int kCtaMaxK = 64;           // one-CTA Phase A up to this k
 #endif
 constexpr float kTolA = CABS_SVD_TOL_A;  // Phase A rotation threshold |g| > tol sqrt(a b)
 // Phase A stops after a sweep in which no pair had |g| > kStopA sqrt(a b):
-// cyclic Jacobi converges quadratically there, so the next sweep would find
-// every |g| near kStopA^2 times a small constant, at the rotation threshold
-// (a CPU model of the kernel on the sketching workloads: 6.7e-4 in the last
-// sweep that rotated, 1e-5 in the next, which then rotated nothing), and
-// the FP64 refinement takes the factors from there.
-constexpr float kStopA = 1e-3f;
+// cyclic Jacobi converges quadratically there, so the factors are then
+// orthogonal to about kStopA^2 (a CPU model of the kernel on the sketching
+// workloads: largest |g| / sqrt(a b) per sweep 0.03, 8e-3, 7e-4, 1e-5), and
+// the quadratically convergent FP64 refinement takes them from there. At
+// 1e-2 the k = 256 dense sketch stops one sweep earlier than at 1e-3 (8
+// instead of 9) with the same 3 refinement iterations; at 5e-2 (7 sweeps)
+// the refinement needed a 4th iteration, which costs more than the sweep.
+#ifndef CABS_SVD_STOP_A
+#define CABS_SVD_STOP_A 1e-2f
+#endif
+constexpr float kStopA = CABS_SVD_STOP_A;
 constexpr int kMaxSweepsA = 40;
 constexpr int kItersB = 8;
 constexpr double kMaxCorrB = 0.05;      // Phase B: larger first-order corrections are deferred
