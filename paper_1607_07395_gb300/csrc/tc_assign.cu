@@ -95,8 +95,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ tc::Barriers bars;
   __shared__ Best2 xchg[4][32];
+  __shared__ float zn_s[kBN];  // |z_j|^2, +inf past k2 (such columns never win)
+  for (int j = threadIdx.x; j < kBN; j += blockDim.x) zn_s[j] = j < k2 ? zn[j] : __int_as_float(0x7f800000);
   uint8_t *Bres, *Aring;
-  tc::setup<BN>(smem_raw, nch, Bres, Aring, &bars);
+  tc::setup<BN>(smem_raw, nch, Bres, Aring, &bars);  // its __syncthreads publishes zn_s
   const int u0 = (int)((long long)units * blockIdx.x / gridDim.x);
   const int u1 = (int)((long long)units * (blockIdx.x + 1) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -128,17 +130,30 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
       accph[ab] ^= 1;
       tc::fence_after_sync();
       Best2 s{__int_as_float(0x7f800000), __int_as_float(0x7f800000), 0x7fffffff, 0x7fffffff};
-#pragma unroll 1
-      for (int j = 0; j < BN / 2 / 32; ++j) {
-        const int lc = half * (BN / 2) + j * 32;  // column inside the block
-        const int c0 = cb * BN + lc;              // centre index
-        if (c0 >= k2) break;                      // warp-uniform
-        float v[32];
-        tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * BN + lc) + ((uint32_t)(sub * 32) << 16), v);
+      // this half's columns in groups of 32, the next group loading from
+      // TMEM while the current one is scanned; within a thread the centre
+      // index only grows, so a strict < keeps the lower index on ties
+      constexpr int kGroups = BN / 2 / 32;
+      const int c_half = cb * BN + half * (BN / 2);  // first centre of this half
+      const int ng = min(kGroups, max(0, (k2 - c_half + 31) / 32));  // warp-uniform
+      const uint32_t taddr = bars.tmem_base + (uint32_t)(ab * BN + half * (BN / 2)) + ((uint32_t)(sub * 32) << 16);
+      uint32_t r[2][32];
+      if (ng > 0) tc::tmem_ld32_issue(taddr, r[0]);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int jj = c0 + q;
-          if (jj < k2) best2_push(s, fmaf(-2.f, v[q], __ldg(zn + jj)), jj);
+      for (int j = 0; j < kGroups; ++j) {
+        if (j < ng) {
+          tc::tmem_ld_wait(r[j & 1]);
+          if (j + 1 < ng) tc::tmem_ld32_issue(taddr + (uint32_t)((j + 1) * 32), r[(j + 1) & 1]);
+          const int c0 = c_half + j * 32;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float dv = fmaf(-2.f, __uint_as_float(r[j & 1][q]), zn_s[c0 + q]);
+            const bool lt1 = dv < s.b1, lt2 = dv < s.b2;
+            s.b2 = lt1 ? s.b1 : (lt2 ? dv : s.b2);
+            s.j2 = lt1 ? s.j1 : (lt2 ? c0 + q : s.j2);
+            s.b1 = lt1 ? dv : s.b1;
+            s.j1 = lt1 ? c0 + q : s.j1;
+          }
         }
       }
       tc::fence_before_sync();
