@@ -19,7 +19,7 @@
 //     same direct FP32 distances as step 1 decide the 8 candidates.
 //  3. snap_greedy_kernel (cooperative): CTA 0's warp 0 walks the centres in
 //     order and picks the lowest untaken candidate inside the tie window of
-//     the first untaken one (a bitmap of taken rows); only if all 8 are taken,
+//     the first untaken one (taken rows in shared memory); only if all 8 are taken,
 //     or the window reaches the 8th, do all CTAs scan every row for that
 //     centre. The picks are then sorted ascending.
 #include "common.cuh"
@@ -232,6 +232,14 @@ __device__ __forceinline__ void taken_add(int* set, int r) {
   }
 }
 
+// rows per warp and step of a full scan (FP64 keeps half: its loads take
+// twice the registers)
+template <typename T>
+__host__ __device__ constexpr int scan_rows() { return sizeof(T) == 4 ? 8 : 4; }
+// Rows whose taken set fits in shared memory as a bitmap (64 KB): larger
+// inputs keep the open-addressing set of the rows taken so far.
+constexpr long long kMaxBitWords = 16384;
+
 // Pass 1 of a full scan: the (distance, row) minimum over rows [lo, hi) not
 // in the taken bitmap, for centre z; each computed distance is also stored
 // in dist[l] for pass 2.
@@ -239,21 +247,25 @@ template <typename T>
 __device__ void scan_slice(const T* __restrict__ X, int d, const T* __restrict__ z, long long lo, long long hi,
                            const unsigned* taken, T* __restrict__ dist, T& best, int& brow) {
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int kScanRows_T = scan_rows<T>();
   best = pos_inf<T>();
   brow = 0x7fffffff;
-  for (long long l0 = lo + (long long)wi * 4; l0 < hi; l0 += (long long)nw * 4) {
-    bool skip[4];
-    T s4[4];
+  for (long long l0 = lo + (long long)wi * kScanRows_T; l0 < hi; l0 += (long long)nw * kScanRows_T) {
+    bool skip[kScanRows_T];
+    T s4[kScanRows_T];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kScanRows_T; ++u) {
       const long long l = l0 + u;
       skip[u] = l >= hi || ((((volatile const unsigned*)taken)[l >> 5] >> (l & 31)) & 1u);
       s4[u] = T(0);
     }
+    // unrolled so that the rows' loads (d <= 256: 8 per row and lane) are in
+    // flight together; each lane still sums its dimensions in order
+#pragma unroll 8
     for (int q = lane; q < d; q += 32) {
       const T zq = z[q];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kScanRows_T; ++u) {
         if (!skip[u]) {
           const T t = X[(l0 + u) * d + q] - zq;
           s4[u] = fma(t, t, s4[u]);
@@ -261,7 +273,7 @@ __device__ void scan_slice(const T* __restrict__ X, int d, const T* __restrict__
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kScanRows_T; ++u) {
       const T sv = warp_sum(s4[u]);
       if (skip[u]) continue;
       if (lane == 0) dist[l0 + u] = sv;
@@ -325,7 +337,7 @@ __device__ void cta_reduce(T best, int brow, bool window, T* wd, int* wr, T* cta
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
+__global__ void __launch_bounds__(kGreedyThreads, 1) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
     const T* __restrict__ top_d, T tie_rtol, unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row,
     T* fb_lim, T* dist, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks,
@@ -334,18 +346,29 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
   __shared__ int wr[kGreedyThreads / 32];
   // CTA 0's walk reads the candidate lists, their distances, the centres'
   // squared norms and the rows taken so far from shared memory: the lists
-  // are staged once, the taken rows (at most k2) live in an open-addressing
-  // set of kTakenSlots slots. The global bitmap is written too, for the CTAs'
-  // scans when a centre's list does not decide.
-  // dynamic shared memory: s_topd[k2 kTop], s_zz[k2] (T), s_top[k2 kTop], s_taken (int)
+  // are staged once, the taken rows are a bitmap (inputs up to
+  // 32 kMaxBitWords rows) or, beyond that, an open-addressing set of
+  // kTakenSlots slots (at most k2 rows are ever taken). The global bitmap is
+  // written too, for the CTAs' scans when a centre's list does not decide.
+  // dynamic shared memory: s_topd[k2 kTop], s_zz[k2] (T), s_top[k2 kTop], s_taken (int),
+  // then (M <= 32 kMaxBitWords) the taken rows as a bitmap s_bits
   extern __shared__ __align__(16) unsigned char greedy_smem[];
   T* s_topd = (T*)greedy_smem;
   T* s_zz = s_topd + (size_t)CABS_MAX_K * kTop;
   int* s_top = (int*)(s_zz + CABS_MAX_K);
   int* s_taken = s_top + (size_t)CABS_MAX_K * kTop;
+  unsigned* s_bits = (unsigned*)(s_taken + kTakenSlots);
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
+  const bool use_bits = words <= kMaxBitWords;
+  auto has = [&](int r) { return use_bits ? ((s_bits[r >> 5] >> (r & 31)) & 1u) != 0u : taken_has(s_taken, r); };
+  auto add = [&](int r) {
+    if (use_bits)
+      s_bits[r >> 5] |= 1u << (r & 31);
+    else
+      taken_add(s_taken, r);
+  };
   // a barrier that gave up: report it (diagnostics status bit 2) and leave
   auto gave_up = [&]() {
     if (tid == 0 && status) atomicOr(status, 4);
@@ -358,6 +381,8 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       s_topd[e] = top_d[e];
     }
     for (int e = tid; e < kTakenSlots; e += blockDim.x) s_taken[e] = -1;
+    if (use_bits)
+      for (long long e = tid; e < words; e += blockDim.x) s_bits[e] = 0u;
     for (int j = wi; j < k2; j += nw) {
       T s = T(0);
       for (int q = lane; q < d; q += 32) s = fma(Z[(size_t)j * d + q], Z[(size_t)j * d + q], s);
@@ -373,7 +398,7 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       for (; jj < k2; ++jj) {
         const int r = lane < kTop ? s_top[jj * kTop + lane] : 0x7fffffff;
         const T dv = lane < kTop ? s_topd[jj * kTop + lane] : pos_inf<T>();
-        const bool ok = lane < kTop && r >= 0 && r < M && !taken_has(s_taken, r);
+        const bool ok = lane < kTop && r >= 0 && r < M && !has(r);
         const unsigned good = __ballot_sync(0xffffffffu, ok);
         if (!good) break;
         const T dstar = __shfl_sync(0xffffffffu, dv, __ffs(good) - 1);
@@ -382,10 +407,12 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
         if (dlast <= lim) break;  // rows outside the list may lie inside the window
         int cand = (ok && dv <= lim) ? r : 0x7fffffff;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, off));
+        for (int off = kTop / 2; off > 0; off >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, off));
         if (lane == 0) {
-          taken_add(s_taken, cand);
-          taken[cand >> 5] |= 1u << (cand & 31);
+          add(cand);
+          // a reduction, not a read-modify-write: the walk does not wait on it
+          // (the scans read the bitmap only after the next grid barrier)
+          atomicOr(&taken[cand >> 5], 1u << (cand & 31));
           picks[jj] = cand;
         }
         __syncwarp();
@@ -423,8 +450,8 @@ __global__ void __launch_bounds__(kGreedyThreads) snap_greedy_kernel(
       int bi = cta_row[0];
       for (unsigned b = 1; b < G; ++b) bi = min(bi, cta_row[b]);
       if (bi >= 0 && bi < M) {
-        taken[bi >> 5] |= 1u << (bi & 31);
-        taken_add(s_taken, bi);
+        atomicOr(&taken[bi >> 5], 1u << (bi & 31));
+        add(bi);
       }
       picks[j] = bi;
       if (fallbacks) atomicAdd(fallbacks, 1);
@@ -514,11 +541,15 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
     CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
     CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
   }
-  const size_t gsmem = (size_t)CABS_MAX_K * (kTop + 1) * sizeof(T) + (size_t)(CABS_MAX_K * kTop + kTakenSlots) * 4;
+  const long long words = (M + 31) / 32;
+  const size_t gsmem = (size_t)CABS_MAX_K * (kTop + 1) * sizeof(T) + (size_t)(CABS_MAX_K * kTop + kTakenSlots) * 4 +
+                       (words <= kMaxBitWords ? (size_t)words * 4 : 0);
   cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, gsmem);
-  const int G = std::max(1, std::min({(int)ceil_div(M, 2048), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
+  // a CTA per 512 rows, so that a full scan (a centre whose candidates are
+  // all taken) has enough loads in flight
+  const int G = std::max(1, std::min({(int)ceil_div(M, 512), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
   CABS_LAUNCH(stream, "snap_state_init", snap_state_init_kernel<<<1, 1, 0, stream>>>(w.bar, w.next_fb, wait_limit()));
   const T* Xc = X;
   const T* Zc = Z;

@@ -216,13 +216,16 @@ __global__ void __launch_bounds__(256) assign_resolve_kernel(const float* __rest
     const long long l = base + lane;
     const int a2 = l < M ? alt[l] : -1;
     unsigned mask = __ballot_sync(0xffffffffu, a2 >= 0);
+    const int lab = (mask && l < M) ? labels[l] : 0;
     while (mask) {
       const int b = __ffs(mask) - 1;
       mask &= mask - 1;
       const long long r = base + b;
-      const int j1 = __shfl_sync(0xffffffffu, l < M ? labels[l] : 0, b);
+      const int j1 = __shfl_sync(0xffffffffu, lab, b);
       const int j2 = __shfl_sync(0xffffffffu, a2, b);
       float s1 = 0.f, s2 = 0.f;
+      // unrolled so that a row's loads (d <= 256: 8 per operand) are all in flight at once
+#pragma unroll 8
       for (int q = lane; q < d; q += 32) {
         const float x = __ldg(X + r * d + q);
         const float t1 = x - __ldg(Z + (size_t)j1 * d + q);
