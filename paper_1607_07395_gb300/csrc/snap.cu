@@ -232,13 +232,14 @@ __device__ __forceinline__ void taken_add(int* set, int r) {
   }
 }
 
-// rows per warp and step of a full scan (FP64 keeps half: its loads take
-// twice the registers)
+// rows per warp and step of a full scan: with the dimension loop unrolled,
+// 4 rows keep 32 loads per lane in flight within the kernel's register
+// budget (two 512-thread CTAs per SM)
 template <typename T>
-__host__ __device__ constexpr int scan_rows() { return sizeof(T) == 4 ? 8 : 4; }
-// Rows whose taken set fits in shared memory as a bitmap (64 KB): larger
-// inputs keep the open-addressing set of the rows taken so far.
-constexpr long long kMaxBitWords = 16384;
+__host__ __device__ constexpr int scan_rows() { return 4; }
+// Rows whose taken set fits in shared memory as a bitmap (16 KB, 131072
+// rows): larger inputs keep the open-addressing set of the rows taken so far.
+constexpr long long kMaxBitWords = 4096;
 
 // Pass 1 of a full scan: the (distance, row) minimum over rows [lo, hi) not
 // in the taken bitmap, for centre z; each computed distance is also stored
@@ -337,7 +338,7 @@ __device__ void cta_reduce(T best, int brow, bool window, T* wd, int* wr, T* cta
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kGreedyThreads, 1) snap_greedy_kernel(
+__global__ void __launch_bounds__(kGreedyThreads, 2) snap_greedy_kernel(
     const T* __restrict__ X, long long M, int d, const T* __restrict__ Z, int k2, const int* __restrict__ top_r,
     const T* __restrict__ top_d, T tie_rtol, unsigned* taken, int* picks, int* next_fb, T* cta_best, int* cta_row,
     T* fb_lim, T* dist, GridBarrier* bar, int* __restrict__ order, int* __restrict__ sorted, int* fallbacks,
@@ -350,14 +351,15 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) snap_greedy_kernel(
   // 32 kMaxBitWords rows) or, beyond that, an open-addressing set of
   // kTakenSlots slots (at most k2 rows are ever taken). The global bitmap is
   // written too, for the CTAs' scans when a centre's list does not decide.
-  // dynamic shared memory: s_topd[k2 kTop], s_zz[k2] (T), s_top[k2 kTop], s_taken (int),
-  // then (M <= 32 kMaxBitWords) the taken rows as a bitmap s_bits
-  extern __shared__ __align__(16) unsigned char greedy_smem[];
-  T* s_topd = (T*)greedy_smem;
-  T* s_zz = s_topd + (size_t)CABS_MAX_K * kTop;
-  int* s_top = (int*)(s_zz + CABS_MAX_K);
-  int* s_taken = s_top + (size_t)CABS_MAX_K * kTop;
-  unsigned* s_bits = (unsigned*)(s_taken + kTakenSlots);
+  // shared memory: s_topd[k2 kTop], s_zz[k2] (T), s_top[k2 kTop], s_taken (int),
+  // then (M <= 32 kMaxBitWords) the taken rows as a bitmap s_bits; static
+  // shared memory (at most 46 KB in FP64), so the cooperative launch passes
+  // no dynamic size
+  __shared__ __align__(16) T s_topd[CABS_MAX_K * kTop];
+  __shared__ T s_zz[CABS_MAX_K];
+  __shared__ int s_top[CABS_MAX_K * kTop];
+  __shared__ int s_taken[kTakenSlots];
+  __shared__ unsigned s_bits[kMaxBitWords];
   const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5, nw = blockDim.x >> 5;
   const unsigned G = gridDim.x;
   const long long words = (M + 31) / 32;
@@ -541,12 +543,8 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
     CABS_LAUNCH(stream, "snap_cand_kernel", snap_cand_kernel<T><<<nblk, 256, smem, stream>>>(X, M, d, Z, k2, (T*)w.cand_d, w.cand_r));
     CABS_LAUNCH(stream, "snap_merge_kernel", snap_merge_kernel<T><<<k2, 256, 0, stream>>>((const T*)w.cand_d, w.cand_r, nblk, k2, (T*)w.top_d, w.top_r));
   }
-  const long long words = (M + 31) / 32;
-  const size_t gsmem = (size_t)CABS_MAX_K * (kTop + 1) * sizeof(T) + (size_t)(CABS_MAX_K * kTop + kTakenSlots) * 4 +
-                       (words <= kMaxBitWords ? (size_t)words * 4 : 0);
-  cudaFuncSetAttribute(snap_greedy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, gsmem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, snap_greedy_kernel<T>, kGreedyThreads, 0);
   // a CTA per 512 rows, so that a full scan (a centre whose candidates are
   // all taken) has enough loads in flight
   const int G = std::max(1, std::min({(int)ceil_div(M, 512), coop_grid_cap(sm_count() * std::max(per_sm, 1)), 1024}));
@@ -569,7 +567,7 @@ cabs_status snap_typed(const T* X, int64_t M, int d, const T* Z, int k2, int pre
                   &sorted, &fallbacks, &status};
   CABS_LAUNCH(stream, "snap_greedy_kernel",
               cudaLaunchCooperativeKernel((const void*)snap_greedy_kernel<T>, dim3(G), dim3(kGreedyThreads), args,
-                                          gsmem, stream));
+                                          0, stream));
   return CABS_OK;
 }
 
