@@ -65,12 +65,12 @@ constexpr float kTolA = CABS_SVD_TOL_A;  // Phase A rotation threshold |g| > tol
 // cyclic Jacobi converges quadratically there, so the factors are then
 // orthogonal to about kStopA^2 (a CPU model of the kernel on the sketching
 // workloads: largest |g| / sqrt(a b) per sweep 0.03, 8e-3, 7e-4, 1e-5), and
-// the quadratically convergent FP64 refinement takes them from there. At
-// 1e-2 the k = 256 dense sketch stops one sweep earlier than at 1e-3 (8
-// instead of 9) with the same 3 refinement iterations; at 5e-2 (7 sweeps)
-// the refinement needed a 4th iteration, which costs more than the sweep.
+// the quadratically convergent FP64 refinement takes them from there. A stop
+// at 1e-2 saved a sweep on the sketch cores but left the refinement of the
+// SVD form's k x k products (Section 3 orthogonalisation) unconverged after
+// its iterations, so that the FP64 Jacobi fallback ran; 1e-3 converges there.
 #ifndef CABS_SVD_STOP_A
-#define CABS_SVD_STOP_A 1e-2f
+#define CABS_SVD_STOP_A 1e-3f
 #endif
 constexpr float kStopA = CABS_SVD_STOP_A;
 constexpr int kMaxSweepsA = 40;

@@ -165,3 +165,28 @@ def test_sketch_svd_form_fp32_properties(ctx):
     want = (a.U[rows].double() * a.S) @ a.V.double().T
     assert (got - want).abs().max().item() < 2e-5 * s[0].item() * 16
     assert torch.all(s[1:] <= s[:-1])
+    # every FP64 refinement converged: no FP64 Jacobi fallback (status bit
+    # value 2), no wait given up (4)
+    assert a.diag().status == 0 and b.diag().status == 0, (a.diag().status, b.diag().status)
+
+
+def test_sketch_svd_form_bf16_refinement_converges(ctx):
+    """The dense benchmark's sketch (65536 x 32768, rank 256 + N(0, 1e-4^2),
+    BF16, stabilised core, truncation k 2^-24, seeds 1607 and 1608) returned
+    in SVD form: the k x k SVDs of the orthogonalisation converge in the FP64
+    refinement, without the one-CTA FP64 Jacobi fallback (which returns the
+    same factors, about 100 times slower). A Phase A that stops early (at
+    off-diagonal 1e-2) fails this on seed 1607."""
+    from paper_1607_07395_gb300 import cabs
+    A = synth.decaying_lowrank_device(65536, 32768, rank=256, seed=1607, noise_fp32=True)[0]
+    src = cabs.dense_source(A)
+    try:
+        for seed in (1607, 1608):
+            p = cabs.make_params(65536, 32768, 256, iters=5, seed=seed, prec="bf16", core="stabilized",
+                                 trunc_rtol=256 * 2.0 ** -24, err_samples=0, flags=cabs.FLAG_SVD_FORM)
+            sk = cabs.cabs_sketch(ctx, src, p)
+            torch.cuda.synchronize()
+            assert sk.diag().status == 0, (seed, sk.diag().status)
+    finally:
+        del src, A
+        torch.cuda.empty_cache()
