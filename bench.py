@@ -348,6 +348,34 @@ def roofline(prof, wl, k, iters, elem_bytes, svd_sweeps, steps, peaks, prec, wor
 
 # ------------------------------------------------------------------ clocks
 
+def bind_to_gpu_local_cpus(local):
+    """Restricts this process to the CPUs that the GPU's PCI device lists as
+    local (sysfs local_cpulist), so that pinned host buffers allocated after
+    this land on the GPU's own memory node (first touch). Returns the list
+    as a string, or why it was left unbound."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return "unbound (no local CPU available to this process)"
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except Exception as e:  # noqa: BLE001 -- the measurement runs unbound
+        return f"unbound ({type(e).__name__})"
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
 
@@ -657,6 +685,8 @@ def run_cabs(args):
     # step's inputs, the sketches and their errors, D2H of factors and indices
     e2e = None
     if not args.no_e2e:
+        all_cpus = os.sched_getaffinity(0)
+        host_cpus = bind_to_gpu_local_cpus(local)
         if wl["kind"] == "rbf":
             hx = torch.from_numpy(inp["X_host"]).pin_memory()
             hy = torch.from_numpy(inp["Y_host"]).pin_memory()
@@ -691,7 +721,10 @@ def run_cabs(args):
 
         _, e2e_ms, _ = timed_steps(ctx, cabs, e2e_step, args.steps, stream, world, barrier, flush)
         e2e = dict(value=round(job_value(world, B, args.steps, e2e_ms), 4), unit="sketches/s",
-                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
+                   host_cpus=f"process bound to the GPU-local CPUs {host_cpus} before the pinned buffers were "
+                             f"allocated" if not host_cpus.startswith("unbound") else host_cpus)
+        os.sched_setaffinity(0, all_cpus)  # the CPU baseline keeps every core
 
     # ---- the plain FP32 form on the same GPU, one sketch at a time (comparison)
     plain = None
