@@ -1220,9 +1220,15 @@ __global__ void __launch_bounds__(256) refine_persistent_kernel(RefineArgs a) {
     // than 1e-13. Pairs deferred for a correction above kMaxCorrB are not
     // counted either: in FP32 data they can stay deferred with |T_ij| near
     // 1e-7, as before this check existed.
+    // For data carried in FP32 or less (resolve_rtol > 0) the factors need
+    // only reach the data's own resolution: corrections below
+    // 1e-2 sqrt(resolve_rtol) (about 1e-5 at 2^-20) leave an error of order
+    // 1e-10, four orders below it, so the update that brought them is the
+    // last; FP64 data keeps kConvB.
+    const double conv_m = a.resolve_rtol > 0.0 ? fmax(kConvB, 1e-2 * sqrt(a.resolve_rtol)) : kConvB;
     const double m = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + t));
     const double mc = __longlong_as_double((long long)*(volatile unsigned long long*)(a.maxoff + kItersB + t));
-    const bool conv = (m < kConvB || (t >= 1 && m < 1e-7 && m > 0.25 * prev)) &&
+    const bool conv = (m < conv_m || (t >= 1 && m < 1e-7 && m > 0.25 * prev)) &&
                       mc <= fmax(kCloseOffB, a.resolve_rtol) * sqrt(dmax2);
     prev = m;
     if (!grid_sync(a.bar, nb)) return;
