@@ -204,25 +204,27 @@ __global__ void __launch_bounds__(256) tc_assign_merge_kernel(const Best2* __res
 
 // Rows whose two best centres were closer than the operand rounding bound:
 // both distances again in FP32 by direct differences (one warp per row, lanes
-// over dimensions, coalesced); the smaller wins, ties to the lower index.
+// over dimensions, coalesced); the smaller wins, ties to the lower index. A
+// CTA covers 256 rows at a time: their flagged rows are gathered into a
+// shared list and dealt out to the 8 warps, so that no warp walks many
+// flagged rows one after another (each row's decision is independent).
 __global__ void __launch_bounds__(256) assign_resolve_kernel(const float* __restrict__ X, long long M, int d,
                                                              const float* __restrict__ Z, int* __restrict__ labels,
                                                              const int* __restrict__ alt, int* rechecks) {
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  __shared__ int list[256];
+  __shared__ int cnt;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int nre = 0;
-  for (long long base = warp * 32; base < M; base += nwarps * 32) {
-    const long long l = base + lane;
-    const int a2 = l < M ? alt[l] : -1;
-    unsigned mask = __ballot_sync(0xffffffffu, a2 >= 0);
-    const int lab = (mask && l < M) ? labels[l] : 0;
-    while (mask) {
-      const int b = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const long long r = base + b;
-      const int j1 = __shfl_sync(0xffffffffu, lab, b);
-      const int j2 = __shfl_sync(0xffffffffu, a2, b);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < M; base += (long long)gridDim.x * blockDim.x) {
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const long long l = base + threadIdx.x;
+    if (l < M && alt[l] >= 0) list[atomicAdd(&cnt, 1)] = threadIdx.x;
+    __syncthreads();
+    const int n = cnt;
+    for (int e = wi; e < n; e += nw) {
+      const long long r = base + list[e];
+      const int j1 = labels[r], j2 = alt[r];
       float s1 = 0.f, s2 = 0.f;
       // unrolled so that a row's loads (d <= 256: 8 per operand) are all in flight at once
 #pragma unroll 8
@@ -240,6 +242,7 @@ __global__ void __launch_bounds__(256) assign_resolve_kernel(const float* __rest
         if (s2 < s1 || (s2 == s1 && j2 < j1)) labels[r] = j2;
       }
     }
+    __syncthreads();  // the list is rebuilt for the next 256 rows
   }
   if (lane == 0 && nre && rechecks) atomicAdd(rechecks, nre);
 }
