@@ -130,10 +130,23 @@ __global__ void __launch_bounds__(tc::kThreads, 1)
         float v[32];
         tc::tmem_ld32(bars.tmem_base + (uint32_t)(ab * kBN + col0) + ((uint32_t)(sub * 32) << 16), v);
         const float xl = p0 + lane < M ? __ldg(xn + p0 + lane) : 0.f;
+        // one pass marks the values below this centre's current 8th best
+        // (a superset: the bound only falls as values enter), then only those
+        // are inserted, rows rising, each checked against the bound of the
+        // moment -- the same list as inserting every value in turn
+        float dv[32];
+        unsigned cand = 0u;
+        const float bound = bd[kTopTc - 1];
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const float xq = __shfl_sync(0xffffffffu, xl, q);
-          if (p0 + q < M) topn_insert<kTopTc>(bd, br, fmaf(-2.f, v[q], xq), (int)(p0 + q));
+          dv[q] = p0 + q < M ? fmaf(-2.f, v[q], xq) : __int_as_float(0x7f800000);
+          cand |= dv[q] < bound ? (1u << q) : 0u;
+        }
+        while (cand) {
+          const int q = __ffs(cand) - 1;
+          cand &= cand - 1u;
+          topn_insert<kTopTc>(bd, br, dv[q], (int)(p0 + q));
         }
       }
       tc::fence_before_sync();
