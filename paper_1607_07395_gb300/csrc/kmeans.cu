@@ -286,32 +286,62 @@ __global__ void __launch_bounds__(256) label_hist_kernel(const int* __restrict__
   for (int j = threadIdx.x; j < k2; j += blockDim.x) chunk_cnt[(size_t)blockIdx.x * k2 + j] = h[j];
 }
 
-// One CTA of k2 threads: chunk_off[c][j] = start of chunk c's members of
-// centre j in the sorted order; base[j], cnt[j] = centre j's range.
-__global__ void __launch_bounds__(CABS_MAX_K) label_offsets_kernel(const int* __restrict__ chunk_cnt, int chunks,
-                                                                   int k2, int* __restrict__ chunk_off,
-                                                                   int* __restrict__ base, int* __restrict__ cnt) {
-  __shared__ int tot[CABS_MAX_K];
-  const int j = threadIdx.x;
-  int t = 0;
-  if (j < k2)
-    for (int c = 0; c < chunks; ++c) t += chunk_cnt[(size_t)c * k2 + j];
-  tot[j] = j < k2 ? t : 0;
+// One CTA of 4 CABS_MAX_K threads: chunk_off[c][j] = start of chunk c's
+// members of centre j in the sorted order; base[j], cnt[j] = centre j's
+// range. Four threads per centre each take a quarter of the chunks (so the
+// count loads of one centre are spread over four threads); the centre totals
+// are scanned by warp shuffles and a scan of the warp totals.
+constexpr int kOffParts = 4;
+__global__ void __launch_bounds__(kOffParts * CABS_MAX_K) label_offsets_kernel(const int* __restrict__ chunk_cnt,
+                                                                               int chunks, int k2,
+                                                                               int* __restrict__ chunk_off,
+                                                                               int* __restrict__ base,
+                                                                               int* __restrict__ cnt) {
+  __shared__ int ptot[kOffParts][CABS_MAX_K];  // each part's count of each centre
+  __shared__ int pref[CABS_MAX_K];             // exclusive prefix of the centre totals inside their warp
+  __shared__ int wtot[CABS_MAX_K / 32];        // warp totals, then their inclusive scan
+  const int j = threadIdx.x % CABS_MAX_K, part = threadIdx.x / CABS_MAX_K;
+  const int lane = j & 31, w = j >> 5;
+  const int c0 = (int)((long long)chunks * part / kOffParts), c1 = (int)((long long)chunks * (part + 1) / kOffParts);
+  int tp = 0;
+  if (j < k2) {
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) tp += chunk_cnt[(size_t)c * k2 + j];
+  }
+  ptot[part][j] = tp;
   __syncthreads();
-  if (j == 0) {
-    int run = 0;
-    for (int i = 0; i < k2; ++i) {
-      const int v = tot[i];
-      tot[i] = run;
-      run += v;
+  int t = 0;
+  for (int q = 0; q < kOffParts; ++q) t += ptot[q][j];  // centre j's total (every part)
+  if (part == 0) {
+    int incl = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
     }
+    if (lane == 31) wtot[w] = incl;
+    pref[j] = incl - t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int x = lane < CABS_MAX_K / 32 ? wtot[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += o;
+    }
+    if (lane < CABS_MAX_K / 32) wtot[lane] = x;
   }
   __syncthreads();
   if (j < k2) {
-    int run = tot[j];
-    base[j] = run;
-    cnt[j] = t;
-    for (int c = 0; c < chunks; ++c) {
+    int run = pref[j] + (w > 0 ? wtot[w - 1] : 0);  // start of centre j
+    if (part == 0) {
+      base[j] = run;
+      cnt[j] = t;
+    }
+    for (int q = 0; q < part; ++q) run += ptot[q][j];  // the earlier parts' members of centre j
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) {
       chunk_off[(size_t)c * k2 + j] = run;
       run += chunk_cnt[(size_t)c * k2 + j];
     }
@@ -595,7 +625,7 @@ cabs_status kmeans_typed(const T* X, int64_t M, int d, const int* init_rows, int
     const int ch = sort_chunks(M);
     CABS_LAUNCH(stream, "label_hist_kernel", label_hist_kernel<<<ch, 256, 0, stream>>>(lab, M, k2, w.chunk_cnt));
     CABS_LAUNCH(stream, "label_offsets_kernel",
-                label_offsets_kernel<<<1, CABS_MAX_K, 0, stream>>>(w.chunk_cnt, ch, k2, w.chunk_off, w.lbase, w.lcnt));
+                label_offsets_kernel<<<1, kOffParts * CABS_MAX_K, 0, stream>>>(w.chunk_cnt, ch, k2, w.chunk_off, w.lbase, w.lcnt));
     CABS_LAUNCH(stream, "label_scatter_kernel",
                 label_scatter_kernel<<<ch, 32, 0, stream>>>(lab, M, k2, w.chunk_off, w.perm));
     CABS_LAUNCH(stream, "update_kernel",
