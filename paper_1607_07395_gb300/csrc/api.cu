@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -204,12 +205,39 @@ __global__ void diag_clear_kernel(cabs_diag* d) {
   for (size_t i = threadIdx.x; i < sizeof(cabs_diag) / sizeof(int); i += blockDim.x) p[i] = 0;
 }
 
+// A second stream per (device, stream) on which a sketch runs its column
+// side of step 3 (k-means and snap of Q) while the row side runs on its own
+// stream; created on first use, kept until exit. Work issued on one stream is
+// serialised, so its side stream serves one sketch at a time; the fork and
+// join are event waits, which stream capture turns into graph edges.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static cabs_status side_stream_of(cudaStream_t main, SideStream& out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, cudaStream_t>, SideStream> sides;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  SideStream& e = sides[{dev, main}];
+  if (!e.s) {
+    if (cudaStreamCreateWithFlags(&e.s, cudaStreamNonBlocking) != cudaSuccess) return check_cuda("side stream");
+    if (cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess)
+      return check_cuda("side stream events");
+  }
+  out = e;
+  return CABS_OK;
+}
+
 constexpr int kTagLevRows = 6;  // Philox tags of the leverage-score draws
 constexpr int kTagLevCols = 7;
 
 // The launch sequence of one sketch on one stream.
 cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
-                           const cabs_result& out) {
+                           const cabs_result& out, bool fork_sides) {
   Carve cv(ws, ws_bytes);
   SketchWs w = carve_sketch(cv, src, p);
   if (!cv.fits()) {
@@ -243,17 +271,38 @@ cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* w
     CABS_TRY(launch_leverage_select(w.lev_Y, n, k1, k2, f64, p.seed, kTagLevCols, out.cols, w.side_c, w.side_c_bytes,
                                     s));
   } else {
-    // step 3: weighted k-means on P and Q, snap to rows
+    // step 3: weighted k-means on P and Q, snap to rows. The two sides are
+    // independent (their own workspaces; the shared diagnostics are updated
+    // atomically): for a sketch on its own the column side runs on the side
+    // stream, forked after the pilot and joined before the follow-up gather
+    // (in a batch it stays on the lane's stream: the lanes are concurrent
+    // already, and more streams measured slower there).
+    SideStream ss;
+    ss.s = s;
+    if (fork_sides) {
+      CABS_TRY(side_stream_of(s, ss));
+      if (cudaEventRecord(ss.fork, s) != cudaSuccess || cudaStreamWaitEvent(ss.s, ss.fork, 0) != cudaSuccess)
+        return check_cuda("side stream fork");
+    }
+    CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
+                           &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, ss.s));
+    CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
+                         &dg->snap_fallbacks, &dg->status, ss.s));
+    if (p.flags & CABS_FLAG_FOLLOW_ERR)
+      CABS_TRY(launch_encoding_error(w.Q, n, k1, out.cols, k2, p.prec, p.upsilon_pow, &dg->e_follow_cols, w.side_c,
+                                     w.side_c_bytes, ss.s));
     CABS_TRY(launch_kmeans(w.P, m, k1, w.pr_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zr, dg->e_rows,
                            &dg->T_rows, &dg->rechecked, w.side_r, w.side_r_bytes, s));
-    CABS_TRY(launch_kmeans(w.Q, n, k1, w.pc_drawn, k2, p.iters, p.prec, p.upsilon_pow, nullptr, w.Zc, dg->e_cols,
-                           &dg->T_cols, &dg->rechecked, w.side_c, w.side_c_bytes, s));
     CABS_TRY(launch_snap(w.P, m, k1, w.Zr, k2, p.prec, w.fr_order, out.rows, w.side_r, w.side_r_bytes,
                          &dg->snap_fallbacks, &dg->status, s));
-    CABS_TRY(launch_snap(w.Q, n, k1, w.Zc, k2, p.prec, w.fc_order, out.cols, w.side_c, w.side_c_bytes,
-                         &dg->snap_fallbacks, &dg->status, s));
+    if (p.flags & CABS_FLAG_FOLLOW_ERR)
+      CABS_TRY(launch_encoding_error(w.P, m, k1, out.rows, k2, p.prec, p.upsilon_pow, &dg->e_follow_rows, w.side_r,
+                                     w.side_r_bytes, s));
+    if (fork_sides &&
+        (cudaEventRecord(ss.join, ss.s) != cudaSuccess || cudaStreamWaitEvent(s, ss.join, 0) != cudaSuccess))
+      return check_cuda("side stream join");
   }
-  if (p.flags & CABS_FLAG_FOLLOW_ERR) {
+  if ((p.flags & CABS_FLAG_FOLLOW_ERR) && (p.flags & (CABS_FLAG_HARD_THRESHOLD | CABS_FLAG_LEVERAGE))) {
     CABS_TRY(launch_encoding_error(w.P, m, k1, out.rows, k2, p.prec, p.upsilon_pow, &dg->e_follow_rows, w.side_r,
                                    w.side_r_bytes, s));
     CABS_TRY(launch_encoding_error(w.Q, n, k1, out.cols, k2, p.prec, p.upsilon_pow, &dg->e_follow_cols, w.side_c,
@@ -665,7 +714,7 @@ cabs_status batched_enqueue(cabs_ctx* ctx, int count, const cabs_source* src, co
     const int i = order[t];
     const size_t need = sketch_ws_bytes(src[i], p[i]);
     TuneScope shape(tune_lookup(ctx, p[i]));
-    CABS_TRY(sketch_enqueue(src[i], p[i], (char*)ws + off[i], need, ctx->lanes[t % lanes], out[i]));
+    CABS_TRY(sketch_enqueue(src[i], p[i], (char*)ws + off[i], need, ctx->lanes[t % lanes], out[i], false));
   }
   for (int l = 0; l < lanes; ++l) {
     if (cudaEventRecord(ctx->lane_events[l], ctx->lanes[l]) != cudaSuccess) return check_cuda("join record");

@@ -49,8 +49,10 @@ cabs_status validate_error_request(const cabs_source* src, const cabs_params* p,
 cabs_status validate_source(const cabs_source* src, int64_t m, int64_t n);
 cabs_status validate_params(const cabs_params* p);
 cabs_status validate_result(const cabs_result* out);
+// fork_sides: run the column side of step 3 on a second stream (a sketch on
+// its own; a batch's lanes already run sketches side by side)
 cabs_status sketch_enqueue(const cabs_source& src, const cabs_params& p, void* ws, size_t ws_bytes, cudaStream_t s,
-                           const cabs_result& out);
+                           const cabs_result& out, bool fork_sides = true);
 // Batched form: members largest first over `lanes` internal streams forked
 // from and joined back to s (each member under its bucket's launch shape).
 cabs_status ensure_lanes(cabs_ctx* ctx, int lanes);

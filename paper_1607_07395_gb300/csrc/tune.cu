@@ -170,11 +170,11 @@ double time_member(const cabs_source& src, const cabs_params& p, void* ws, const
   TuneScope ts(t);
   SharersScope alone(1);
   const size_t need = sketch_ws_bytes(src, p);
-  if (sketch_enqueue(src, p, ws, need, s, out) != CABS_OK) return -1.0;
+  if (sketch_enqueue(src, p, ws, need, s, out, false) != CABS_OK) return -1.0;
   double best = 1e300;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(tm.a, s);
-    if (sketch_enqueue(src, p, ws, need, s, out) != CABS_OK) return -1.0;
+    if (sketch_enqueue(src, p, ws, need, s, out, false) != CABS_OK) return -1.0;
     cudaEventRecord(tm.b, s);
     if (cudaEventSynchronize(tm.b) != cudaSuccess) return -1.0;
     float ms = 0.f;
