@@ -250,6 +250,28 @@ def test_snap_fallback_when_candidates_taken(ctx, C):
         assert len(set(to_np(order).tolist())) == Z.shape[0]
 
 
+@pytest.mark.parametrize("M", [131072, 131073, 150000])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_snap_taken_set_both_forms(ctx, C, M, prec):
+    """The greedy walk keeps the rows taken so far as a bitmap in shared
+    memory up to 131072 rows and as an open-addressing set beyond: both forms
+    give the oracle's picks (Section 3.2), with repeated centres so that lists
+    run out (full scans) and later centres meet rows taken before them."""
+    g = np.random.default_rng(M)
+    X = g.standard_normal((M, 8))
+    base = X[g.choice(M, 6, replace=False)]
+    Z = np.concatenate([np.repeat(base[:2], [11, 9], axis=0), base[2:] + 0.01 * g.standard_normal((4, 8)),
+                        g.standard_normal((10, 8))])
+    dt = np.float64 if prec == "fp64" else np.float32
+    Xd, Zd = dev(X.astype(dt)), dev(Z.astype(dt))
+    order, srt = C.cabs_snap(ctx, Xd, Zd, prec=prec)
+    want_o, want_s = o.snap(X.astype(dt).astype(np.float64), Z.astype(dt).astype(np.float64),
+                            tie_rtol=o.SNAP_TIE_RTOL if prec == "fp64" else 2.0 ** -16)
+    assert to_np(order).tolist() == want_o.tolist()
+    assert to_np(srt).tolist() == want_s.tolist()
+    assert len(set(to_np(order).tolist())) == Z.shape[0]
+
+
 # ------------------------------------------------------- whole sketch (a1-a8)
 
 def _run(ctx, C, src_np, src_dev, m, n, k, iters, seed, prec, mode):
