@@ -136,15 +136,16 @@ def test_tc_snap_fallback_when_candidates_taken(ctx, C, prec):
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32"])
 @pytest.mark.parametrize("m,n,k,core", [(1000, 700, 256, "pinv"), (777, 1333, 200, "stabilized"),
-                                        (300, 129, 65, "pinv"), (5000, 257, 33, "stabilized"), (130, 300, 8, "pinv")])
+                                        (300, 129, 65, "pinv"), (5000, 257, 33, "stabilized"), (130, 300, 8, "pinv"),
+                                        (100, 90, 40, "pinv")])
 def test_tc_extrapolation_matches_fp64(ctx, C, prec, m, n, k, core):
     """The extrapolation products a = C V_w, b = R^T U_w of the sketching
     routine (Section 4.1) on the tensor cores (three TF32 products, BF16 and
     TF32 modes): U = a N_c^-1, V = b N_r^-1 and S against the same products
     in FP64 from the GPU's own V_w, U_w, to 2e-5 per column (the FP32
     CUDA-core path is held to the same bar). Row counts are not multiples of
-    the 128-row tile, and k = 65, 33 exercise widths that are not multiples
-    of 4."""
+    the 128-row tile (100 and 90 fill less than one), and k = 65, 33 exercise
+    widths that are not multiples of 4."""
     g = np.random.default_rng(m + n + k)
     Cm = (g.standard_normal((m, k)) * g.uniform(0.1, 10.0, size=k)).astype(np.float32)
     Rt = (g.standard_normal((n, k)) * g.uniform(0.1, 10.0, size=k)).astype(np.float32)
