@@ -38,17 +38,39 @@ struct AsgCfg {
 };
 
 template <bool kTF32>
+// Eight consecutive operand entries of one row per thread (Kp is a multiple
+// of 32, so a group never straddles rows): two 16-byte loads when d is a
+// multiple of 4 and the group lies inside the row, and one 16-byte (BF16) or
+// two (TF32) stores; entries at or beyond d are zero.
 __global__ void to_operand_kernel(const float* __restrict__ X, long long rows, int d, int Kp, void* __restrict__ out) {
-  const long long total = rows * Kp;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / Kp;
-    const int q = (int)(e - r * Kp);
-    const float v = q < d ? X[r * d + q] : 0.f;
-    if constexpr (kTF32)
-      ((float*)out)[e] = v;
-    else
-      ((__nv_bfloat16*)out)[e] = __float2bfloat16_rn(v);
+  const long long groups = rows * (Kp / 8);
+  const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
+       gi += (long long)gridDim.x * blockDim.x) {
+    const long long e0 = gi * 8;
+    const long long r = e0 / Kp;
+    const int q0 = (int)(e0 - r * Kp);
+    const float* src = X + r * d + q0;
+    float v[8];
+    if (vec && q0 + 8 <= d) {
+      const float4 a = *reinterpret_cast<const float4*>(src);
+      const float4 b = *reinterpret_cast<const float4*>(src + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = q0 + i < d ? src[i] : 0.f;
+    }
+    if constexpr (kTF32) {
+      float4* o = reinterpret_cast<float4*>((float*)out + e0);
+      o[0] = make_float4(v[0], v[1], v[2], v[3]);
+      o[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn(v[i]);
+      *reinterpret_cast<uint4*>((__nv_bfloat16*)out + e0) = *reinterpret_cast<const uint4*>(h);
+    }
   }
 }
 
@@ -310,10 +332,10 @@ cabs_status tc_assign_typed(const float* X, int64_t M, int d, const float* Z, co
   const int sms = sm_count();
   if (prep_points)
     CABS_LAUNCH(stream, "tc_assign_points_prep",
-                to_operand_kernel<kTF32><<<std::max(1, std::min(ceil_div(M * Kp, 256), sms * 8)), 256, 0, stream>>>(
+                to_operand_kernel<kTF32><<<std::max(1, std::min(ceil_div(M * Kp / 8, 256), sms * 8)), 256, 0, stream>>>(
                     X, M, d, Kp, t.Pp));
   CABS_LAUNCH(stream, "tc_assign_centres_prep",
-              to_operand_kernel<kTF32><<<std::max(1, ceil_div((int64_t)kBN * Kp, 256)), 256, 0, stream>>>(
+              to_operand_kernel<kTF32><<<std::max(1, ceil_div((int64_t)kBN * Kp / 8, 256)), 256, 0, stream>>>(
                   Z, k2, d, Kp, t.Zp));
   if (cudaMemsetAsync(t.err, 0, sizeof(int), stream) != cudaSuccess) return check_cuda("tc_assign err clear");
   CUtensorMap tmA, tmB;
@@ -337,7 +359,7 @@ int tc_kp_of(int d, bool tf32) { return kp_of(d, tf32); }
 
 cabs_status tc_to_operand(const float* X, int64_t rows, int d, int Kp, bool tf32, void* out, const char* name,
                           cudaStream_t stream) {
-  const int blocks = std::max(1, std::min(ceil_div(rows * Kp, 256), sm_count() * 8));
+  const int blocks = std::max(1, std::min(ceil_div(rows * Kp / 8, 256), sm_count() * 8));
   if (tf32)
     CABS_LAUNCH(stream, name, to_operand_kernel<true><<<blocks, 256, 0, stream>>>(X, rows, d, Kp, out));
   else
