@@ -238,46 +238,68 @@ __device__ __forceinline__ void store_col(float* x, int lane, const float* xr) {
   for (int i = 0; i < R / 4; ++i) x4[lane + 32 * i] = make_float4(xr[4 * i], xr[4 * i + 1], xr[4 * i + 2], xr[4 * i + 3]);
 }
 
-// The rotation of rotate_pair_reg with column x held in registers (xr) and
-// column y in shared memory; V is left alone and (c, s) is recorded in *cs
-// ((1, 0) when the pair is already orthogonal to the tolerance). The squared
-// norms travel with the columns -- a in a register, b in shared memory at
-// *bn -- and are updated by the exact identities |c x - s y|^2 =
-// c^2 a - 2 c s g + s^2 b and |s x + c y|^2 = s^2 a + 2 c s g + c^2 b, so a
-// step reduces only the inner product g across the warp. They are
-// recomputed from the columns at the start of every round.
-template <int R>
-__device__ __forceinline__ int rotate_top_reg(float* xr, float& a, float* y, float* bn, int lane, float2* cs) {
-  float yr[R];
-  load_col<R>(y, lane, yr);
-  // every lane reads b before the shuffles below, which lane 0 must pass
-  // before it overwrites *bn
-  const float b = *bn;
-  float g = 0.f;
-#pragma unroll
-  for (int i = 0; i < R; ++i) g = fmaf(xr[i], yr[i], g);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
-  float c, s;
-  const int code = jacobi_cs(a, b, g, c, s);
-  if (!code) {
-    if (lane == 0) *cs = make_float2(1.f, 0.f);
-    return 0;
+// One step of a block round for a warp. kW: the rotation of rotate_pair_reg
+// with column x held in registers (xr) and column y in shared memory, (c, s)
+// recorded in *cs_out ((1, 0) when the pair is already orthogonal to the
+// tolerance). The squared norms travel with the columns -- a in a register,
+// b in shared memory at *bn -- and are updated by the exact identities
+// |c x - s y|^2 = c^2 a - 2 c s g + s^2 b and |s x + c y|^2 = s^2 a + 2 c s g
+// + c^2 b, so a step reduces only the inner product g across the warp (they
+// are recomputed from the columns at the start of every round). kV: the V
+// columns (vx, vy) take the rotation recorded one step earlier (*cs_prev).
+// Both sit in one branch-free block, so that the V columns' loads, rotation
+// and stores fill the latency of the warp sum; a pair below the threshold
+// gets c = 1, s = 0, which leaves columns and norms as they are.
+template <int R, bool kW, bool kV>
+__device__ __forceinline__ int rotate_step(float* xr, float& a, float* y, float* bn, float2* cs_out, float* vx,
+                                           float* vy, const float2* cs_prev, int lane) {
+  float pr[R], qr[R], yr[R];
+  float2 cp = make_float2(1.f, 0.f);
+  if constexpr (kV) {
+    cp = *cs_prev;
+    load_col<R>(vx, lane, pr);
+    load_col<R>(vy, lane, qr);
   }
+  float b = 0.f, g = 0.f;
+  if constexpr (kW) {
+    load_col<R>(y, lane, yr);
+    // every lane reads b before the shuffles below, which lane 0 must pass
+    // before it overwrites *bn
+    b = *bn;
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const float u = xr[i], v = yr[i];
-    xr[i] = c * u - s * v;
-    yr[i] = s * u + c * v;
+    for (int i = 0; i < R; ++i) g = fmaf(xr[i], yr[i], g);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
   }
-  store_col<R>(y, lane, yr);
-  const float cc = c * c, ss = s * s, cs2 = 2.f * c * s * g;
-  const float a2 = cc * a - cs2 + ss * b;
-  if (lane == 0) {
-    *bn = ss * a + cs2 + cc * b;
-    *cs = make_float2(c, s);
+  if constexpr (kV) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const float p = pr[i], q = qr[i];
+      pr[i] = cp.x * p - cp.y * q;
+      qr[i] = cp.y * p + cp.x * q;
+    }
+    store_col<R>(vx, lane, pr);
+    store_col<R>(vy, lane, qr);
   }
-  a = a2;
+  int code = 0;
+  if constexpr (kW) {
+    float c, s;
+    code = jacobi_cs(a, b, g, c, s);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const float u = xr[i], v = yr[i];
+      xr[i] = c * u - s * v;
+      yr[i] = s * u + c * v;
+    }
+    store_col<R>(y, lane, yr);
+    const float cc = c * c, ss = s * s, cs2 = 2.f * c * s * g;
+    const float a2 = cc * a - cs2 + ss * b;
+    if (lane == 0) {
+      *bn = ss * a + cs2 + cc * b;
+      *cs_out = make_float2(c, s);
+    }
+    a = a2;
+  }
   return code;
 }
 
@@ -290,23 +312,6 @@ __device__ __forceinline__ float col_sq(const float* xr) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
   return a;
-}
-
-// V columns (vx, vy) <- the rotation recorded for their W columns.
-template <int R>
-__device__ __forceinline__ void apply_rot_v(float* vx, float* vy, int lane, float2 cs) {
-  if (cs.y == 0.f) return;
-  float pr[R], qr[R];
-  load_col<R>(vx, lane, pr);
-  load_col<R>(vy, lane, qr);
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const float p = pr[i], q = qr[i];
-    pr[i] = cs.x * p - cs.y * q;
-    qr[i] = cs.y * p + cs.x * q;
-  }
-  store_col<R>(vx, lane, pr);
-  store_col<R>(vy, lane, qr);
 }
 
 // Writes U0 (normalised columns) and V0 in FP64, column-major k x k.
@@ -738,17 +743,28 @@ __global__ void __launch_bounds__(kClusterThreads, 1) svd32_cluster_kernel(const
           if (lane == 0) bnorm[warp] = bq;  // read in step 0 by this warp only
           __syncwarp();
         }
-        for (int s = 0; s <= b; ++s) {
-          if (warp < b && s < b) {
+        // step 0: W only; steps 1 .. b - 1: W and the previous step's V;
+        // step b: V only
+        if (warp < b)
+          my_rot |= rotate_step<R, true, false>(xr, an, Wb + (size_t)warp * kp, &bnorm[warp], &rot_cs[0][warp],
+                                                nullptr, nullptr, nullptr, lane);
+        __syncthreads();
+        for (int s = 1; s < b; ++s) {
+          if (warp < b) {
             const int q = warp + s - (warp + s >= b ? b : 0);  // (warp + s) mod b, both < b
-            my_rot |= rotate_top_reg<R>(xr, an, Wb + (size_t)q * kp, &bnorm[q], lane, &rot_cs[s][warp]);
-          }
-          if (s >= 1 && warp < b) {
-            const int q = warp + s - 1 - (warp + s - 1 >= b ? b : 0);
-            apply_rot_v<R>(Vt + (size_t)warp * kp, Vb + (size_t)q * kp, lane, rot_cs[s - 1][warp]);
+            const int qv = q == 0 ? b - 1 : q - 1;             // (warp + s - 1) mod b
+            my_rot |= rotate_step<R, true, true>(xr, an, Wb + (size_t)q * kp, &bnorm[q], &rot_cs[s][warp],
+                                                 Vt + (size_t)warp * kp, Vb + (size_t)qv * kp, &rot_cs[s - 1][warp],
+                                                 lane);
           }
           __syncthreads();
         }
+        if (warp < b) {
+          const int qv = warp == 0 ? b - 1 : warp - 1;  // (warp + b - 1) mod b
+          rotate_step<R, false, true>(xr, an, nullptr, nullptr, nullptr, Vt + (size_t)warp * kp, Vb + (size_t)qv * kp,
+                                      &rot_cs[b - 1][warp], lane);
+        }
+        __syncthreads();
         if (warp < b) store_col<R>(Wt + (size_t)warp * kp, lane, xr);
         __syncthreads();
       }
