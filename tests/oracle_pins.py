@@ -558,3 +558,73 @@ def pin_error_closed_form(err_fn):
     V = np.array([[1.0], [0.0]])
     assert abs(err_fn(A, U, np.array([1.0]), V) - 1 / math.sqrt(2)) < 1e-15
     assert err_fn(A, np.eye(2), np.ones(2), np.eye(2)) == 0.0
+
+
+def pin_sampled_error_closed_form(err_fn, source_cls):
+    """The sampled error on a case computed by hand: A = u v^T with distinct
+    entries, approximated by U S V^T = A / 2 (U = u/|u|, V = v/|v|,
+    S = |u||v| / 2). Every entry then has a - a_hat = a / 2, so the error is
+    1/2 whatever entries are drawn; with S = |u||v| it is 0."""
+    u = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    v = np.array([1.0, -2.0, 0.5, 3.0, 7.0])
+    src = source_cls(np.outer(u, v))
+    U = (u / np.linalg.norm(u))[:, None]
+    V = (v / np.linalg.norm(v))[:, None]
+    S = np.array([np.linalg.norm(u) * np.linalg.norm(v) / 2])
+    assert abs(err_fn(src, U, S, V, 5, 400) - 0.5) < 1e-14
+    assert err_fn(src, U, 2 * S, V, 5, 400) < 1e-14
+
+
+# ---------------------------------------------------------------- RBF entries
+
+def pin_rbf_closed_forms(entries_fn):
+    """exp(-|x - y|^2 / (2 sigma^2)) at points chosen by hand: x = y gives 1;
+    sigma = 1 with |x - y|^2 = 2 gives exp(-1), with |x - y|^2 = 4 (an L1
+    distance of 2) exp(-2); sigma = 2 with |x - y|^2 = 8 gives exp(-1)."""
+    X = np.array([[0.0, 0.0], [1.0, 1.0]], dtype=np.float32)
+    Y = np.array([[0.0, 0.0], [0.0, 2.0]], dtype=np.float32)
+    v = entries_fn(X, Y, 1.0, [0, 1, 0], [0, 0, 1])
+    assert v[0] == 1.0 and abs(v[1] - np.exp(-1.0)) < 1e-16 and abs(v[2] - np.exp(-2.0)) < 1e-16
+    w = entries_fn(np.array([[2.0, 2.0]], dtype=np.float32), np.zeros((1, 2), dtype=np.float32), 2.0, [0], [0])
+    assert abs(w[0] - np.exp(-1.0)) < 1e-16
+
+
+def pin_rbf_block_and_gather(block_fn, gather_fn, entries_fn, m=9, n=7, d=3, seed=31):
+    """Every generated entry is the kernel of its own pair: block[a, b] =
+    entry(rows[a], cols[b]); the gather's C = A[:, cols], R^T = A[rows, :]^T
+    and W = A[rows, cols] of the same implicit matrix."""
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((m, d)).astype(np.float32)
+    Y = g.standard_normal((n, d)).astype(np.float32)
+    sigma = 1.3
+    rows, cols = np.array([8, 0, 5]), np.array([6, 2])
+    def A(ii, jj):
+        I, J = np.meshgrid(ii, jj, indexing="ij")
+        return entries_fn(X, Y, sigma, I.ravel(), J.ravel()).reshape(I.shape)
+    assert np.allclose(block_fn(X, Y, sigma, rows, cols), A(rows, cols), rtol=1e-15, atol=0)
+    C, Rt, W = gather_fn(X, Y, sigma, rows, cols)
+    assert np.allclose(C, A(np.arange(m), cols), rtol=1e-15, atol=0)
+    assert np.allclose(Rt, A(rows, np.arange(n)).T, rtol=1e-15, atol=0)
+    assert np.allclose(W, A(rows, cols), rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------- weights, encoding error
+
+def pin_upsilon_weights(ups_fn):
+    """Upsilon(|x|) = |x|^p on rows of norm 5 and 0: p = 1 gives 5 and 0, p = 2
+    gives 25 and 0, p = 0 gives 1 for both (0^0 = 1)."""
+    X = np.array([[3.0, 4.0], [0.0, 0.0]])
+    assert ups_fn(X, 1.0).tolist() == [5.0, 0.0]
+    assert ups_fn(X, 2.0).tolist() == [25.0, 0.0]
+    assert ups_fn(X, 0.0).tolist() == [1.0, 1.0]
+
+
+def pin_encoding_error_closed_form(enc_fn):
+    """Points 0, 1, 3, 10 on a line with representatives rows 0 and 3 (the
+    points 0 and 10): nearest squared distances 0, 1, 9, 0, labels 0, 0, 0, 1,
+    largest cluster 3; the unweighted error is 10, and with Upsilon(t) = t
+    (weights 0, 1, 3, 10) it is 1 + 27 = 28."""
+    X = np.array([[0.0], [1.0], [3.0], [10.0]])
+    err, lab, T = enc_fn(X, [0, 3], 0.0)
+    assert err == 10.0 and lab.tolist() == [0, 0, 0, 1] and T == 3
+    assert enc_fn(X, [0, 3], 1.0)[0] == 28.0

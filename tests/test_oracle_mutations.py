@@ -211,3 +211,75 @@ LEV_MUTANTS = [
 def test_leverage_mutants_rejected(old, new):
     bad = mutate(o.leverage_scores, old, new)
     assert rejects(lambda: pins.pin_leverage_scores(bad, o.orthogonalize))
+
+
+RBF_ENTRY_MUTANTS = [
+    ("return np.exp(-d2 / (2.0 * s * s))", "return np.exp(-d2 / (s * s))"),       # sigma^2 for 2 sigma^2
+    ("return np.exp(-d2 / (2.0 * s * s))", "return np.exp(-d2 / (2.0 * s))"),     # sigma for sigma^2
+    ("d2 = ((x - y) ** 2).sum(axis=-1)", "d2 = np.abs(x - y).sum(axis=-1)"),      # L1 distance
+]
+
+
+@pytest.mark.parametrize("old,new", RBF_ENTRY_MUTANTS)
+def test_rbf_entry_mutants_rejected(old, new):
+    bad = mutate(o.rbf_entries, old, new)
+    assert rejects(lambda: pins.pin_rbf_closed_forms(bad))
+
+
+RBF_BLOCK = "out[:, t] = np.exp(-((x - y[t]) ** 2).sum(axis=1) / (2.0 * s * s))"
+RBF_GATHER_MUTANTS = [
+    ("C = rbf_block(X, Y, sigma, np.arange(m), cols)", "C = rbf_block(X, Y, sigma, np.arange(m), rows)"),
+    ("Rt = rbf_block(X, Y, sigma, rows, np.arange(n)).T.copy()",
+     "Rt = rbf_block(X, Y, sigma, cols, np.arange(n)).T.copy()"),
+    ("W = rbf_block(X, Y, sigma, rows, cols)", "W = rbf_block(X, Y, sigma, rows, cols[::-1])"),
+]
+
+
+@pytest.mark.parametrize("old,new", [(RBF_BLOCK, RBF_BLOCK.replace("2.0 * s * s", "s * s")),
+                                     (RBF_BLOCK, RBF_BLOCK.replace("y[t]", "y[0]"))])
+def test_rbf_block_mutants_rejected(old, new):
+    bad = mutate(o.rbf_block, old, new)
+    assert rejects(lambda: pins.pin_rbf_block_and_gather(bad, o.gather_rbf, o.rbf_entries))
+
+
+@pytest.mark.parametrize("old,new", RBF_GATHER_MUTANTS)
+def test_rbf_gather_mutants_rejected(old, new):
+    bad = mutate(o.gather_rbf, old, new)
+    assert rejects(lambda: pins.pin_rbf_block_and_gather(o.rbf_block, bad, o.rbf_entries))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("nrm = np.sqrt((X * X).sum(axis=1))", "nrm = (X * X).sum(axis=1)"),          # squared norm
+    ("nrm = np.sqrt((X * X).sum(axis=1))", "nrm = np.sqrt((X * X).sum(axis=0))"),  # column norms
+    ("return nrm ** p", "return nrm ** (p / 2)"),
+])
+def test_upsilon_mutants_rejected(old, new):
+    bad = mutate(o.upsilon_weights, old, new)
+    assert rejects(lambda: pins.pin_upsilon_weights(bad))
+
+
+ENC_ERR = "err = float((w * D[np.arange(X.shape[0]), s]).sum())"
+
+
+@pytest.mark.parametrize("old,new", [
+    (ENC_ERR, ENC_ERR.replace("w * ", "")),                                       # weights dropped
+    ("s = np.argmin(D, axis=1)", "s = np.argmax(D, axis=1)"),                     # farthest representative
+    ("T = int(np.bincount(s, minlength=Z.shape[0]).max())", "T = int(np.bincount(s, minlength=Z.shape[0]).min())"),
+])
+def test_encoding_error_mutants_rejected(old, new):
+    bad = mutate(o.encoding_error, old, new)
+    assert rejects(lambda: pins.pin_encoding_error_closed_form(bad))
+
+
+SAMPLED_US = "US = np.asarray(U, dtype=np.float64) * np.asarray(S, dtype=np.float64)[None, :]"
+SAMPLED_AHAT = "ahat = (US[ii] * np.asarray(V, dtype=np.float64)[jj]).sum(axis=1)"
+
+
+@pytest.mark.parametrize("old,new", [
+    ("return math.sqrt(num / den) if den > 0 else 0.0", "return num / den if den > 0 else 0.0"),  # no square root
+    (SAMPLED_US, "US = np.asarray(U, dtype=np.float64)"),                                          # S dropped
+    (SAMPLED_AHAT, SAMPLED_AHAT.replace("[jj]", "[ii]")),                                          # wrong index
+])
+def test_sampled_error_mutants_rejected(old, new):
+    bad = mutate(o.rel_fro_error_sampled, old, new)
+    assert rejects(lambda: pins.pin_sampled_error_closed_form(bad, o.DenseSource))

@@ -58,11 +58,23 @@ def test_gather_intersection_invariant():
 
 
 def test_rbf_entry_closed_forms():
-    X = np.array([[0.0, 0.0], [1.0, 1.0]], dtype=np.float32)
-    Y = np.array([[0.0, 0.0], [0.0, 2.0]], dtype=np.float32)
-    # |x - y|^2 = 2 sigma^2 -> exp(-1); x = y -> 1
-    v = o.rbf_entries(X, Y, 1.0, [0, 1, 0], [0, 0, 1])
-    assert v[0] == 1.0 and abs(v[1] - np.exp(-1.0)) < 1e-16 and abs(v[2] - np.exp(-2.0)) < 1e-16
+    pins.pin_rbf_closed_forms(o.rbf_entries)
+
+
+def test_rbf_block_and_gather_match_entries():
+    pins.pin_rbf_block_and_gather(o.rbf_block, o.gather_rbf, o.rbf_entries)
+
+
+def test_upsilon_weights_closed_form():
+    pins.pin_upsilon_weights(o.upsilon_weights)
+
+
+def test_encoding_error_closed_form():
+    pins.pin_encoding_error_closed_form(o.encoding_error)
+
+
+def test_sampled_error_closed_form():
+    pins.pin_sampled_error_closed_form(o.rel_fro_error_sampled, o.DenseSource)
 
 
 def test_pinv_exact_recovery_rank_k():
