@@ -628,3 +628,40 @@ def pin_encoding_error_closed_form(enc_fn):
     err, lab, T = enc_fn(X, [0, 3], 0.0)
     assert err == 10.0 and lab.tolist() == [0, 0, 0, 1] and T == 3
     assert enc_fn(X, [0, 3], 1.0)[0] == 28.0
+
+
+# ------------------------------------------------------- the Algorithm 2 driver
+
+def pin_follow_up_improves_encoding(cabs_fn, source_cls, trials=20):
+    """Step 3 of Algorithm 2 moves the representatives from the pilot draw to
+    the snapped k-means centres, which lowers the weighted encoding error of
+    both embeddings (the premise of Theorem 2, e_f < e_p) on at least 95 % of
+    seeds of a decaying-spectrum matrix (strictly: the k-means iterations
+    move the centres)."""
+    A, _, _, _ = synth.decaying_lowrank_host(300, 240, rank=40, decay=10, noise_std=1e-4,
+                                             seed=3, dtype=np.float64)
+    src = source_cls(A)
+    ok = 0
+    for seed in range(trials):
+        r = cabs_fn(src, 16, iters=5, seed=seed, mode="stabilized")
+        ok += (r.e_follow[0] < r.e_pilot[0]) and (r.e_follow[1] < r.e_pilot[1])
+    assert ok >= 0.95 * trials
+
+
+def pin_driver_wiring(cabs_fn, source_cls, sketch_fn, embed_fn, kmeans_fn, snap_fn):
+    """Algorithm 2 composes its steps in order: P = U S^(1/2), Q = V S^(1/2) of
+    the pilot sketch (step 2); k-means on P and Q from the first k2 pilot
+    draws, snapped (step 3); the final sketch is the sketching routine on the
+    gather at the snapped indices (step 4), which here differ from the pilot
+    ones."""
+    A = synth.plain_lowrank(120, 90, 6)
+    src = source_cls(A)
+    r = cabs_fn(src, 10, k2=7, iters=3, seed=5, mode="stabilized")
+    assert np.array_equal(r.P, embed_fn(r.pilot.U, r.pilot.S))
+    assert np.array_equal(r.Q, embed_fn(r.pilot.V, r.pilot.S))
+    km_r = kmeans_fn(r.P, r.pilot_rows_drawn[:7], 3)
+    km_c = kmeans_fn(r.Q, r.pilot_cols_drawn[:7], 3)
+    assert np.array_equal(r.rows, snap_fn(r.P, km_r.Z)[1]) and np.array_equal(r.cols, snap_fn(r.Q, km_c.Z)[1])
+    assert not (np.array_equal(r.rows, r.pilot_rows[:7]) and np.array_equal(r.cols, r.pilot_cols[:7]))
+    f = sketch_fn(*src.gather(r.rows, r.cols), 120, 90, "stabilized")
+    assert np.array_equal(r.final.U, f.U) and np.array_equal(r.final.S, f.S) and np.array_equal(r.final.V, f.V)

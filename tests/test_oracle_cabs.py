@@ -4,6 +4,7 @@ import math
 import numpy as np
 
 from oracle import cabs_ref as o
+from tests import oracle_pins as pins
 from workloads import synth
 
 
@@ -39,16 +40,12 @@ def test_cabs_init_uses_pilot_rows_in_draw_order():
 
 
 def test_follow_up_encoding_error_drops():
-    """e_f <= e_p (the premise of Theorem 2) on at least 95% of seeds."""
-    A, _, _, _ = synth.decaying_lowrank_host(300, 240, rank=40, decay=10, noise_std=1e-4,
-                                             seed=3, dtype=np.float64)
-    src = o.DenseSource(A)
-    ok = 0
-    trials = 20
-    for seed in range(trials):
-        r = o.cabs(src, 16, iters=5, seed=seed, mode="stabilized")
-        ok += (r.e_follow[0] <= r.e_pilot[0]) and (r.e_follow[1] <= r.e_pilot[1])
-    assert ok >= 0.95 * trials
+    """e_f < e_p (the premise of Theorem 2) on at least 95% of seeds."""
+    pins.pin_follow_up_improves_encoding(o.cabs, o.DenseSource)
+
+
+def test_driver_composes_the_steps_in_order():
+    pins.pin_driver_wiring(o.cabs, o.DenseSource, o.sketching, o.embed, o.weighted_kmeans, o.snap)
 
 
 def test_sampled_error_within_three_standard_errors():

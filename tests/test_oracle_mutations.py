@@ -283,3 +283,20 @@ SAMPLED_AHAT = "ahat = (US[ii] * np.asarray(V, dtype=np.float64)[jj]).sum(axis=1
 def test_sampled_error_mutants_rejected(old, new):
     bad = mutate(o.rel_fro_error_sampled, old, new)
     assert rejects(lambda: pins.pin_sampled_error_closed_form(bad, o.DenseSource))
+
+
+DRIVER_MUTANTS = [
+    ("Cb, Rtb, Wb = source.gather(rows, cols)", "Cb, Rtb, Wb = source.gather(Ir, Ic)"),            # no follow-up gather
+    ("rows_o, rows = snap(P, km_r.Z)", "rows_o, rows = snap(P, km_r.centres[0])"),                 # k-means skipped
+    ("P = embed(pilot.U, pilot.S)", "P = pilot.U"),                                                # no embedding
+    ("km_c = weighted_kmeans(Q, Ic_drawn[:k2], iters, upsilon_pow)",
+     "km_c = weighted_kmeans(Q, Ic[:k2], iters, upsilon_pow)"),                                   # sorted, not drawn
+]
+
+
+@pytest.mark.parametrize("old,new", DRIVER_MUTANTS)
+def test_driver_mutants_rejected(old, new):
+    bad = mutate(o.cabs, old, new)
+    checks = [lambda: pins.pin_driver_wiring(bad, o.DenseSource, o.sketching, o.embed, o.weighted_kmeans, o.snap),
+              lambda: pins.pin_follow_up_improves_encoding(bad, o.DenseSource, trials=4)]
+    assert any(rejects(c) for c in checks)
