@@ -346,10 +346,13 @@ cabs_status cabs_gather(cabs_ctx* ctx, const cabs_source* src, int64_t m, int64_
                         int32_t prec, void* C, void* Rt, double* W, cabs_stream stream);
 
 /* Steps a3 / a4 / a8, Section 4.1 (sketching routine) and Algorithm 2 step 2.
- * FP64 one-sided Jacobi SVD W = U_w Sigma_w V_w^T (k x k, k = k_r = k_c),
- * truncation to sigma_i > max(trunc_rtol, k 2^-52) sigma_1, extrapolation
- * a = C V_w (m x k), b = Rt U_w (n x k), column norms N_c, N_r, scale S
- * (per cabs_core), then
+ * SVD W = U_w Sigma_w V_w^T (k x k, k = k_r = k_c) to FP64 accuracy in every
+ * mode (an FP32 one-sided Jacobi refined in FP64; an FP64 Jacobi when the
+ * refinement does not converge), truncation to
+ * sigma_i > max(trunc_rtol, k 2^-52) sigma_1, extrapolation a = C V_w
+ * (m x k), b = Rt U_w (n x k) -- FP64 in the FP64 mode, FP32 in the FP32
+ * mode, three TF32 tensor-core products with FP32 accumulation in the TF32
+ * and BF16 modes -- column norms N_c, N_r, scale S (per cabs_core), then
  *   embed == 0: out1 = U = a N_c^-1, out2 = V = b N_r^-1       (factors)
  *   embed != 0: out1 = P = U S^1/2,  out2 = Q = V S^1/2        (embeddings)
  * out1 (m x k) and out2 (n x k) are elem, ld k; S (k, FP64); columns and S
