@@ -248,9 +248,10 @@ cabs_status cabs_sketch_batched(cabs_ctx* ctx, int32_t count, const cabs_source*
  * serving loop use for every sketch of that bucket; buckets without an entry
  * use the defaults. cabs_autotune fills the table from timed trials. */
 typedef struct {
-  int32_t extrap_tn;    /* extrapolation GEMMs (C V_w, R^T U_w): output columns per
-                         * thread, 16 extrap_tn per CTA: 2, 4 or 8 (8 in FP32 modes
-                         * only); 0 = default (8 FP32, 4 FP64) */
+  int32_t extrap_tn;    /* CUDA-core extrapolation GEMMs (C V_w, R^T U_w; FP32 and
+                         * FP64 modes, the TF32 / BF16 modes run them on tensor
+                         * cores): output columns per thread, 16 extrap_tn per CTA:
+                         * 2, 4 or 8 (8 in FP32 only); 0 = default (8 FP32, 4 FP64) */
   int32_t gather_rows;  /* dense column gather: rows of A per warp in flight: 2, 4 or
                          * 8; 0 = default (4) */
   int32_t assign_bn;    /* TF32 / BF16 k-means assignment: centres per tensor-core
