@@ -499,6 +499,7 @@ cabs_status cabs_sketching_workspace_size(int64_t m, int64_t n, int32_t k, int32
   clear_error();
   CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
   CABS_REQUIRE(m >= 1 && n >= 1 && k >= 1 && k <= CABS_MAX_K && k <= std::min(m, n), "bad m, n, k");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
   *bytes = core_ws_bytes(m, n, k, prec == CABS_PREC_FP64);
   return CABS_OK;
 }
@@ -526,6 +527,7 @@ cabs_status cabs_kmeans_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t
   CABS_REQUIRE(M >= 1 && M < INT32_MAX && d >= 1 && d <= CABS_MAX_K && k2 >= 1 && k2 <= CABS_MAX_K && k2 <= M,
                "bad M, d, k2");
   CABS_REQUIRE(iters >= 0 && iters <= CABS_MAX_ITERS, "bad iters");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
   *bytes = kmeans_ws_bytes(M, d, k2, iters, prec);
   return CABS_OK;
 }
@@ -552,6 +554,7 @@ cabs_status cabs_snap_workspace_size(int64_t M, int32_t d, int32_t k2, int32_t p
   CABS_REQUIRE(bytes != nullptr, "bytes is NULL");
   CABS_REQUIRE(M >= 1 && M < INT32_MAX && d >= 1 && d <= CABS_MAX_K && k2 >= 1 && k2 <= CABS_MAX_K && k2 <= M,
                "bad M, d, k2");
+  CABS_REQUIRE(prec >= CABS_PREC_FP64 && prec <= CABS_PREC_BF16, "unknown precision");
   *bytes = snap_ws_bytes(M, d, k2, prec);
   return CABS_OK;
 }

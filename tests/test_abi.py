@@ -146,3 +146,43 @@ def test_no_cpu_fallback_without_gpu(L):
         pytest.skip("a GPU is present")
     h = C.c_void_p()
     assert L.cabs_create(C.byref(h), 0) == cabs.CABS_ECUDA
+
+
+def test_step_workspace_sizes_validate_on_host(L):
+    """Every per-step workspace query answers on the host, grows with its
+    problem, and refuses what its compute call would refuse."""
+    n, n2 = C.c_size_t(), C.c_size_t()
+    OK, BAD = cabs.CABS_OK, cabs.CABS_EINVAL
+    f64, bf16 = cabs.PREC_FP64, cabs.PREC_BF16
+    # sketching routine: 1 <= k <= min(m, n, 256)
+    assert L.cabs_sketching_workspace_size(2000, 1500, 20, f64, C.byref(n)) == OK and n.value > 0
+    assert L.cabs_sketching_workspace_size(20000, 1500, 20, f64, C.byref(n2)) == OK and n2.value > n.value
+    for m_, n_, k_, p_ in [(2000, 1500, 0, f64), (2000, 1500, 257, f64), (10, 1500, 11, f64), (2000, 1500, 20, 7)]:
+        assert L.cabs_sketching_workspace_size(m_, n_, k_, p_, C.byref(n)) == BAD, (m_, n_, k_, p_)
+    # k-means: 1 <= d, k2 <= 256, k2 <= M, 0 <= iters <= 64
+    assert L.cabs_kmeans_workspace_size(5000, 64, 64, 5, bf16, C.byref(n)) == OK and n.value > 0
+    assert L.cabs_kmeans_workspace_size(50000, 64, 64, 5, bf16, C.byref(n2)) == OK and n2.value > n.value
+    for args in [(5000, 0, 64, 5, bf16), (5000, 257, 64, 5, bf16), (5000, 64, 257, 5, bf16), (10, 64, 11, 5, bf16),
+                 (5000, 64, 64, 65, bf16), (5000, 64, 64, -1, bf16), (5000, 64, 64, 5, 7), (0, 64, 1, 5, bf16)]:
+        assert L.cabs_kmeans_workspace_size(*args, C.byref(n)) == BAD, args
+    # snap: the same bounds on M, d, k2
+    assert L.cabs_snap_workspace_size(5000, 64, 64, bf16, C.byref(n)) == OK and n.value > 0
+    for args in [(5000, 257, 64, bf16), (5000, 64, 0, bf16), (10, 64, 11, bf16), (5000, 64, 64, -1)]:
+        assert L.cabs_snap_workspace_size(*args, C.byref(n)) == BAD, args
+    # threshold: 1 <= M < 2^31
+    assert L.cabs_threshold_workspace_size(5000, C.byref(n)) == OK and n.value > 0
+    assert L.cabs_threshold_workspace_size(0, C.byref(n)) == BAD
+    assert L.cabs_threshold_workspace_size(2 ** 31, C.byref(n)) == BAD
+    # orthogonalisation: 1 <= k <= 256
+    assert L.cabs_orthogonalize_workspace_size(2000, 1500, 20, f64, C.byref(n)) == OK and n.value > 0
+    for args in [(2000, 1500, 0, f64), (2000, 1500, 257, f64), (0, 1500, 20, f64), (2000, 1500, 20, 9)]:
+        assert L.cabs_orthogonalize_workspace_size(*args, C.byref(n)) == BAD, args
+    # Sketch-CUR: 1 <= kb, kt <= min(m, n, 256)
+    cp = cabs.make_cur_params(2000, 1500, 20, 60)
+    assert L.cabs_sketch_cur_workspace_size(C.byref(_src()), C.byref(cp), C.byref(n)) == OK and n.value > 0
+    for kb, kt in [(0, 60), (20, 257), (20, 0)]:
+        bad = cabs.make_cur_params(2000, 1500, kb, kt)
+        assert L.cabs_sketch_cur_workspace_size(C.byref(_src()), C.byref(bad), C.byref(n)) == BAD, (kb, kt)
+    for fn in ("cabs_sketching_workspace_size", "cabs_threshold_workspace_size"):
+        args = (2000, 1500, 20, f64) if fn.startswith("cabs_sketching") else (5000,)
+        assert getattr(L, fn)(*args, None) == BAD
