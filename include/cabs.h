@@ -220,7 +220,12 @@ cabs_status cabs_workspace_size(const cabs_source* src, const cabs_params* p, si
  * ws: device workspace of at least cabs_workspace_size() bytes, 256-byte
  * aligned, owned by the caller and not used by anything else until the
  * stream has passed this sketch. Returns CABS_EINVAL for CABS_FLAG_ERROR
- * without out->err, or with err_samples == 0 on an implicit source. */
+ * without out->err, or with err_samples == 0 on an implicit source.
+ * The column side of step 3 (k-means and snap of Q) runs on a second,
+ * internal stream forked from `stream` and joined back before the follow-up
+ * gather; the library creates one such stream and two events per (device,
+ * caller stream) it is given and keeps them until the process exits, so a
+ * caller should reuse its streams rather than create one per call. */
 cabs_status cabs_sketch(cabs_ctx* ctx, const cabs_source* src, const cabs_params* p,
                         void* ws, size_t ws_bytes, cabs_stream stream, const cabs_result* out);
 
