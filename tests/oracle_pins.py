@@ -665,3 +665,41 @@ def pin_driver_wiring(cabs_fn, source_cls, sketch_fn, embed_fn, kmeans_fn, snap_
     assert not (np.array_equal(r.rows, r.pilot_rows[:7]) and np.array_equal(r.cols, r.pilot_cols[:7]))
     f = sketch_fn(*src.gather(r.rows, r.cols), 120, 90, "stabilized")
     assert np.array_equal(r.final.U, f.U) and np.array_equal(r.final.S, f.S) and np.array_equal(r.final.V, f.V)
+
+
+# ----------------------------------------------- uniforms and sampled entries
+
+def _numpy_philox_words(seed, tag, t):
+    """The four words of block (t, 0, 0, 0) under key (seed, tag), from numpy's
+    own Philox4x64-10 (it increments its counter before each block)."""
+    c = (t - 1) % (1 << 256)
+    start = np.array([(c >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+    bg = np.random.Philox(key=np.array([seed, tag], dtype=np.uint64), counter=start)
+    return [int(x) for x in bg.random_raw(4)]
+
+
+def pin_philox_uniform(pu_fn, seed=11, tag=6, N=9):
+    """u_i = ((r_i >> 11) + 1/2) 2^-53 from word 0 of numpy's Philox block i:
+    every u lies in (0, 1), 2^53 u - 1/2 is a whole number, and the values are
+    those of the independent generator."""
+    u = pu_fn(seed, tag, N)
+    assert np.array_equal(u, philox_uniform_for_pin(seed, tag, N))
+    assert np.all((u > 0) & (u < 1))
+    x = u * 2.0 ** 53 - 0.5
+    assert np.array_equal(x, np.floor(x))
+
+
+def pin_eval_samples(es_fn, seed=5, m=1000, n=777, count=12):
+    """The sampled error's entries: row hi64(w0 m), column hi64(w1 n) of
+    block (t, 0, 0, 0) under key (seed, 2), the words from numpy's Philox."""
+    ii, jj = es_fn(seed, m, n, count)
+    for t in range(count):
+        w = _numpy_philox_words(seed, 2, t)
+        assert ii[t] == (w[0] * m) >> 64 and jj[t] == (w[1] * n) >> 64, t
+
+
+def pin_sq_dists(sq_fn):
+    """Squared distances by hand: from (1, 1) the points (0, 0), (3, 4) and
+    (1, 1) lie at 2, 13 and 0."""
+    X = np.array([[0.0, 0.0], [3.0, 4.0], [1.0, 1.0]])
+    assert sq_fn(X, np.array([1.0, 1.0])).tolist() == [2.0, 13.0, 0.0]

@@ -300,3 +300,39 @@ def test_driver_mutants_rejected(old, new):
     checks = [lambda: pins.pin_driver_wiring(bad, o.DenseSource, o.sketching, o.embed, o.weighted_kmeans, o.snap),
               lambda: pins.pin_follow_up_improves_encoding(bad, o.DenseSource, trials=4)]
     assert any(rejects(c) for c in checks)
+
+
+PU = "return ((r0 >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53"
+
+
+@pytest.mark.parametrize("old,new", [
+    (PU, PU.replace(" + 0.5", "")),                                                    # u = 0 possible
+    (PU, PU.replace("np.uint64(11)", "np.uint64(12)")),                                # wrong shift
+    ("r0 = philox4x64_10_vec(c0, z, z, z, seed, tag)[0]", "r0 = philox4x64_10_vec(c0, z, z, z, seed, tag)[1]"),
+])
+def test_philox_uniform_mutants_rejected(old, new):
+    bad = mutate(o.philox_uniform, old, new)
+    assert rejects(lambda: pins.pin_philox_uniform(bad))
+
+
+ES_RET = "return mulhi64_vec(w0, m).astype(np.int64), mulhi64_vec(w1, n).astype(np.int64)"
+
+
+@pytest.mark.parametrize("old,new", [
+    (ES_RET, "return mulhi64_vec(w1, m).astype(np.int64), mulhi64_vec(w0, n).astype(np.int64)"),  # words swapped
+    (ES_RET, "return (w0 % np.uint64(m)).astype(np.int64), (w1 % np.uint64(n)).astype(np.int64)"),  # modulo map
+    ("w0, w1, _, _ = philox4x64_10_vec(t, z, z, z, seed, TAG_EVAL)",
+     "w0, w1, _, _ = philox4x64_10_vec(t, z, z, z, seed, TAG_ROWS)"),                               # wrong key
+])
+def test_eval_samples_mutants_rejected(old, new):
+    bad = mutate(o.eval_samples, old, new)
+    assert rejects(lambda: pins.pin_eval_samples(bad))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("d = X - z[None, :]", "d = X + z[None, :]"),
+    ("return (d * d).sum(axis=1)", "return np.abs(d).sum(axis=1)"),
+])
+def test_sq_dists_mutants_rejected(old, new):
+    bad = mutate(o.sq_dists_to, old, new)
+    assert rejects(lambda: pins.pin_sq_dists(bad))

@@ -258,3 +258,15 @@ def test_sparse_error_identity():
     num = np.sum(v.astype(np.float64) ** 2) - 2 * cross + l2
     want = o.rel_fro_error_dense(A, U, S, V)
     assert abs(np.sqrt(num / np.sum(A ** 2)) - want) < 1e-12 * want
+
+
+def test_philox_uniform_definition():
+    pins.pin_philox_uniform(o.philox_uniform)
+
+
+def test_eval_samples_definition():
+    pins.pin_eval_samples(o.eval_samples)
+
+
+def test_sq_dists_closed_form():
+    pins.pin_sq_dists(o.sq_dists_to)
