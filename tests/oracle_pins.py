@@ -703,3 +703,23 @@ def pin_sq_dists(sq_fn):
     (1, 1) lie at 2, 13 and 0."""
     X = np.array([[0.0, 0.0], [3.0, 4.0], [1.0, 1.0]])
     assert sq_fn(X, np.array([1.0, 1.0])).tolist() == [2.0, 13.0, 0.0]
+
+
+def pin_csr_gather(csr_cls, dense_cls):
+    """The sparse source's gathers and entries equal the dense source's on the
+    same matrix held densely (numpy indexing of a dense array, independent of
+    scipy's sparse slicing), bit for bit; rows with no stored entries gather
+    as zeros."""
+    ip, ix, v = synth.sparse_lowrank(300, 200, 0.03, rank=4, seed=3)
+    src = csr_cls(ip, ix, v, 200)
+    A = np.zeros((300, 200))
+    for r in range(300):
+        A[r, ix[ip[r]:ip[r + 1]]] = v[ip[r]:ip[r + 1]]
+    dense = dense_cls(A)
+    g = np.random.default_rng(2)
+    rows = np.sort(g.choice(300, 17, replace=False))
+    cols = np.sort(g.choice(200, 13, replace=False))
+    for a, b in zip(src.gather(rows, cols), dense.gather(rows, cols)):
+        assert a.shape == b.shape and np.array_equal(a, b)
+    ii, jj = g.integers(0, 300, 500), g.integers(0, 200, 500)
+    assert np.array_equal(src.entries(ii, jj), dense.entries(ii, jj))

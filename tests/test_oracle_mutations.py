@@ -336,3 +336,17 @@ def test_eval_samples_mutants_rejected(old, new):
 def test_sq_dists_mutants_rejected(old, new):
     bad = mutate(o.sq_dists_to, old, new)
     assert rejects(lambda: pins.pin_sq_dists(bad))
+
+
+@pytest.mark.parametrize("old,new", [
+    ("C = np.asarray(self.A[:, cols].toarray(), dtype=np.float64)",
+     "C = np.asarray(self.A[:, rows].toarray(), dtype=np.float64)"),                       # wrong index set
+    ("Rt = np.asarray(self.A[rows, :].toarray().T, dtype=np.float64)",
+     "Rt = np.asarray(self.A[rows, :].toarray(), dtype=np.float64)"),                      # not transposed
+    ("W = np.asarray(self.A[rows, :][:, cols].toarray(), dtype=np.float64)",
+     "W = np.asarray(self.A[cols, :][:, rows].toarray().T, dtype=np.float64)"),            # transposed intersection
+])
+def test_csr_gather_mutants_rejected(old, new):
+    bad = mutate(o.CSRSource.gather, old, new)
+    Bad = type("Bad", (o.CSRSource,), {"gather": bad})
+    assert rejects(lambda: pins.pin_csr_gather(Bad, o.DenseSource))

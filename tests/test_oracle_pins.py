@@ -270,3 +270,7 @@ def test_eval_samples_definition():
 
 def test_sq_dists_closed_form():
     pins.pin_sq_dists(o.sq_dists_to)
+
+
+def test_csr_gather_against_explicit_dense():
+    pins.pin_csr_gather(o.CSRSource, o.DenseSource)
