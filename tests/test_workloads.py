@@ -72,3 +72,19 @@ def test_batched_specs_ranges():
     assert m.min() >= 1000 and m.max() <= 20000 and r.min() >= 10 and r.max() <= 100
     assert k.min() >= 16 and k.max() <= 128
     assert specs == synth.batched_specs(count=300, seed=11)
+
+
+def test_decaying_lowrank_device_generator_on_cpu():
+    """The generator of the dense benchmark matrix (run here on torch's CPU
+    device, in row blocks and into a wider preallocated buffer, as the bench
+    uses it): the same recipe as the host version."""
+    import torch
+    out = torch.zeros(700, 520, dtype=torch.float32)
+    A, U, s, V = synth.decaying_lowrank_device(700, 500, rank=40, decay=30, noise_std=1e-4, seed=7, device="cpu",
+                                               out=out, row_block=256)
+    assert A is out and torch.all(out[:, 500:] == 0)
+    U, s, V = U.numpy(), s.numpy(), V.numpy()
+    assert np.allclose(U.T @ U, np.eye(40), atol=1e-12) and np.allclose(V.T @ V, np.eye(40), atol=1e-12)
+    assert np.allclose(s, np.exp(-np.arange(1, 41) / 30.0), rtol=1e-15, atol=0)
+    E = out[:, :500].double().numpy() - (U * s) @ V.T
+    assert abs(E.std() / 1e-4 - 1) < 0.02
