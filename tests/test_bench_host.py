@@ -90,3 +90,37 @@ def test_traffic_figure_goes_stale_with_its_source(tmp_path, monkeypatch):
     assert bench.kernel_traffic("y_kernel", "dense") is None
     src.write_text("kernel v2")
     assert bench.kernel_traffic("x_kernel", "dense") is None
+
+
+def _run_bench(args, env_extra=None):
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), *args], capture_output=True,
+                          text=True, env=env, timeout=600)
+
+
+def test_reference_arm_line_on_the_host():
+    """The reference arm (the oracle on one host core) needs no GPU: one JSON
+    line with the metric, the reference marker, its cpu_baseline and an e2e
+    that copies nothing."""
+    out = _run_bench(["--impl", "reference", "--workload", "plain", "--steps", "1", "--warmup", "0"])
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "sketches/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == dict(value=d["value"], unit="sketches/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    assert d["config"]["workload"] == "plain"
+    # the plain workload's error as the oracle computes it on the whole matrix
+    assert abs(cb["oracle_error"] - 0.1162543807549) < 1e-9
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    out = _run_bench(["--impl", "reference", "--workload", "plain", "--steps", "1", "--warmup", "0"],
+                     {"RANK": "1", "WORLD_SIZE": "2"})
+    assert out.returncode == 0 and out.stdout.strip() == ""
